@@ -1,0 +1,355 @@
+"""Benchmark of the GB300 Stratego engine.
+
+Default workload (the headline): 65,536 parallel game slots, random legal
+policy, auto-reset, 2,000 plies per slot per step through the persistent
+launch (st_env_run), every ply's 1,264-byte legal mask, action, reward, done
+flag and ply counter written to a 16-row output ring (1.3 GB, larger than L2).
+Reported: env-steps/s, the HBM roofline of the step kernel, the plain
+per-ply launch path beside it, an end-to-end number through the public API
+with host buffers, and the oracle on the host cores.  Secondary workloads:
+observation planes for 16,384 replayed positions and belief-sample rollouts
+for 4,096 positions x 256 samples x depth 32.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MASK_BYTES = 1264
+BYTES_PER_ENV_STEP = MASK_BYTES + 2 + 1 + 1 + 2   # mask + action + reward + done + ply
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--games", type=int, default=65536)
+    p.add_argument("--plies", type=int, default=2000, help="plies per slot per step")
+    p.add_argument("--ring", type=int, default=16)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--wpb", type=int, default=0, help="warps per block (0 = tuned default)")
+    p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
+    p.add_argument("--no-extras", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle on the host
+
+def oracle_env_rate(seed, plies, budget_s=12.0, chunk=64):
+    """Oracle env-steps/s on one host thread over a bounded sample of slots."""
+    import oracle
+    t0 = time.perf_counter()
+    steps = 0
+    slot = 0
+    while True:
+        oracle.env_run(seed, chunk, plies, slot0=slot)
+        steps += chunk * plies
+        slot += chunk
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, "%d slots x %d plies (masks written), slots 0..%d" % (slot, plies, slot - 1), dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.lib()
+    plies = args.plies
+    chunk = 16
+    for _ in range(args.warmup):
+        oracle.env_run(args.seed, 4, 100)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.env_run(args.seed, chunk, plies, slot0=k * chunk)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * chunk * plies / total
+    sample = "%d steps x (%d slots x %d plies) of the %d-slot workload, masks written" % (
+        args.steps, chunk, plies, args.games)
+    line = {"impl": "reference", "metric": "env steps/s at 65,536 games", "value": value, "unit": "env-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "65,536 random-policy Stratego games, auto-reset, 2,000 plies per slot",
+                       "games": args.games, "plies_per_step": plies},
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2511_07312_gb300 as st
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    N, S, R = args.games, args.plies, args.ring
+    env = st.Env(N, seed=args.seed + rank, device=local)
+    wpb = args.wpb or 4
+    gpf = args.gpf or 1
+    env.set_launch(wpb, 0, gpf)
+    ring = env.run(1, R)   # allocates the ring; later calls reuse it
+    env.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (also captures the CUDA graph)
+    for _ in range(args.warmup):
+        env.run(S, R, out=ring)
+    env.sync()
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(env.stream)
+        for _ in range(args.steps):
+            env.run(S, R, out=ring)
+        end.record(env.stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    env.sync()
+    env_steps = float(N) * S * args.steps * world
+    value = env_steps / (ms / 1000.0)
+    per_launch_s = ms / 1000.0 / args.steps
+    bytes_per_launch = float(N) * S * BYTES_PER_ENV_STEP
+    peak, peak_kind = peaks()
+    achieved = bytes_per_launch / per_launch_s / 1e9
+    clocks = clk.summary()
+
+    extras = {}
+    # plain per-ply launch path on the same workload shape (fewer plies)
+    plain_plies = 50
+    out = env.step()
+    env.sync()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(env.stream)
+    for _ in range(plain_plies):
+        env.step(out=out)
+    s1.record(env.stream)
+    s1.synchronize()
+    plain_ms = s0.elapsed_time(s1)
+    extras["plain_path"] = {"value": N * plain_plies / (plain_ms / 1000.0), "unit": "env-steps/s",
+                            "plies": plain_plies, "note": "one st_env_step launch per ply, same outputs"}
+
+    # end to end through the public API with host buffers: H2D of the
+    # per-slot restart requests, the run, D2H of the per-slot counters
+    which_h = torch.zeros(N, dtype=torch.uint8).pin_memory()
+    stats_h = torch.empty((N, 8), dtype=torch.int32).pin_memory()
+    which_d = torch.empty(N, dtype=torch.uint8, device=dev)
+    e2e_steps = max(2, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(env.stream):
+        e0.record(env.stream)
+        for _ in range(e2e_steps):
+            which_d.copy_(which_h, non_blocking=True)
+            env.reset(which=which_d)
+            env.run(S, R, out=ring)
+            stats_h.copy_(env.stats(), non_blocking=True)
+        e1.record(env.stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": float(N) * S * e2e_steps * world / (e2e_ms / 1000.0), "unit": "env-steps/s",
+           "h2d_bytes_per_step": N, "d2h_bytes_per_step": N * 8 * 4}
+
+    if not args.no_extras and rank == 0:
+        try:
+            extras.update(secondary(st, torch, dev, args))
+        except Exception as exc:  # secondary workloads never hide the headline
+            extras["secondary_error"] = repr(exc)
+
+    cpu = None
+    if rank == 0:
+        rate, sample, secs = oracle_env_rate(args.seed, S)
+        cpu = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 1)}
+
+    if rank == 0:
+        line = {"metric": "env steps/s at 65,536 games", "value": value, "unit": "env-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic",
+                "config": {"workload": "65,536 random-policy Stratego games, auto-reset, 2,000 plies per slot "
+                                       "per step (configs[1])",
+                           "games_per_gpu": N, "plies_per_step": S, "ring_rows": R,
+                           "l2": "output ring %.2f GB > L2 (inputs larger than L2, no flush)" %
+                                 (R * N * MASK_BYTES / 1e9),
+                           "launch": {"warps_per_block": wpb, "games_per_fetch": gpf}},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_kind": peak_kind + " hbm_gbs (copy, burst)",
+                             "algorithmic_bytes_per_env_step": BYTES_PER_ENV_STEP, "kernel": "k_env_run"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+                "cpu_baseline": cpu, "extras": extras}
+        print(json.dumps(line), flush=True)
+    env.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def secondary(st, torch, dev, args):
+    """Configs 3 and 4: observation planes and belief-sample rollouts."""
+    import numpy as np
+    out = {}
+    # config 1 trajectories, played on the GPU: 64 games to their end
+    G = 64
+    env = st.Env(G, seed=1, autoreset=False, device=dev.index)
+    setups = env.export(torch.arange(G))[:, :80].contiguous()
+    traj = env.run(1000, 1000, want=("action",))
+    env.sync()
+    acts = traj["action"].t().contiguous()
+    lengths = (acts >= 0).sum(1).cpu().numpy()
+    rng = np.random.default_rng(3)
+    B = 16384
+    games = rng.integers(0, G, B).astype(np.int32)
+    plies = np.array([rng.integers(0, min(600, max(1, lengths[g]) - 1) + 1) for g in games], np.int16)
+    order = np.lexsort((plies, games))
+    games, plies = games[order], plies[order]
+    gi = torch.from_numpy(games).to(dev)
+    pl = torch.from_numpy(plies).to(dev)
+    o = st.obs_encode(setups, acts, gi, pl)
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        st.obs_encode(setups, acts, gi, pl, out=o)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    byts = B * (487 * 100 * 3 + MASK_BYTES)
+    out["obs_encode"] = {"positions_per_s": B / (ms / 1000), "ms": ms, "GB_per_s_written": byts / (ms / 1000) / 1e9,
+                         "positions": B, "bytes_written_per_position": 487 * 100 * 3 + MASK_BYTES}
+    # config 4: 4,096 positions x 256 samples x depth 32
+    P, K, D = 4096, 256, 32
+    sel = np.linspace(0, B - 1, P).astype(np.int64)
+    pos, status = st.replay_positions(setups, acts, gi[sel].contiguous(), pl[sel].contiguous())
+    tallies, _ = st.rollout(pos, K, D, seed=7)
+    torch.cuda.synchronize()
+    t0.record()
+    reps = 3
+    for _ in range(reps):
+        st.rollout(pos, K, D, seed=7, out=tallies)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    tl = tallies.sum(0).cpu().numpy().tolist()
+    out["belief_rollout"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K, "depth": D,
+                             "tallies_win_loss_draw_unfinished": tl}
+    env.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

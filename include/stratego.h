@@ -1,0 +1,272 @@
+/*
+ * stratego.h -- C ABI of the GB300 Stratego engine.
+ *
+ * A batched, GPU-resident implementation of the game engine that self-play
+ * and test-time search of arXiv 2511.07312 ("Superhuman AI for Stratego
+ * Using Self-Play Reinforcement Learning and Test-Time Search") spend their
+ * non-network time in: legal-move masks, move apply and battles, endings with
+ * auto-reset, observation planes, belief samples of the opponent's hidden
+ * pieces and fixed-depth random rollouts.  Section references are to that
+ * paper: App. A (rules), App. B (simulator), App. C (information state),
+ * App. D.1 (game-rule hyperparameters), App. E (search).
+ *
+ * Conventions shared by every entry point
+ *  - Square s = 10*row + col, row 0 is red's back row, col 0 is file a.
+ *    Lakes: 42,43,52,53,46,47,56,57 (App. A: 92 occupiable squares).
+ *  - Piece ids: red 0-39 start on squares 0-39, blue 40-79 on squares 60-99.
+ *  - Type codes 0-11: Spy, Scout, Miner, Sergeant, Lieutenant, Captain,
+ *    Major, Colonel, General, Marshal, Flag, Bomb (the order of App. C
+ *    channels 0-11).
+ *  - Action a = from*100 + to.  A legal-action mask is 1264 bytes: bit a&7 of
+ *    byte a>>3, bytes 1250-1263 zero.
+ *  - Red (player 0) moves on even plies.
+ *  - Ending codes: 0 none, 1 flag captured, 2 the player to move has no legal
+ *    move (the other player wins), 3 neither player can move (draw), 4 k
+ *    battleless plies (draw), 5 game-length cap (draw).  Rewards are from the
+ *    red player's view: +1, -1, or 0 (App. B.1, ComputeRewardPl0).
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *    seed (low word first); the counter layout of each draw is given at the
+ *    entry point that makes it.  A uniform draw in [0,n) is floor(r*n/2^32).
+ *
+ * Memory and streams
+ *  - Every array argument is a caller-owned DEVICE pointer unless the
+ *    comment says HOST.  The library never frees caller memory.
+ *  - Calls are asynchronous on the given stream (cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  The caller keeps inputs alive and
+ *    unmodified until the work completes.
+ *  - An st_env owns its device state (allocated once in st_env_create, App.
+ *    B "no dynamic allocation after construction") and its stream.
+ *
+ * Errors
+ *  - Every call returns st_status.  Argument errors are detected on the host
+ *    before anything is enqueued (ST_ERR_INVALID, nothing changes).
+ *  - st_last_error() returns a thread-local description of the last failure.
+ *  - Errors found on the device (an illegal supplied action, an invalid
+ *    snapshot) never fault: the item is left unchanged and the error is
+ *    latched; st_env_sync() reports it for an env, per-item status arrays
+ *    report it for the stateless calls.
+ */
+#ifndef STRATEGO_GB300_H
+#define STRATEGO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum st_status {
+    ST_OK = 0,
+    ST_ERR_INVALID = 1,          /* bad argument; nothing was enqueued */
+    ST_ERR_OOM = 2,              /* device allocation failed at create time */
+    ST_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+    ST_ERR_ILLEGAL_ACTION = 4,   /* a supplied action was not legal (latched) */
+    ST_ERR_TIMEOUT = 5,          /* a bounded wait expired */
+    ST_ERR_BUSY = 6,             /* no capacity right now; retry later */
+    ST_ERR_NOT_READY = 7,        /* result not available yet */
+    ST_ERR_BAD_POSITION = 8      /* a snapshot or log failed validation (latched) */
+} st_status;
+
+/* Rule flags (App. A "Additional rules for competitive play"). */
+#define ST_RULE_TWO_SQUARE 1u    /* two-square rule, App. A and App. B.2 */
+#define ST_RULE_CHASE      2u    /* continuous-chasing rule, Tab. chase, App. B.3 */
+#define ST_AUTORESET       4u    /* env only: ended games restart at once (App. B.1) */
+#define ST_RULES_ALL       (ST_RULE_TWO_SQUARE | ST_RULE_CHASE)
+
+#define ST_MASK_BYTES   1264
+#define ST_NCHAN        487      /* observation channels, App. C */
+#define ST_MAX_GAMES    (1 << 22)
+#define ST_MAX_BATTLELESS 255
+
+/* Game-rule parameters (App. D.1, Tab. game-hyper). */
+typedef struct st_rules {
+    int16_t battleless_limit;    /* k of the k-move rule: 1..255 (paper: 100 training, 200 online) */
+    int16_t max_plies;           /* draw after this many plies: 1..32767 (paper: 4000) */
+    uint32_t flags;              /* ST_RULE_* */
+} st_rules;
+
+/*
+ * Position snapshot: everything needed to continue a game exactly (App. B.4
+ * "reset to a non-initial state"), 784 bytes, little endian.
+ *   flags[p]: bit0 alive, bit1 revealed (a battle showed the type), bit2 has
+ *   moved, bit3 moved more than one square once (so it is a Scout), bits4-6
+ *   cause of death 1-6 (App. C.1 "Causes of death"), 0 while alive.
+ *   square[p]: current square, or the battle square of a captured piece.
+ *   last_battle: the previous ply was a battle.
+ *   chaser: player whose continuous chase is in progress (0xFF none);
+ *   chase_plies: plies since that chase began (its moves are hist[0..n-1]).
+ *   ts_*: two-square rule state per player -- last-moved piece, number of
+ *   squares recorded (2-4) and those squares, oldest first (0xFF unused).
+ *   hist[i]: the action played i+1 plies ago, 0xFFFF if unknown.
+ */
+typedef struct st_position {
+    uint8_t type[80];
+    uint8_t square[80];
+    uint8_t flags[80];
+    int16_t ply;
+    int16_t battleless;
+    uint8_t last_battle;
+    uint8_t chaser;
+    uint8_t chase_plies;
+    uint8_t reserved0;            /* zero */
+    uint8_t ts_pid[2];
+    uint8_t ts_len[2];
+    uint8_t ts_sq[2][4];
+    uint8_t reserved1[12];        /* zero */
+    uint16_t hist[256];
+} st_position;
+
+typedef struct st_env st_env;
+
+typedef struct st_env_config {
+    int32_t num_games;            /* parallel game slots N, 1..ST_MAX_GAMES */
+    uint64_t seed;                /* Philox key */
+    st_rules rules;
+    uint32_t env_flags;           /* ST_AUTORESET */
+    int32_t device;               /* CUDA device ordinal */
+    void* stream;                 /* cudaStream_t for every call on this env; NULL = default */
+} st_env_config;
+
+/* Library identification and the thread-local text of the last error. */
+const char* st_version(void);
+const char* st_last_error(void);
+
+/*
+ * st_env_create: allocate the env's device state for cfg->num_games slots
+ * and start every slot's first game (episode 0).  Setup of slot i, episode e
+ * (App. A: 40 pieces on each side's four back rows): each side's sorted
+ * 40-piece multiset is Fisher-Yates shuffled, i = 39..1, j = U[0,i+1) from
+ * draw d = 39-i, word d%4 of Philox at counter (i, e, 0, 1<<24 | side<<8 | d/4),
+ * and laid on the side's squares in ascending order.
+ * Errors: ST_ERR_INVALID (bad config), ST_ERR_OOM, ST_ERR_CUDA.
+ */
+st_status st_env_create(const st_env_config* cfg, st_env** out);
+
+/* Release every device allocation of the env (synchronizes its stream). */
+st_status st_env_destroy(st_env* env);
+
+/*
+ * st_env_reset: start a new game in the slots with which[i] != 0 (all slots
+ * if which is NULL).  Each restarted slot's episode counter is incremented.
+ * setups: [N][80] type per piece id, or NULL for the Philox setup above.
+ * A setup whose type counts per side differ from Tab. pieces leaves the slot
+ * unchanged and latches ST_ERR_BAD_POSITION.
+ */
+st_status st_env_reset(st_env* env, const uint8_t* setups, const uint8_t* which);
+
+/*
+ * st_env_step: one ply in every slot (App. B.1 ApplyActions and
+ * SampleRandomLegalAction).  actions[N] int16: the action for each slot, or
+ * -1 for the uniform random policy; NULL = random everywhere.  The random
+ * policy at ply t of episode e in slot i takes word 0 of Philox at counter
+ * (i, e, t, 2<<24) and plays the floor(r*n/2^32)-th of the n legal actions in
+ * ascending order.  After the ply, endings are checked in ending-code order;
+ * with ST_AUTORESET an ended game restarts at once.
+ * Outputs (each may be NULL), per slot:
+ *   action_out[N] int16  action played (-1 if none was played)
+ *   reward_out[N] int8   red-player reward of a game that ended on this ply
+ *   done_out[N]   uint8  ending code
+ *   ply_out[N]    int16  ply index of the action in its game
+ *   mask_out[N][1264]    legal mask of the player to move afterwards (of the
+ *                        new game after an auto-reset; zero for an ended game
+ *                        without auto-reset)
+ * A slot whose supplied action is illegal is left unchanged (action_out -1,
+ * mask of the unchanged state) and ST_ERR_ILLEGAL_ACTION is latched.
+ */
+st_status st_env_step(st_env* env, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
+                      uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out);
+
+/*
+ * st_env_run: n_steps random-policy plies in every slot in one persistent
+ * launch, game state held on chip between plies.  Step j of the call writes
+ * the outputs of st_env_step into ring row j % ring_steps of each output
+ * ([ring_steps][N] and [ring_steps][N][1264]); any output may be NULL.
+ * Results are identical to n_steps calls of st_env_step with actions NULL.
+ */
+st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
+                     int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring);
+
+/* Launch shape of st_env_run: warps per block (1..32), blocks per SM (>=1,
+ * 0 = occupancy maximum) and slots a warp claims per queue fetch (>=1). */
+st_status st_env_set_launch(st_env* env, int32_t warps_per_block, int32_t blocks_per_sm,
+                            int32_t games_per_fetch);
+
+/* Wait for the env's stream; return and clear a latched device error. */
+st_status st_env_sync(st_env* env);
+
+/* Per-slot counters [N][8] uint32: games ended with codes 1-5, plies played,
+ * red wins, blue wins (cumulative since create). */
+st_status st_env_stats(st_env* env, uint32_t* stats_out);
+
+/* Snapshots of slots idx[0..n-1] (App. B.4).  Export writes out[n]; import
+ * replaces the slots' games (episode counters unchanged).  An invalid
+ * snapshot leaves its slot unchanged and latches ST_ERR_BAD_POSITION. */
+st_status st_env_export(st_env* env, const int32_t* idx, int32_t n, st_position* out);
+st_status st_env_import(st_env* env, const int32_t* idx, int32_t n, const st_position* in);
+
+/*
+ * Replay of action logs (App. B.1: states are reconstructed on demand from
+ * compact records).  Game g < num_logs starts from setups[g] (type per piece
+ * id, [num_logs][80]) and plays actions[g][0..log_len-1] ([num_logs][log_len]
+ * int16); item b is game[b] after ply[b] plies.  Every logged action is
+ * checked for legality and no intermediate position may have ended the game.
+ * Items sorted by (game, ply) are cheapest: a warp walks consecutive items of
+ * one game once.  item_status[B] (may be NULL): 0 ok, 1 out-of-range item,
+ * bad setup or illegal log entry (its outputs are zero).
+ */
+st_status st_replay_positions(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
+                              const int32_t* game, const int16_t* ply, int32_t B, const st_rules* rules,
+                              st_position* out, uint8_t* item_status, void* stream);
+
+/* Items a replay warp takes (default 4); a process-wide tuning knob. */
+st_status st_replay_set_chunk(int32_t items_per_warp);
+
+/*
+ * st_obs_encode: observation planes of App. C for B replayed items, for the
+ * player player[b] (0/1) or the player to move (-1 or player NULL), in the
+ * absolute board frame.  planes [B][487][100] uint8: indicators 0/1, history
+ * -1 as 255, probabilities and fractions num/den as floor(255*num/den+1/2);
+ * planes_bf16 [B][487][100] bf16 bits: the same values with num/den rounded
+ * to nearest-even bf16; mask [B][1264]: legal mask of the player to move.
+ * Any output may be NULL.
+ */
+st_status st_obs_encode(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
+                        const int32_t* game, const int16_t* ply, const int8_t* player, int32_t B,
+                        const st_rules* rules, uint8_t* planes, uint16_t* planes_bf16, uint8_t* mask,
+                        uint8_t* item_status, void* stream);
+
+/*
+ * st_belief_sample: K assignments of types to the hidden pieces of the
+ * opponent of the player to move in each position, uniform over the
+ * assignments consistent with the public history (App. E step 1, with the
+ * uniform posterior standing in for the belief network): revealed and
+ * captured pieces keep their type, a piece that moved more than one square is
+ * a Scout, a moved piece is neither Bomb nor Flag, type counts are respected.
+ * Draw w of sample k of position p is word w%4 of Philox at counter
+ * (stream_ids[p] or p, k, 0, 3<<24 | w/4); the immovable pieces are placed
+ * by a partial Fisher-Yates over the unmoved hidden pieces in ascending
+ * square order, the movable multiset by a full Fisher-Yates over the other
+ * hidden pieces in ascending square order.
+ * types[P][K][40]: type of opponent piece id 40*opp + i for i < 40.
+ */
+st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_t seed,
+                           const uint32_t* stream_ids, uint8_t* types, uint8_t* item_status, void* stream);
+
+/*
+ * st_rollout: for each position and each of K samples, replace the hidden
+ * opponent types by the sample (types, or the st_belief_sample draw when
+ * types is NULL) and play up to `depth` random-policy plies, ply d taking
+ * word 0 of Philox at counter (stream_ids[p] or p, k, d, 4<<24) (App. E step
+ * 2 with a random policy in place of the move network).  tallies[P][4]
+ * int32: wins, losses, draws of the player to move at the root, and
+ * rollouts unfinished after `depth` plies.
+ */
+st_status st_rollout(const st_position* pos, int32_t P, int32_t K, int32_t depth, uint64_t seed,
+                     const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
+                     int32_t* tallies, uint8_t* item_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

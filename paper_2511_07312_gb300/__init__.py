@@ -1,0 +1,258 @@
+"""Python binding of the GB300 Stratego engine (libstratego_gb300.so).
+
+Argument marshalling only: every step of the game engine runs in the CUDA
+kernels behind the C ABI of include/stratego.h.  PyTorch supplies device
+memory and streams; tensors are passed by data pointer.  The library is
+required: if it cannot be loaded every entry point raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MASK_BYTES = 1264
+NCHAN = 487
+POS_BYTES = 784
+RULE_TWO_SQUARE = 1
+RULE_CHASE = 2
+RULES_ALL = RULE_TWO_SQUARE | RULE_CHASE
+AUTORESET = 4
+
+ST_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "cuda error", 4: "illegal action",
+                5: "timeout", 6: "busy", 7: "not ready", 8: "bad position"}
+
+
+class StrategoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "error"), code, msg))
+        self.code = code
+
+
+class st_rules(ctypes.Structure):
+    _fields_ = [("battleless_limit", ctypes.c_int16), ("max_plies", ctypes.c_int16), ("flags", ctypes.c_uint32)]
+
+
+class st_env_config(ctypes.Structure):
+    _fields_ = [("num_games", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rules", st_rules),
+                ("env_flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i32, i16, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int16, ctypes.c_uint64
+    L.st_version.restype = ctypes.c_char_p
+    L.st_last_error.restype = ctypes.c_char_p
+    for name, args in {
+        "st_env_create": [ctypes.POINTER(st_env_config), ctypes.POINTER(vp)],
+        "st_env_destroy": [vp],
+        "st_env_reset": [vp, vp, vp],
+        "st_env_step": [vp, vp, vp, vp, vp, vp, vp],
+        "st_env_run": [vp, i32, i32, vp, vp, vp, vp, vp],
+        "st_env_set_launch": [vp, i32, i32, i32],
+        "st_env_sync": [vp],
+        "st_env_stats": [vp, vp],
+        "st_env_export": [vp, vp, i32, vp],
+        "st_env_import": [vp, vp, i32, vp],
+        "st_replay_positions": [vp, vp, i32, i32, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp],
+        "st_replay_set_chunk": [i32],
+        "st_obs_encode": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
+        "st_belief_sample": [vp, i32, i32, u64, vp, vp, vp, vp],
+        "st_rollout": [vp, i32, i32, i32, u64, vp, vp, ctypes.POINTER(st_rules), vp, vp, vp],
+    }.items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+
+
+def _check(code):
+    if code != ST_OK:
+        raise StrategoError(code, lib().st_last_error().decode())
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def set_replay_chunk(items_per_warp):
+    _check(lib().st_replay_set_chunk(int(items_per_warp)))
+
+
+def make_rules(k=100, cap=1000, flags=RULES_ALL):
+    return st_rules(int(k), int(cap), int(flags))
+
+
+def version():
+    return lib().st_version().decode()
+
+
+class Env:
+    """N game slots on one GPU (App. B.1).  All outputs are CUDA tensors."""
+
+    def __init__(self, num_games, seed=1, k=100, cap=1000, flags=RULES_ALL, autoreset=True, device=0,
+                 stream=None):
+        self.device = torch.device("cuda", device)
+        self.N = int(num_games)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        cfg = st_env_config(self.N, int(seed) & 0xFFFFFFFFFFFFFFFF, make_rules(k, cap, flags),
+                            AUTORESET if autoreset else 0, int(device), self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        _check(lib().st_env_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().st_env_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, shape, dtype):
+        with torch.cuda.device(self.device):
+            return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def wait_for_current(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def step(self, actions=None, want_mask=True, out=None):
+        """One ply in every slot; returns dict(action, reward, done, ply, mask)."""
+        if out is None:
+            out = dict(action=self._empty(self.N, torch.int16), reward=self._empty(self.N, torch.int8),
+                       done=self._empty(self.N, torch.uint8), ply=self._empty(self.N, torch.int16),
+                       mask=self._empty((self.N, MASK_BYTES), torch.uint8) if want_mask else None)
+        if actions is not None:
+            self.wait_for_current()
+        _check(lib().st_env_step(self._h, _ptr(actions, torch.int16, "actions"), _ptr(out["action"]),
+                                 _ptr(out["reward"]), _ptr(out["done"]), _ptr(out["ply"]), _ptr(out.get("mask"))))
+        return out
+
+    def run(self, n_steps, ring_steps=None, want=("action", "reward", "done", "ply", "mask"), out=None):
+        ring_steps = int(ring_steps or n_steps)
+        if out is None:
+            shp = (ring_steps, self.N)
+            out = dict(action=self._empty(shp, torch.int16) if "action" in want else None,
+                       reward=self._empty(shp, torch.int8) if "reward" in want else None,
+                       done=self._empty(shp, torch.uint8) if "done" in want else None,
+                       ply=self._empty(shp, torch.int16) if "ply" in want else None,
+                       mask=self._empty(shp + (MASK_BYTES,), torch.uint8) if "mask" in want else None)
+        _check(lib().st_env_run(self._h, int(n_steps), ring_steps, _ptr(out["action"]), _ptr(out["reward"]),
+                                _ptr(out["done"]), _ptr(out["ply"]), _ptr(out["mask"])))
+        return out
+
+    def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1):
+        _check(lib().st_env_set_launch(self._h, int(warps_per_block), int(blocks_per_sm), int(games_per_fetch)))
+
+    def reset(self, setups=None, which=None):
+        self.wait_for_current()
+        _check(lib().st_env_reset(self._h, _ptr(setups, torch.uint8, "setups"), _ptr(which, torch.uint8, "which")))
+
+    def sync(self):
+        _check(lib().st_env_sync(self._h))
+
+    def stats(self):
+        out = self._empty((self.N, 8), torch.int32)
+        _check(lib().st_env_stats(self._h, _ptr(out)))
+        return out
+
+    def export(self, idx):
+        idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
+        out = self._empty((idx.numel(), POS_BYTES), torch.uint8)
+        self.wait_for_current()
+        _check(lib().st_env_export(self._h, _ptr(idx), idx.numel(), _ptr(out)))
+        return out
+
+    def import_(self, idx, pos):
+        idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
+        self.wait_for_current()
+        _check(lib().st_env_import(self._h, _ptr(idx), idx.numel(), _ptr(pos, torch.uint8, "positions")))
+
+
+def _dev(t, dtype, device):
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+def replay_positions(setups, actions, game, ply, k=100, cap=1000, flags=RULES_ALL, stream=None):
+    dev = setups.device
+    B = game.numel()
+    out = torch.empty((B, POS_BYTES), dtype=torch.uint8, device=dev)
+    status = torch.empty(B, dtype=torch.uint8, device=dev)
+    r = make_rules(k, cap, flags)
+    _check(lib().st_replay_positions(_ptr(setups, torch.uint8), _ptr(actions, torch.int16), actions.shape[1],
+                                     actions.shape[0], _ptr(game, torch.int32), _ptr(ply, torch.int16), B, ctypes.byref(r),
+                                     _ptr(out), _ptr(status), _stream(stream)))
+    return out, status
+
+
+def obs_encode(setups, actions, game, ply, player=None, k=100, cap=1000, flags=RULES_ALL, want_u8=True,
+               want_bf16=True, want_mask=True, out=None, stream=None):
+    dev = setups.device
+    B = game.numel()
+    if out is None:
+        out = dict(planes=torch.empty((B, NCHAN, 100), dtype=torch.uint8, device=dev) if want_u8 else None,
+                   planes_bf16=torch.empty((B, NCHAN, 100), dtype=torch.bfloat16, device=dev) if want_bf16 else None,
+                   mask=torch.empty((B, MASK_BYTES), dtype=torch.uint8, device=dev) if want_mask else None,
+                   status=torch.empty(B, dtype=torch.uint8, device=dev))
+    r = make_rules(k, cap, flags)
+    _check(lib().st_obs_encode(_ptr(setups, torch.uint8), _ptr(actions, torch.int16), actions.shape[1],
+                               actions.shape[0], _ptr(game, torch.int32), _ptr(ply, torch.int16), _ptr(player, torch.int8), B,
+                               ctypes.byref(r), _ptr(out["planes"]), _ptr(out["planes_bf16"]), _ptr(out["mask"]),
+                               _ptr(out["status"]), _stream(stream)))
+    return out
+
+
+def belief_sample(pos, K, seed, stream_ids=None, stream=None):
+    P = pos.shape[0]
+    types = torch.empty((P, K, 40), dtype=torch.uint8, device=pos.device)
+    status = torch.empty(P, dtype=torch.uint8, device=pos.device)
+    _check(lib().st_belief_sample(_ptr(pos, torch.uint8), P, int(K), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                  _ptr(stream_ids, torch.int32), _ptr(types), _ptr(status), _stream(stream)))
+    return types, status
+
+
+def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, flags=RULES_ALL, out=None,
+            stream=None):
+    P = pos.shape[0]
+    tallies = out if out is not None else torch.empty((P, 4), dtype=torch.int32, device=pos.device)
+    status = torch.empty(P, dtype=torch.uint8, device=pos.device)
+    r = make_rules(k, cap, flags)
+    _check(lib().st_rollout(_ptr(pos, torch.uint8), P, int(K), int(depth), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                            _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
+                            _ptr(tallies), _ptr(status), _stream(stream)))
+    return tallies, status

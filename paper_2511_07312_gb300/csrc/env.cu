@@ -1,0 +1,564 @@
+// env.cu -- the batched environment (App. B.1 StrategoRolloutBuffer as a
+// simulator): N independent game slots kept in HBM, stepped one ply per
+// launch (st_env_step, the plain path) or many plies per persistent launch
+// (st_env_run), with auto-reset, snapshots and per-slot counters.
+#include <cstring>
+#include <mutex>
+#include <vector>
+#include <algorithm>
+#include "engine.cuh"
+#include "snapshot.cuh"
+#include "host_common.h"
+
+using namespace stg;
+
+struct st_env {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int N = 0;
+    uint64_t seed = 0;
+    Rules rules{};
+    GameCore* core = nullptr;
+    uint16_t* ring = nullptr;
+    uint64_t* pi = nullptr;
+    uint32_t* stats = nullptr;
+    int32_t* status = nullptr;      // [0] latched st_status, [1] first slot (min)
+    int32_t* queue = nullptr;       // work counter of the persistent launch
+    int wpb = 4, bps = 0, gpf = 1;  // launch shape of st_env_run
+    int sms = 0;
+    int max_bps = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_key[10] = {0};
+};
+
+namespace stg {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+}  // namespace stg
+
+extern "C" const char* st_last_error(void) { return stg::g_err.c_str(); }
+extern "C" const char* st_version(void) { return "stratego-gb300 0.1 (sm_103a)"; }
+
+namespace {
+
+struct EnvArgs {
+    GameCore* core;
+    uint16_t* ring;
+    uint64_t* pi;
+    uint32_t* stats;
+    int32_t* status;
+    int N;
+    uint32_t k0, k1;
+    Rules R;
+};
+
+__device__ __forceinline__ void latch(int32_t* status, int code, int slot)
+{
+    atomicCAS(&status[0], 0, code);
+    atomicMin(&status[1], slot);
+}
+
+__device__ __forceinline__ void write_mask(const SmemGame* G, uint8_t* dst)
+{
+    const uint4* src = reinterpret_cast<const uint4*>(G->mask);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i = lane_id(); i < kMaskBytes / 16; i += 32) d[i] = src[i];
+}
+
+__device__ __forceinline__ bool setup_counts_ok(const uint8_t* s)
+{
+    int cnt[2][12];
+    for (int a = 0; a < 2; ++a)
+        for (int t = 0; t < 12; ++t) cnt[a][t] = 0;
+    for (int p = 0; p < 80; ++p) {
+        if (s[p] >= 12) return false;
+        cnt[p / 40][s[p]]++;
+    }
+    const int want[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+    for (int a = 0; a < 2; ++a)
+        for (int t = 0; t < 12; ++t)
+            if (cnt[a][t] != want[t]) return false;
+    return true;
+}
+
+// One ply of slot g (App. B.1): the mask of the player to move is in G->mask
+// with count n.  given: the supplied action or -1 for the random policy.
+__device__ PlyResult env_ply(SmemGame* G, int& n, const EnvArgs& A, uint32_t slot, int given, uint16_t* ring,
+                             uint64_t* pi, bool& illegal)
+{
+    PlyResult res;
+    res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = G->c.ply;
+    illegal = false;
+    if (G->c.terminated) return res;
+    if (n == 0) {
+        start_end(G, A.R, ring, pi, res.code, res.winner);
+    } else {
+        int a = given;
+        if (a >= 0) {
+            if (!mask_has(G, a)) { illegal = true; return res; }
+        } else {
+            const uint4 w = philox(make_uint4(slot, G->c.episode, (uint32_t)G->c.ply, 2u << 24), A.k0, A.k1);
+            a = select_action(G, uniform_below(w.x, (uint32_t)n));
+        }
+        apply_move(G, a, ring, pi);
+        res.action = a;
+        check_end(G, A.R, ring, pi, res.code, res.winner, n);
+    }
+    if (res.code) {
+        if (A.R.flags & kAutoreset) {
+            reset_game(G, A.k0, A.k1, slot, G->c.episode + 1, nullptr);
+            n = gen_moves(G, 0, A.R.flags, false, true, ring, pi);
+        } else {
+            if (lane_id() == 0) G->c.terminated = (uint8_t)res.code;
+            zero_mask(G);
+            n = 0;
+        }
+    }
+    return res;
+}
+
+__device__ __forceinline__ int reward_of(const PlyResult& r)
+{
+    if (r.code == 1 || r.code == 2) return r.winner == 0 ? 1 : -1;
+    return 0;
+}
+
+__device__ __forceinline__ void count_result(uint32_t* st, const PlyResult& r)
+{
+    if (r.action >= 0) st[5] += 1;
+    if (r.code) {
+        st[r.code - 1] += 1;
+        const int rw = reward_of(r);
+        if (rw > 0) st[6] += 1;
+        if (rw < 0) st[7] += 1;
+    }
+}
+
+__global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* which, int first)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= A.N) return;
+    if (which && !which[g]) return;
+    const uint8_t* setup = setups ? setups + 80 * (size_t)g : nullptr;
+    if (setup && !setup_counts_ok(setup)) {
+        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, g);
+        return;
+    }
+    uint32_t episode = 0;
+    if (!first) {
+        load_core(G, A.core + g);
+        episode = G->c.episode + 1;
+    }
+    if (first && lane_id() < 8) A.stats[8 * (size_t)g + lane_id()] = 0;
+    reset_game(G, A.k0, A.k1, (uint32_t)g, episode, setup);
+    const int n = gen_moves(G, 0, A.R.flags, false, false, A.ring + (size_t)g * kRing, A.pi + (size_t)g * kPiCap);
+    if (lane_id() == 0) G->c.n_legal = (uint16_t)n;
+    store_core(G, A.core + g);
+}
+
+__global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
+                           uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= A.N) return;
+    uint16_t* ring = A.ring + (size_t)g * kRing;
+    uint64_t* pi = A.pi + (size_t)g * kPiCap;
+    load_core(G, A.core + g);
+    build_board(G);
+    const int P = G->c.ply & 1;
+    int n = 0;
+    if (G->c.terminated) zero_mask(G);
+    else n = gen_moves(G, P, A.R.flags, false, true, ring, pi);
+    bool illegal = false;
+    const int given = actions ? (int)actions[g] : -1;
+    const PlyResult r = env_ply(G, n, A, (uint32_t)g, given, ring, pi, illegal);
+    if (lane_id() == 0) {
+        if (illegal) latch(A.status, ST_ERR_ILLEGAL_ACTION, g);
+        if (action_out) action_out[g] = (int16_t)r.action;
+        if (reward_out) reward_out[g] = (int8_t)reward_of(r);
+        if (done_out) done_out[g] = (uint8_t)r.code;
+        if (ply_out) ply_out[g] = (int16_t)r.ply_idx;
+        if (!illegal) {
+            uint32_t* st = A.stats + 8 * (size_t)g;
+            count_result(st, r);
+        }
+        G->c.n_legal = (uint16_t)n;
+    }
+    if (mask_out) write_mask(G, mask_out + (size_t)g * kMaskBytes);
+    if (!illegal) store_core(G, A.core + g);
+}
+
+// Persistent form: each warp claims `gpf` slots at a time from a global
+// counter and plays n_steps plies in each, keeping the game in shared memory.
+__global__ void k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf, int16_t* action_ring,
+                          int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const int lane = lane_id();
+    for (;;) {
+        int start = 0;
+        if (lane == 0) start = atomicAdd(queue, gpf);
+        start = __shfl_sync(0xFFFFFFFFu, start, 0);
+        if (start >= A.N) break;
+        const int end = min(start + gpf, A.N);
+        for (int g = start; g < end; ++g) {
+            uint16_t* ring = A.ring + (size_t)g * kRing;
+            uint64_t* pi = A.pi + (size_t)g * kPiCap;
+            load_core(G, A.core + g);
+            build_board(G);
+            int n = 0;
+            if (G->c.terminated) zero_mask(G);
+            else n = gen_moves(G, G->c.ply & 1, A.R.flags, false, true, ring, pi);
+            uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int j = 0; j < n_steps; ++j) {
+                bool illegal;
+                const PlyResult r = env_ply(G, n, A, (uint32_t)g, -1, ring, pi, illegal);
+                count_result(st, r);
+                const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
+                if (lane == 0) {
+                    if (action_ring) action_ring[o] = (int16_t)r.action;
+                    if (reward_ring) reward_ring[o] = (int8_t)reward_of(r);
+                    if (done_ring) done_ring[o] = (uint8_t)r.code;
+                    if (ply_ring) ply_ring[o] = (int16_t)r.ply_idx;
+                }
+                if (mask_ring) write_mask(G, mask_ring + o * kMaskBytes);
+            }
+            if (lane < 8) A.stats[8 * (size_t)g + lane] += st[lane];
+            if (lane == 0) G->c.n_legal = (uint16_t)n;
+            store_core(G, A.core + g);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- snapshots
+
+__global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int g = idx[i];
+    if (g < 0 || g >= A.N) {
+        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, i);
+        return;
+    }
+    load_core(G, A.core + g);
+    const uint16_t* ring = A.ring + (size_t)g * kRing;
+    st_position* o = out + i;
+    uint8_t* ob = reinterpret_cast<uint8_t*>(o);
+    const int lane = lane_id();
+    for (int b = lane; b < 240; b += 32) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
+    for (int h = lane; h < 256; h += 32) o->hist[h] = (uint16_t)hist_at(G, ring, h);
+    if (lane == 0) {
+        o->ply = G->c.ply;
+        o->battleless = G->c.battleless;
+        o->last_battle = G->c.last_battle;
+        o->chaser = G->c.chaser;
+        o->chase_plies = G->c.chase_plies;
+        o->reserved0 = 0;
+        for (int p = 0; p < 2; ++p) {
+            o->ts_pid[p] = G->c.ts_pid[p];
+            o->ts_len[p] = G->c.ts_len[p];
+            for (int k = 0; k < 4; ++k) o->ts_sq[p][k] = k < G->c.ts_len[p] ? G->c.ts_sq[p][k] : kNone;
+        }
+        for (int k = 0; k < 12; ++k) o->reserved1[k] = 0;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_position* in)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int g = idx[i];
+    if (g < 0 || g >= A.N) {
+        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, i);
+        return;
+    }
+    // keep the episode counter of the slot
+    const uint32_t episode = A.core[g].episode;
+    uint16_t* ring = A.ring + (size_t)g * kRing;
+    uint64_t* pi = A.pi + (size_t)g * kPiCap;
+    const int bad = import_position(G, in + i, ring, pi);
+    if (bad) {
+        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, g);
+        return;
+    }
+    const int nl = gen_moves(G, G->c.ply & 1, A.R.flags, false, false, ring, pi);
+    if (lane_id() == 0) {
+        G->c.episode = episode;
+        G->c.n_legal = (uint16_t)nl;
+    }
+    store_core(G, A.core + g);
+}
+
+EnvArgs env_args(st_env* e)
+{
+    EnvArgs a;
+    a.core = e->core; a.ring = e->ring; a.pi = e->pi; a.stats = e->stats; a.status = e->status;
+    a.N = e->N; a.k0 = (uint32_t)e->seed; a.k1 = (uint32_t)(e->seed >> 32); a.R = e->rules;
+    return a;
+}
+
+constexpr int kPlainWarps = 4;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~DeviceGuard() { int cur; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
+{
+    ST_CHECK_ARG(cfg && out, "st_env_create: null argument");
+    ST_CHECK_ARG(cfg->num_games >= 1 && cfg->num_games <= ST_MAX_GAMES, "st_env_create: num_games %d out of range",
+                 cfg->num_games);
+    ST_CHECK_ARG(rules_ok(&cfg->rules), "st_env_create: invalid rules");
+    ST_CHECK_ARG((cfg->env_flags & ~ST_AUTORESET) == 0, "st_env_create: unknown env_flags");
+    int ndev = 0;
+    ST_CUDA(cudaGetDeviceCount(&ndev));
+    ST_CHECK_ARG(cfg->device >= 0 && cfg->device < ndev, "st_env_create: device %d not present", cfg->device);
+    *out = nullptr;
+    DeviceGuard guard(cfg->device);
+    st_env* e = new st_env();
+    e->device = cfg->device;
+    e->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+    e->N = cfg->num_games;
+    e->seed = cfg->seed;
+    e->rules.k = cfg->rules.battleless_limit;
+    e->rules.cap = cfg->rules.max_plies;
+    e->rules.flags = cfg->rules.flags | (cfg->env_flags & ST_AUTORESET ? kAutoreset : 0u);
+    const size_t N = (size_t)e->N;
+    cudaError_t err = cudaSuccess;
+    err = cudaMalloc(&e->core, N * sizeof(GameCore));
+    if (err == cudaSuccess) err = cudaMalloc(&e->ring, N * kRing * sizeof(uint16_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->pi, N * kPiCap * sizeof(uint64_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->stats, N * 8 * sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->status, 2 * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->queue, sizeof(int32_t));
+    if (err != cudaSuccess) {
+        stg::set_error("st_env_create: device allocation failed: %s", cudaGetErrorString(err));
+        cudaGetLastError();
+        st_env_destroy(e);
+        return ST_ERR_OOM;
+    }
+    e->sms = sm_count();
+    const int32_t init_status[2] = {0, 0x7FFFFFFF};
+    err = cudaMemcpyAsync(e->status, init_status, sizeof(init_status), cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        stg::set_error("st_env_create: %s", cudaGetErrorString(err));
+        st_env_destroy(e);
+        return ST_ERR_CUDA;
+    }
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_reset<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, nullptr, nullptr, 1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        stg::set_error("st_env_create: reset launch failed: %s", cudaGetErrorString(err));
+        st_env_destroy(e);
+        return ST_ERR_CUDA;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_run, 32 * e->wpb, e->wpb * sizeof(SmemGame));
+    e->max_bps = occ;
+    *out = e;
+    return ST_OK;
+}
+
+extern "C" st_status st_env_destroy(st_env* e)
+{
+    if (!e) return ST_OK;
+    DeviceGuard guard(e->device);
+    cudaStreamSynchronize(e->stream);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    cudaFree(e->core); cudaFree(e->ring); cudaFree(e->pi); cudaFree(e->stats);
+    cudaFree(e->status); cudaFree(e->queue);
+    delete e;
+    return ST_OK;
+}
+
+extern "C" st_status st_env_reset(st_env* e, const uint8_t* setups, const uint8_t* which)
+{
+    ST_CHECK_ARG(e, "st_env_reset: null env");
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_reset<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, setups, which, 0);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
+                                 uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out)
+{
+    ST_CHECK_ARG(e, "st_env_step: null env");
+    ST_CHECK_ARG(!mask_out || aligned16(mask_out), "st_env_step: mask_out must be 16-byte aligned");
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_step<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
+        a, actions, action_out, reward_out, done_out, ply_out, mask_out);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32_t blocks_per_sm,
+                                       int32_t games_per_fetch)
+{
+    ST_CHECK_ARG(e, "st_env_set_launch: null env");
+    ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= 32, "st_env_set_launch: warps_per_block 1..32");
+    ST_CHECK_ARG(blocks_per_sm >= 0 && blocks_per_sm <= 64, "st_env_set_launch: blocks_per_sm 0..64");
+    ST_CHECK_ARG(games_per_fetch >= 1 && games_per_fetch <= 4096, "st_env_set_launch: games_per_fetch 1..4096");
+    DeviceGuard guard(e->device);
+    const int smem = warps_per_block * (int)sizeof(SmemGame);
+    if (smem > 48 * 1024)
+        ST_CUDA(cudaFuncSetAttribute(k_env_run, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int occ = 0;
+    ST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_run, 32 * warps_per_block, smem));
+    ST_CHECK_ARG(occ >= 1, "st_env_set_launch: %d warps per block do not fit on an SM", warps_per_block);
+    e->wpb = warps_per_block;
+    e->max_bps = occ;
+    e->bps = blocks_per_sm == 0 ? occ : std::min(blocks_per_sm, occ);
+    e->gpf = games_per_fetch;
+    if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+    return ST_OK;
+}
+
+extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
+                                int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+{
+    ST_CHECK_ARG(e, "st_env_run: null env");
+    ST_CHECK_ARG(n_steps >= 0, "st_env_run: n_steps < 0");
+    ST_CHECK_ARG(ring_steps >= 1, "st_env_run: ring_steps must be >= 1");
+    ST_CHECK_ARG(!mask_ring || aligned16(mask_ring), "st_env_run: mask_ring must be 16-byte aligned");
+    if (n_steps == 0) return ST_OK;
+    DeviceGuard guard(e->device);
+    const int bps = e->bps > 0 ? e->bps : std::max(1, e->max_bps);
+    const int64_t key[10] = {n_steps, ring_steps, (int64_t)action_ring, (int64_t)reward_ring, (int64_t)done_ring,
+                             (int64_t)ply_ring, (int64_t)mask_ring, e->wpb, bps, e->gpf};
+    const int blocks = std::max(1, std::min(e->sms * bps, (e->N + e->wpb - 1) / e->wpb));
+    EnvArgs a = env_args(e);
+    // A non-default stream gets the launch pair (queue reset + persistent
+    // kernel) captured once into a CUDA graph and replayed afterwards.
+    if (e->stream != nullptr) {
+        if (e->graph && std::memcmp(key, e->graph_key, sizeof(key)) == 0) {
+            ST_CUDA(cudaGraphLaunch(e->graph, e->stream));
+            return ST_OK;
+        }
+        if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+        cudaGraph_t graph = nullptr;
+        ST_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream);
+        k_env_run<<<blocks, 32 * e->wpb, e->wpb * sizeof(SmemGame), e->stream>>>(
+            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+        const cudaError_t launch_err = cudaGetLastError();
+        const cudaError_t cap_err = cudaStreamEndCapture(e->stream, &graph);
+        if (launch_err != cudaSuccess || cap_err != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            stg::set_error("st_env_run: capture failed: %s",
+                           cudaGetErrorString(launch_err != cudaSuccess ? launch_err : cap_err));
+            return ST_ERR_CUDA;
+        }
+        const cudaError_t inst_err = cudaGraphInstantiate(&e->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (inst_err != cudaSuccess) {
+            e->graph = nullptr;
+            stg::set_error("st_env_run: graph instantiate failed: %s", cudaGetErrorString(inst_err));
+            return ST_ERR_CUDA;
+        }
+        std::memcpy(e->graph_key, key, sizeof(key));
+        ST_CUDA(cudaGraphLaunch(e->graph, e->stream));
+        return ST_OK;
+    }
+    ST_CUDA(cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream));
+    k_env_run<<<blocks, 32 * e->wpb, e->wpb * sizeof(SmemGame), e->stream>>>(
+        a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_sync(st_env* e)
+{
+    ST_CHECK_ARG(e, "st_env_sync: null env");
+    DeviceGuard guard(e->device);
+    int32_t h[2];
+    ST_CUDA(cudaMemcpyAsync(h, e->status, sizeof(h), cudaMemcpyDeviceToHost, e->stream));
+    ST_CUDA(cudaStreamSynchronize(e->stream));
+    if (h[0] != 0) {
+        const int32_t init_status[2] = {0, 0x7FFFFFFF};
+        ST_CUDA(cudaMemcpyAsync(e->status, init_status, sizeof(init_status), cudaMemcpyHostToDevice, e->stream));
+        ST_CUDA(cudaStreamSynchronize(e->stream));
+        stg::set_error("device error latched: code %d, first index %d", h[0], h[1]);
+        return (st_status)h[0];
+    }
+    return ST_OK;
+}
+
+extern "C" st_status st_env_stats(st_env* e, uint32_t* stats_out)
+{
+    ST_CHECK_ARG(e && stats_out, "st_env_stats: null argument");
+    DeviceGuard guard(e->device);
+    ST_CUDA(cudaMemcpyAsync(stats_out, e->stats, (size_t)e->N * 8 * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                            e->stream));
+    return ST_OK;
+}
+
+extern "C" st_status st_env_export(st_env* e, const int32_t* idx, int32_t n, st_position* out)
+{
+    ST_CHECK_ARG(e && (n == 0 || (idx && out)), "st_env_export: null argument");
+    ST_CHECK_ARG(n >= 0, "st_env_export: n < 0");
+    if (n == 0) return ST_OK;
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (n + kPlainWarps - 1) / kPlainWarps;
+    k_env_export<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, idx, n, out);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_import(st_env* e, const int32_t* idx, int32_t n, const st_position* in)
+{
+    ST_CHECK_ARG(e && (n == 0 || (idx && in)), "st_env_import: null argument");
+    ST_CHECK_ARG(n >= 0, "st_env_import: n < 0");
+    if (n == 0) return ST_OK;
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (n + kPlainWarps - 1) / kPlainWarps;
+    k_env_import<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, idx, n, in);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}

@@ -1,0 +1,170 @@
+// features.cuh -- sticky per-piece history features of the information state
+// (App. C.1: threats, evasions, active adjacency, protection moves) and a
+// single-move legality test, for the replay kernels.
+//
+// Per piece two 64-bit words:
+//   A: bits 0-10 threatened (revealed rank Spy..Marshal, or bit 10 hidden),
+//      bits 11-21 evaded, bits 22-32 actively adjacent (same 11-bit layout);
+//      A's bit i is channel 43+i for own pieces and 76+i for opponent pieces.
+//   B: bits 0-51 in the order of channels 251-302 (own) / 303-354 (opponent):
+//      0-10 protected a revealed Spy..Marshal,Bomb, 11 an empty square,
+//      12 a hidden piece; 13-23 protected against a revealed type, 24 padding,
+//      25 against a hidden piece; 26-36 was protected by a revealed type, 37
+//      padding, 38 by a hidden piece; 39-49 was protected against a revealed
+//      type, 50 padding, 51 against a hidden piece.
+// Readings: a threat is a non-battle move ending next to enemy pieces; an
+// evasion moves a piece that stood next to where the opponent's previous
+// non-battle move ended to a square not next to it; active adjacency is an
+// adjacent attack that was legal but not played; a protection answers a
+// threat by moving another piece next to the threatened piece (or next to an
+// empty square next to the threatener) from a square not next to it.
+#pragma once
+#include "engine.cuh"
+
+namespace stg {
+
+struct __align__(16) FeatSmem {
+    uint64_t a[kPieces];
+    uint64_t b[kPieces];
+};
+
+// 0-9 revealed rank, 10 hidden, -1 none (a revealed Bomb or Flag)
+__device__ __forceinline__ int feat_rank_or_hidden(const SmemGame* G, int pid)
+{
+    if (!(G->c.flags[pid] & 2)) return 10;
+    const int t = G->c.type[pid];
+    return t <= kMarshal ? t : -1;
+}
+// 0-9 revealed rank, 10 revealed Bomb, `hidden` if hidden, -1 revealed Flag
+__device__ __forceinline__ int feat_type11(const SmemGame* G, int pid, int hidden)
+{
+    if (!(G->c.flags[pid] & 2)) return hidden;
+    const int t = G->c.type[pid];
+    return t <= kMarshal ? t : (t == kBomb ? 10 : -1);
+}
+__device__ __forceinline__ uint64_t fbit(int i) { return i >= 0 ? (1ull << i) : 0ull; }
+
+// Is action a legal for the player to move?  Warp-uniform.
+__device__ __forceinline__ bool move_legal(const SmemGame* G, int a, uint32_t rule_flags, const uint16_t* ring,
+                                           const uint64_t* pi)
+{
+    if (a < 0 || a >= 10000) return false;
+    const int P = G->c.ply & 1;
+    const int from = a / 100, to = a - 100 * (a / 100);
+    const uint8_t X = G->board[from];
+    if (X >= kPieces || (int)(X / 40) != P) return false;
+    const int t = G->c.type[X];
+    if (t >= kFlag) return false;
+    if (to == from || is_lake(to)) return false;
+    const uint8_t occ = G->board[to];
+    if (occ < kPieces && (int)(occ / 40) == P) return false;
+    const int fr = from / 10, fc = from - 10 * fr, tr = to / 10, tc = to - 10 * tr;
+    if (fr != tr && fc != tc) return false;
+    const int dist = abs(fr - tr) + abs(fc - tc);
+    if (dist > 1) {
+        if (t != kScout) return false;
+        const int step = fr == tr ? (tc > fc ? 1 : -1) : (tr > fr ? 10 : -10);
+        for (int q = from + step; q != to; q += step)
+            if (G->board[q] != kEmpty) return false;
+    }
+    if ((rule_flags & kTwoSquare) && G->c.ts_pid[P] == X && G->c.ts_len[P] == 4 && two_square_blocks(G, P, to))
+        return false;
+    if ((rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0 && occ == kEmpty) {
+        const PlyCtx x = make_ctx(G, ring);
+        if (chase_blocks(G, x, pi, P, X, from, to)) return false;
+    }
+    return true;
+}
+
+// Features that depend on the position before action a (active adjacency,
+// evasion, protection).  Call before apply_move.
+__device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, int a, uint32_t rule_flags,
+                                                const uint16_t* ring)
+{
+    const int lane = lane_id();
+    const int P = G->c.ply & 1;
+    const int from = a / 100, to = a - 100 * (a / 100);
+    const int X = G->board[from];
+    const bool battle = G->board[to] != kEmpty;
+    const bool ts_on = (rule_flags & kTwoSquare) && G->c.ts_pid[P] != kNone && G->c.ts_len[P] == 4;
+    // active adjacency: one lane per own piece
+    for (int j = lane; j < 40; j += 32) {
+        const int pid = P * 40 + j;
+        if (!(G->c.flags[pid] & 1) || G->c.type[pid] >= kFlag) continue;
+        const int s = G->c.sq[pid];
+        const int r = s / 10, c = s - 10 * r;
+        uint64_t bits = 0;
+        for (int dir = 0; dir < 4; ++dir) {
+            const int rr = r + (dir == 0) - (dir == 1), cc = c + (dir == 2) - (dir == 3);
+            if ((unsigned)rr > 9u || (unsigned)cc > 9u) continue;
+            const int n = rr * 10 + cc;
+            const uint8_t Z = G->board[n];
+            if (!enemy_of(Z, P)) continue;
+            if (s * 100 + n == a) continue;
+            if (ts_on && pid == G->c.ts_pid[P] && two_square_blocks(G, P, n)) continue;
+            bits |= fbit(feat_rank_or_hidden(G, Z)) << 22;
+        }
+        F->a[pid] |= bits;
+    }
+    __syncwarp();
+    if (lane == 0 && !battle) {
+        const PlyCtx x = make_ctx(G, ring);
+        const int ap = x.prev_to;
+        if (ap >= 0 && x.prev_nb && enemy_of(G->board[ap], P)) {
+            const int A = G->board[ap];
+            if (adjacent(from, ap) && !adjacent(to, ap))
+                F->a[X] |= fbit(feat_rank_or_hidden(G, A)) << 11;
+            const int ar = ap / 10, ac = ap - 10 * ar;
+            int nb[4], nn = 0;
+            if (ar > 0 && !is_lake(ap - 10)) nb[nn++] = ap - 10;
+            if (ar < 9 && !is_lake(ap + 10)) nb[nn++] = ap + 10;
+            if (ac > 0 && !is_lake(ap - 1)) nb[nn++] = ap - 1;
+            if (ac < 9 && !is_lake(ap + 1)) nb[nn++] = ap + 1;
+            bool threatened = false;
+            for (int i = 0; i < nn; ++i) {
+                const uint8_t q = G->board[nb[i]];
+                threatened |= q < kPieces && (int)(q / 40) == P;
+            }
+            if (threatened) {
+                const int a_idx = feat_type11(G, A, 11);
+                for (int i = 0; i < nn; ++i) {
+                    const int s = nb[i];
+                    const uint8_t B = G->board[s];
+                    if (B < kPieces && ((int)(B / 40) != P || B == X)) continue;
+                    if (!(adjacent(to, s) && !adjacent(from, s))) continue;
+                    uint64_t bx = B == kEmpty ? fbit(11) : fbit(feat_type11(G, B, 12));
+                    if (a_idx >= 0) bx |= fbit(a_idx == 11 ? 25 : 13 + a_idx);
+                    F->b[X] |= bx;
+                    if (B < kPieces) {
+                        const int c_idx = feat_type11(G, X, 11);
+                        uint64_t bb = 0;
+                        if (c_idx >= 0) bb |= fbit(c_idx == 11 ? 38 : 26 + c_idx);
+                        if (a_idx >= 0) bb |= fbit(a_idx == 11 ? 51 : 39 + a_idx);
+                        F->b[B] |= bb;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Threats made by the move just applied (a = from*100+to); call after apply_move.
+__device__ __forceinline__ void features_after(const SmemGame* G, FeatSmem* F, int a, bool battle)
+{
+    if (lane_id() == 0 && !battle) {
+        const int to = a - 100 * (a / 100);
+        const int X = G->board[to];
+        const int P = X / 40;
+        const int r = to / 10, c = to - 10 * r;
+        uint64_t bits = 0;
+        if (r > 0 && enemy_of(G->board[to - 10], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to - 10]));
+        if (r < 9 && enemy_of(G->board[to + 10], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to + 10]));
+        if (c > 0 && enemy_of(G->board[to - 1], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to - 1]));
+        if (c < 9 && enemy_of(G->board[to + 1], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to + 1]));
+        F->a[X] |= bits;
+    }
+    __syncwarp();
+}
+
+}  // namespace stg

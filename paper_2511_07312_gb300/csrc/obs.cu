@@ -1,0 +1,445 @@
+// obs.cu -- replay of action logs into positions and the information-state
+// planes of App. C (st_replay_positions, st_obs_encode).
+//
+// Two kernels.  k_replay: one warp per chunk of consecutive items replays
+// each item's log in shared memory (with full legality checks and the
+// history features), continuing from the previous item of the chunk when it
+// is the same game at a later ply, so items sorted by (game, ply) walk each
+// log once per chunk (App. B.1: compact records, states reconstructed on
+// demand).  It writes the replayed state of every item to a scratch record
+// (or an st_position), plus the legal mask.  k_obs_emit: one warp per item
+// turns the record into the 487 planes, four squares of one channel per lane
+// per store (32-bit uint8 stores and 64-bit bf16 stores, coalesced across the
+// warp).
+#include "engine.cuh"
+#include "features.cuh"
+#include "host_common.h"
+
+using namespace stg;
+
+namespace {
+
+constexpr int kReplayWarps = 4;
+constexpr int kEmitWarps = 4;
+constexpr int kPlaneBytes = ST_NCHAN * 100;        // 48,700
+constexpr int kGroups = ST_NCHAN * 25;             // 4 squares per group
+
+// Replayed state of one item, as the emission kernel needs it.
+struct __align__(16) ItemState {
+    GameCore c;
+    uint16_t hist[32];
+    uint64_t fa[kPieces];
+    uint64_t fb[kPieces];
+};
+static_assert(sizeof(ItemState) == 288 + 64 + 1280, "ItemState layout");
+
+struct __align__(16) ReplaySmem {
+    SmemGame g;
+    FeatSmem f;
+    uint64_t pi[kPiCap];
+    uint16_t ring[kRing];
+};
+
+struct ReplayArgs {
+    const uint8_t* setups;
+    const int16_t* actions;
+    int log_len;
+    int num_logs;
+    const int32_t* game;
+    const int16_t* ply;
+    int B;
+    Rules R;
+    int items_per_warp;
+    ItemState* state_out;    // obs mode
+    st_position* pos_out;    // position mode
+    uint8_t* mask_out;
+    uint8_t* status;
+};
+
+__device__ bool setup_ok(const uint8_t* s)
+{
+    int cnt[24];
+    for (int i = 0; i < 24; ++i) cnt[i] = 0;
+    for (int p = 0; p < 80; ++p) {
+        if (s[p] >= 12) return false;
+        cnt[(p / 40) * 12 + s[p]]++;
+    }
+    const int want[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+    for (int i = 0; i < 24; ++i)
+        if (cnt[i] != want[i % 12]) return false;
+    return true;
+}
+
+__device__ void write_position(const SmemGame* G, const uint16_t* ring, st_position* o)
+{
+    const int lane = lane_id();
+    uint8_t* ob = reinterpret_cast<uint8_t*>(o);
+    for (int b = lane; b < 240; b += 32) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
+    for (int h = lane; h < 256; h += 32) o->hist[h] = (uint16_t)hist_at(G, ring, h);
+    if (lane == 0) {
+        o->ply = G->c.ply;
+        o->battleless = G->c.battleless;
+        o->last_battle = G->c.last_battle;
+        o->chaser = G->c.chaser;
+        o->chase_plies = G->c.chase_plies;
+        o->reserved0 = 0;
+        for (int p = 0; p < 2; ++p) {
+            o->ts_pid[p] = G->c.ts_pid[p];
+            o->ts_len[p] = G->c.ts_len[p];
+            for (int k = 0; k < 4; ++k) o->ts_sq[p][k] = k < G->c.ts_len[p] ? G->c.ts_sq[p][k] : kNone;
+        }
+        for (int k = 0; k < 12; ++k) o->reserved1[k] = 0;
+    }
+}
+
+__device__ void zero_bytes(uint8_t* dst, int n)
+{
+    for (int i = lane_id(); i < n; i += 32) dst[i] = 0;
+}
+
+__global__ void k_replay(ReplayArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ReplaySmem* S = reinterpret_cast<ReplaySmem*>(smem) + (threadIdx.x >> 5);
+    SmemGame* G = &S->g;
+    const int lane = lane_id();
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int i0 = warp * A.items_per_warp;
+    const int i1 = min(A.B, i0 + A.items_per_warp);
+    const bool track = A.state_out != nullptr;
+    int cur_game = -1, cur_ply = 0;
+    bool valid = false;
+    for (int i = i0; i < i1; ++i) {
+        const int gi = A.game[i];
+        const int p = A.ply[i];
+        bool ok = gi >= 0 && gi < A.num_logs && p >= 0 && p <= A.log_len;
+        if (ok && !(valid && gi == cur_game && p >= cur_ply)) {
+            const uint8_t* setup = A.setups + 80 * (size_t)gi;
+            ok = setup_ok(setup);
+            if (ok) {
+                reset_game(G, 0, 0, 0, 0, setup);
+                for (int k = lane; k < kPieces; k += 32) { S->f.a[k] = 0; S->f.b[k] = 0; }
+                __syncwarp();
+                cur_game = gi;
+                cur_ply = 0;
+                valid = true;
+            } else {
+                valid = false;
+            }
+        }
+        if (ok) {
+            const int16_t* log = A.actions + (size_t)A.log_len * (size_t)gi;
+            while (cur_ply < p) {
+                // an intermediate position must not have ended the game
+                if (cur_ply > 0 && (flag_dead(G, G->c.ply & 1) || G->c.battleless >= A.R.k ||
+                                    G->c.ply >= A.R.cap)) { ok = false; break; }
+                const int a = log[cur_ply];
+                if (!move_legal(G, a, A.R.flags, S->ring, S->pi)) { ok = false; break; }
+                const bool battle = G->board[a - 100 * (a / 100)] != kEmpty;
+                if (track) features_before(G, &S->f, a, A.R.flags, S->ring);
+                apply_move(G, a, S->ring, S->pi);
+                if (track) features_after(G, &S->f, a, battle);
+                ++cur_ply;
+            }
+            if (!ok) valid = false;
+        }
+        if (lane == 0 && A.status) A.status[i] = ok ? 0 : 1;
+        if (!ok) {
+            if (A.pos_out) zero_bytes(reinterpret_cast<uint8_t*>(A.pos_out + i), sizeof(st_position));
+            if (A.state_out) zero_bytes(reinterpret_cast<uint8_t*>(A.state_out + i), sizeof(ItemState));
+            if (A.mask_out) zero_bytes(A.mask_out + (size_t)i * kMaskBytes, kMaskBytes);
+            continue;
+        }
+        if (A.pos_out) write_position(G, S->ring, A.pos_out + i);
+        if (A.state_out) {
+            ItemState* o = A.state_out + i;
+            if (lane < 18) reinterpret_cast<uint4*>(&o->c)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
+            o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
+            for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
+        }
+        if (A.mask_out) {
+            gen_moves(G, G->c.ply & 1, A.R.flags, false, true, S->ring, S->pi);
+            const uint4* src = reinterpret_cast<const uint4*>(G->mask);
+            uint4* d = reinterpret_cast<uint4*>(A.mask_out + (size_t)i * kMaskBytes);
+            for (int k = lane; k < kMaskBytes / 16; k += 32) d[k] = src[k];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- emission
+
+struct __align__(16) EmitSmem {
+    ItemState s;
+    uint8_t board[112];
+    uint64_t death[2][100];          // bit 10*(cause-1)+rank per side and square
+    uint32_t ratio[2][2][12];        // side x {unmoved, moved} x type: u8 | bf16<<8
+    uint32_t frac41, frac42;
+};
+
+struct EmitArgs {
+    const ItemState* items;
+    const uint8_t* status;
+    const int8_t* player;
+    int B;
+    Rules R;
+    uint8_t* planes;
+    uint16_t* planes_bf16;
+};
+
+constexpr uint32_t kOne = 1u | (0x3F80u << 8);
+constexpr uint32_t kMinus = 255u | (0xBF80u << 8);
+constexpr uint32_t kRatioOne = 255u | (0x3F80u << 8);
+
+// u8 floor(255*num/den + 1/2) | bf16 bits of num/den << 8 (IEEE fp32 division
+// then round-to-nearest-even; exact for den <= 1600).
+__device__ __forceinline__ uint32_t ratio_code(uint32_t num, uint32_t den)
+{
+    if (num == 0) return 0u;
+    const uint32_t u8 = (510u * num + den) / (2u * den);
+    const float q = __fdiv_rn((float)num, (float)den);
+    uint32_t bits = __float_as_uint(q);
+    bits += 0x7FFFu + ((bits >> 16) & 1u);
+    return u8 | ((bits >> 16) << 8);
+}
+
+__device__ __forceinline__ uint32_t cell(const EmitSmem* E, int ch, int s, int me)
+{
+    const ItemState& st = E->s;
+    const uint8_t occ = E->board[s];
+    const bool piece = occ < kPieces;
+    const int side = piece ? occ / 40 : -1;
+    const bool mine = side == me;
+    const uint8_t f = piece ? st.c.flags[occ] : 0;
+    if (ch < 12) return (piece && mine && st.c.type[occ] == ch) ? kOne : 0u;
+    if (ch < 36) {
+        const int T = ch < 24 ? ch - 12 : ch - 24;
+        const int want = ch < 24 ? 1 - me : me;
+        if (!piece || side != want) return 0u;
+        if (f & 2) return st.c.type[occ] == T ? kRatioOne : 0u;
+        if (f & 8) return T == kScout ? kRatioOne : 0u;
+        return E->ratio[side][(f & 4) ? 1 : 0][T];
+    }
+    if (ch < 43) {
+        switch (ch) {
+            case 36: return (piece && mine && !(f & 2)) ? kOne : 0u;
+            case 37: return (piece && !mine && !(f & 2)) ? kOne : 0u;
+            case 38: return occ == kEmpty ? kOne : 0u;
+            case 39: return (piece && mine && (f & 4)) ? kOne : 0u;
+            case 40: return (piece && !mine && (f & 4)) ? kOne : 0u;
+            case 41: return E->frac41;
+            default: return E->frac42;
+        }
+    }
+    if (ch < 109) {
+        const bool want_mine = ch < 76;
+        if (!piece || mine != want_mine) return 0u;
+        return ((st.fa[occ] >> (ch - (want_mine ? 43 : 76))) & 1ull) ? kOne : 0u;
+    }
+    if (ch < 131) {
+        const bool want_mine = ch < 120;
+        const int ti = ch - (want_mine ? 109 : 120);
+        const int pid = s < 40 ? s : (s >= 60 ? s - 20 : -1);
+        if (pid < 0 || ((pid / 40) == me) != want_mine) return 0u;
+        if (st.c.flags[pid] & 1) return 0u;
+        const int t = st.c.type[pid];
+        const int idx = t <= kMarshal ? t : (t == kBomb ? 10 : -1);
+        return idx == ti ? kOne : 0u;
+    }
+    if (ch < 251) {
+        const bool want_mine = ch < 191;
+        const int bit = ch - (want_mine ? 131 : 191);
+        const int want_side = want_mine ? me : 1 - me;
+        return ((E->death[want_side][s] >> bit) & 1ull) ? kOne : 0u;
+    }
+    if (ch < 355) {
+        const bool want_mine = ch < 303;
+        if (!piece || mine != want_mine) return 0u;
+        return ((st.fb[occ] >> (ch - (want_mine ? 251 : 303))) & 1ull) ? kOne : 0u;
+    }
+    if (ch < 455) return (piece && start_square(occ) == ch - 355) ? kOne : 0u;
+    const int j = ch - 455;
+    const int h = st.hist[j];
+    if (h == 0xFFFF) return 0u;
+    if (s == h % 100) return kOne;
+    if (s == h / 100) return kMinus;
+    return 0u;
+}
+
+__global__ void k_obs_emit(EmitArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    EmitSmem* E = reinterpret_cast<EmitSmem*>(smem) + (threadIdx.x >> 5);
+    const int lane = lane_id();
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= A.B) return;
+    uint8_t* u8 = A.planes ? A.planes + (size_t)b * kPlaneBytes : nullptr;
+    uint16_t* bf = A.planes_bf16 ? A.planes_bf16 + (size_t)b * kPlaneBytes : nullptr;
+    if (A.status && A.status[b]) {
+        for (int g = lane; g < kGroups; g += 32) {
+            if (u8) reinterpret_cast<uint32_t*>(u8)[g] = 0u;
+            if (bf) reinterpret_cast<uint2*>(bf)[g] = make_uint2(0u, 0u);
+        }
+        return;
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(A.items + b);
+        uint4* dst = reinterpret_cast<uint4*>(&E->s);
+        for (int k = lane; k < (int)(sizeof(ItemState) / 16); k += 32) dst[k] = src[k];
+    }
+    for (int s = lane; s < 100; s += 32) { E->death[0][s] = 0; E->death[1][s] = 0; }
+    __syncwarp();
+    for (int s = lane; s < 112; s += 32) E->board[s] = (s < 100 && is_lake(s)) ? kLake : kEmpty;
+    __syncwarp();
+    for (int p = lane; p < kPieces; p += 32) {
+        const uint8_t f = E->s.c.flags[p];
+        if (f & 1) {
+            E->board[E->s.c.sq[p]] = (uint8_t)p;
+        } else {
+            const int cause = f >> 4, t = E->s.c.type[p];
+            if (cause >= 1 && t <= kMarshal)
+                atomicOr(reinterpret_cast<unsigned long long*>(&E->death[p / 40][E->s.c.sq[p]]),
+                         1ull << (10 * (cause - 1) + t));
+        }
+    }
+    // remaining counts per side (lanes 0 and 1), then the probability table
+    if (lane < 2) {
+        const int side = lane;
+        int c[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+        int nS = 0, nM = 0, nU = 0;
+        for (int k = 0; k < 40; ++k) {
+            const int p = side * 40 + k;
+            const uint8_t f = E->s.c.flags[p];
+            if (!(f & 1) || (f & 2)) { c[E->s.c.type[p]]--; continue; }
+            if (f & 8) nS++;
+            else if (f & 4) nM++;
+            else nU++;
+        }
+        c[kScout] -= nS;
+        const int bimm = c[kFlag] + c[kBomb];
+        int m = 0;
+        for (int t = 0; t <= kMarshal; ++t) m += c[t];
+        for (int t = 0; t < 12; ++t) {
+            uint32_t unm = 0, mov = 0;
+            if (t == kFlag || t == kBomb) {
+                if (nU > 0) unm = ratio_code((uint32_t)c[t], (uint32_t)nU);
+            } else {
+                if (m > 0) mov = ratio_code((uint32_t)c[t], (uint32_t)m);
+                if (nU > 0 && m > 0) unm = ratio_code((uint32_t)((nU - bimm) * c[t]), (uint32_t)(nU * m));
+            }
+            E->ratio[side][0][t] = unm;
+            E->ratio[side][1][t] = mov;
+        }
+    }
+    if (lane == 2) {
+        E->frac41 = ratio_code((uint32_t)E->s.c.ply, (uint32_t)A.R.cap);
+        E->frac42 = ratio_code((uint32_t)E->s.c.battleless, (uint32_t)A.R.k);
+    }
+    __syncwarp();
+    const int me = (A.player && A.player[b] >= 0) ? (A.player[b] & 1) : (E->s.c.ply & 1);
+    for (int g = lane; g < kGroups; g += 32) {
+        const int ch = g / 25;
+        const int s0 = (g - 25 * ch) * 4;
+        const uint32_t c0 = cell(E, ch, s0, me), c1 = cell(E, ch, s0 + 1, me);
+        const uint32_t c2 = cell(E, ch, s0 + 2, me), c3 = cell(E, ch, s0 + 3, me);
+        if (u8)
+            reinterpret_cast<uint32_t*>(u8)[g] = (c0 & 0xFFu) | ((c1 & 0xFFu) << 8) | ((c2 & 0xFFu) << 16) |
+                                                 ((c3 & 0xFFu) << 24);
+        if (bf)
+            reinterpret_cast<uint2*>(bf)[g] = make_uint2((c0 >> 8) | ((c1 >> 8) << 16), (c2 >> 8) | ((c3 >> 8) << 16));
+    }
+}
+
+ReplayArgs replay_args(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
+                       const int32_t* game, const int16_t* ply, int32_t B, const st_rules* rules)
+{
+    ReplayArgs a{};
+    a.setups = setups; a.actions = actions; a.log_len = log_len; a.num_logs = num_logs;
+    a.game = game; a.ply = ply; a.B = B;
+    a.R.k = rules->battleless_limit; a.R.cap = rules->max_plies; a.R.flags = rules->flags;
+    a.items_per_warp = 4;
+    return a;
+}
+
+int g_items_per_warp = 4;
+
+}  // namespace
+
+extern "C" st_status st_replay_set_chunk(int32_t items_per_warp)
+{
+    ST_CHECK_ARG(items_per_warp >= 1 && items_per_warp <= 65536, "st_replay_set_chunk: 1..65536");
+    g_items_per_warp = items_per_warp;
+    return ST_OK;
+}
+
+extern "C" st_status st_replay_positions(const uint8_t* setups, const int16_t* actions, int32_t log_len,
+                                         int32_t num_logs, const int32_t* game, const int16_t* ply, int32_t B,
+                                         const st_rules* rules, st_position* out, uint8_t* item_status,
+                                         void* stream)
+{
+    ST_CHECK_ARG(rules_ok(rules), "st_replay_positions: invalid rules");
+    ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_replay_positions: negative size");
+    if (B == 0) return ST_OK;
+    ST_CHECK_ARG(setups && actions && game && ply && out, "st_replay_positions: null argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
+    a.items_per_warp = g_items_per_warp;
+    a.pos_out = out;
+    a.status = item_status;
+    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
+    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
+    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
+                                   const int32_t* game, const int16_t* ply, const int8_t* player, int32_t B,
+                                   const st_rules* rules, uint8_t* planes, uint16_t* planes_bf16, uint8_t* mask,
+                                   uint8_t* item_status, void* stream)
+{
+    ST_CHECK_ARG(rules_ok(rules), "st_obs_encode: invalid rules");
+    ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_obs_encode: negative size");
+    if (B == 0) return ST_OK;
+    ST_CHECK_ARG(setups && actions && game && ply, "st_obs_encode: null argument");
+    ST_CHECK_ARG(!planes || ((uintptr_t)planes & 3u) == 0, "st_obs_encode: planes must be 4-byte aligned");
+    ST_CHECK_ARG(!planes_bf16 || ((uintptr_t)planes_bf16 & 7u) == 0, "st_obs_encode: planes_bf16 must be 8-byte aligned");
+    ST_CHECK_ARG(!mask || aligned16(mask), "st_obs_encode: mask must be 16-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool need_planes = planes || planes_bf16;
+    ItemState* scratch = nullptr;
+    uint8_t* status = item_status;
+    uint8_t* own_status = nullptr;
+    if (need_planes) {
+        ST_CUDA(cudaMallocAsync(&scratch, (size_t)B * sizeof(ItemState), s));
+        if (!status) {
+            ST_CUDA(cudaMallocAsync(&own_status, (size_t)B, s));
+            status = own_status;
+        }
+    }
+    ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
+    a.items_per_warp = g_items_per_warp;
+    a.state_out = scratch;
+    a.mask_out = mask;
+    a.status = status;
+    if (!need_planes && !mask && !status) return ST_OK;
+    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
+    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
+    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && need_planes) {
+        EmitArgs e{};
+        e.items = scratch; e.status = status; e.player = player; e.B = B; e.R = a.R;
+        e.planes = planes; e.planes_bf16 = planes_bf16;
+        const int eblocks = (B + kEmitWarps - 1) / kEmitWarps;
+        k_obs_emit<<<eblocks, 32 * kEmitWarps, kEmitWarps * sizeof(EmitSmem), s>>>(e);
+        err = cudaGetLastError();
+    }
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (own_status) cudaFreeAsync(own_status, s);
+    if (err != cudaSuccess) {
+        stg::set_error("st_obs_encode: launch failed: %s", cudaGetErrorString(err));
+        return ST_ERR_CUDA;
+    }
+    return ST_OK;
+}

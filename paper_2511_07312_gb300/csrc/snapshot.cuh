@@ -1,0 +1,112 @@
+// snapshot.cuh -- device-side reading of st_position snapshots (App. B.4:
+// games reset to non-initial states), shared by the env import and the
+// search kernels.
+#pragma once
+#include "engine.cuh"
+#include "stratego.h"
+
+namespace stg {
+
+// Shared by the env and the stateless search kernels: read and validate a
+// snapshot into G (board built, hash and chase positions rebuilt), writing
+// the history ring and chase store.  Returns 0 when valid.
+static __device__ __noinline__ int import_position(SmemGame* G, const st_position* in, uint16_t* ring, uint64_t* pi)
+{
+    const int lane = lane_id();
+    const uint8_t* ib = reinterpret_cast<const uint8_t*>(in);
+    for (int b = lane; b < 240; b += 32) reinterpret_cast<uint8_t*>(&G->c)[b] = ib[b];
+    __syncwarp();
+    int bad = 0;
+    if (lane == 0) {
+        GameCore& c = G->c;
+        int cnt[2][12];
+        for (int a = 0; a < 2; ++a)
+            for (int t = 0; t < 12; ++t) cnt[a][t] = 0;
+        for (int p = 0; p < 80 && !bad; ++p) {
+            if (c.type[p] >= 12) { bad = 1; break; }
+            cnt[p / 40][c.type[p]]++;
+            if (c.sq[p] >= 100 || is_lake(c.sq[p])) bad = 2;
+            if ((c.flags[p] & 1) && (c.flags[p] >> 4)) bad = 3;
+        }
+        const int want[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+        for (int a = 0; a < 2 && !bad; ++a)
+            for (int t = 0; t < 12; ++t)
+                if (cnt[a][t] != want[t]) bad = 4;
+        c.ply = in->ply;
+        c.battleless = in->battleless;
+        if (!bad && (c.ply < 0 || c.battleless < 0 || c.battleless > c.ply)) bad = 6;
+        c.last_battle = in->last_battle ? 1 : 0;
+        c.chaser = in->chaser;
+        c.chase_plies = in->chase_plies;
+        if (!bad && c.chaser != kNone && c.chaser > 1) bad = 7;
+        for (int p = 0; p < 2; ++p) {
+            c.ts_pid[p] = in->ts_pid[p];
+            c.ts_len[p] = in->ts_len[p];
+            for (int k = 0; k < 4; ++k) c.ts_sq[p][k] = in->ts_sq[p][k];
+            if (!bad && c.ts_pid[p] != kNone && (c.ts_pid[p] >= 80 || c.ts_len[p] < 2 || c.ts_len[p] > 4)) bad = 8;
+            if (!bad && c.ts_pid[p] == kNone && c.ts_len[p] != 0) bad = 8;
+            for (int k = 0; k < c.ts_len[p] && k < 4 && !bad; ++k)
+                if (c.ts_sq[p][k] >= 100 || is_lake(c.ts_sq[p][k])) bad = 8;
+        }
+        if (!bad && c.chaser == kNone && c.chase_plies != 0) bad = 13;
+        if (!bad && c.chaser != kNone && c.chase_plies < 1) bad = 9;
+        c.terminated = 0;
+        c.n_pi = 0;
+    }
+    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
+    if (bad) return bad;
+    // board, checking that no two alive pieces share a square
+    for (int s = lane; s < 112; s += 32) G->board[s] = (s < 100 && is_lake(s)) ? kLake : kEmpty;
+    __syncwarp();
+    if (lane == 0) {
+        for (int p = 0; p < 80 && !bad; ++p) {
+            if (!(G->c.flags[p] & 1)) continue;
+            if (G->board[G->c.sq[p]] != kEmpty) bad = 5;
+            else G->board[G->c.sq[p]] = (uint8_t)p;
+        }
+    }
+    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
+    if (bad) return bad;
+    const int ply = G->c.ply;
+    for (int h = lane; h < kRing; h += 32)
+        if (h < ply) ring[(ply - 1 - h) & (kRing - 1)] = in->hist[h];
+    const uint64_t hash = board_hash(G);
+    __syncwarp();
+    if (lane == 0) {
+        G->c.hash = hash;
+        // chase positions: undo the chase plies from the current board,
+        // hashing the position after each of the chaser's plies
+        if (G->c.chaser != kNone) {
+            uint8_t b[100];
+            for (int s = 0; s < 100; ++s) b[s] = G->board[s];
+            uint64_t h = hash;
+            uint64_t tmp[kPiCap];
+            int nt = 0;
+            for (int i = 0; i < G->c.chase_plies && !bad; ++i) {
+                const int mover = (ply - 1 - i) & 1;
+                const int a = in->hist[i];
+                if (a == 0xFFFF) { bad = 10; break; }
+                if (mover == G->c.chaser) {
+                    if (nt >= kPiCap) { bad = 11; break; }
+                    tmp[nt++] = h;
+                }
+                const int f = a / 100, t = a % 100;
+                if (f >= 100 || b[t] >= kPieces || b[f] != kEmpty || is_lake(f)) { bad = 12; break; }
+                const int p = b[t];
+                b[f] = (uint8_t)p;
+                b[t] = kEmpty;
+                h ^= zkey(p, t) ^ zkey(p, f);
+            }
+            if (!bad) {
+                for (int i = 0; i < nt; ++i) pi[i] = tmp[nt - 1 - i];
+                G->c.n_pi = (uint8_t)nt;
+            }
+        }
+    }
+    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
+    __syncwarp();
+    return bad;
+}
+
+
+}  // namespace stg

@@ -1,0 +1,171 @@
+"""GPU parity of the environment kernels (plain per-ply launch and the
+persistent launch) with the oracle, bit for bit, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2511_07312_gb300 as st  # noqa: E402
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _plain_steps(env, n_steps):
+    outs = {k: [] for k in ("action", "reward", "done", "ply", "mask")}
+    for _ in range(n_steps):
+        o = env.step()
+        for k in outs:
+            outs[k].append(o[k].clone())
+    env.stream.synchronize()
+    return {k: torch.stack(v).cpu().numpy() for k, v in outs.items()}
+
+
+def _compare(gpu, ref, slots=None, steps=None):
+    for k in ("action", "reward", "done", "ply"):
+        g = gpu[k] if slots is None else gpu[k][:, slots]
+        r = ref[k]
+        if steps is not None:
+            g, r = g[steps], r[steps]
+        mism = np.argwhere(g != r)
+        assert mism.size == 0, "%s differs first at (step, slot) %s: gpu %s oracle %s" % (
+            k, mism[0], g[tuple(mism[0])], r[tuple(mism[0])])
+    if gpu.get("mask") is not None and ref.get("mask") is not None:
+        g = gpu["mask"] if slots is None else gpu["mask"][:, slots]
+        r = ref["mask"]
+        if steps is not None:
+            g, r = g[steps], r[steps]
+        mism = np.argwhere((g != r).any(-1))
+        assert mism.size == 0, "mask differs first at (step, slot) %s" % (mism[0],)
+
+
+def test_plain_step_config1_bit_exact():
+    # 64 games, seed 1, to the end or the 1000-ply cap, auto-reset afterwards
+    env = st.Env(64, seed=1)
+    gpu = _plain_steps(env, 1000)
+    ref = oracle.env_run(1, 64, 1000)
+    _compare(gpu, ref)
+    stats = _np(env.stats())
+    np.testing.assert_array_equal(stats, ref["stats"].astype(np.int32))
+
+
+def test_persistent_run_matches_plain_and_oracle():
+    env = st.Env(64, seed=1)
+    out = env.run(1000)
+    env.stream.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = oracle.env_run(1, 64, 1000)
+    _compare(gpu, ref)
+
+
+@pytest.mark.parametrize("wpb,gpf", [(1, 1), (4, 3), (8, 1), (16, 7)])
+def test_persistent_launch_shapes_ragged(wpb, gpf):
+    # 1,000 slots (not a multiple of any block), 300 plies, ring of 7 rows
+    N, S, R = 1000, 300, 7
+    env = st.Env(N, seed=5)
+    env.set_launch(wpb, 0, gpf)
+    out = env.run(S, R)
+    env.stream.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in out.items()}
+    slots = np.array([0, 1, 2, 499, 500, 998, 999] + list(range(37, N, 97)))
+    # oracle per sampled slot (slots are independent)
+    rows = [(S - R + i) for i in range(R)]
+    for s in slots:
+        r = oracle.env_run(5, 1, S, slot0=int(s))
+        for j, row in enumerate(rows):
+            ring_row = row % R
+            for k in ("action", "reward", "done", "ply"):
+                assert gpu[k][ring_row, s] == r[k][row, 0], (k, s, row)
+            assert np.array_equal(gpu["mask"][ring_row, s], r["mask"][row, 0]), ("mask", s, row)
+    stats = _np(env.stats())
+    for s in slots:
+        r = oracle.env_run(5, 1, S, slot0=int(s), want_mask=False)
+        np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
+
+
+def test_supplied_actions_and_illegal_action_latch():
+    env = st.Env(16, seed=3)
+    ref = oracle.env_run(3, 16, 40)
+    acts = torch.from_numpy(ref["action"]).cuda()
+    outs = []
+    for t in range(40):
+        outs.append({k: v.clone() for k, v in env.step(acts[t].contiguous()).items()})
+    env.sync()
+    gpu = {k: torch.stack([o[k] for o in outs]).cpu().numpy() for k in outs[0]}
+    _compare(gpu, ref)
+    # an illegal action leaves that slot unchanged and is latched
+    before = env.export(torch.arange(16))
+    bad = torch.full((16,), -1, dtype=torch.int16, device="cuda")
+    bad[5] = 0
+    o = env.step(bad)
+    with pytest.raises(st.StrategoError) as ei:
+        env.sync()
+    assert ei.value.code == 4
+    after = env.export(torch.arange(16))
+    torch.cuda.synchronize()
+    assert torch.equal(before[5], after[5])
+    assert int(o["action"][5]) == -1
+    env.sync()   # the latch was cleared
+
+
+def test_export_matches_oracle_snapshots_and_import_roundtrip():
+    N, S = 48, 257
+    env = st.Env(N, seed=9)
+    env.run(S, 1, want=())
+    pos = env.export(torch.arange(N))
+    env.sync()
+    ref = oracle.env_run(9, N, S, want_mask=False, want_final=True)
+    np.testing.assert_array_equal(pos.cpu().numpy(), ref["final"])
+    # import into other slots and continue: same as continuing in place
+    env2 = st.Env(N, seed=9)
+    env2.import_(torch.arange(N).flip(0), pos)
+    env2.sync()
+    back = env2.export(torch.arange(N).flip(0))
+    env2.sync()
+    np.testing.assert_array_equal(back.cpu().numpy(), ref["final"])
+
+
+def test_import_of_oracle_positions_then_step_with_given_actions():
+    g = oracle.play_games(13, 8)
+    games = np.repeat(np.arange(8), 4)
+    plies = np.concatenate([np.linspace(0, g["lengths"][i] - 2, 4).astype(np.int16) for i in range(8)])
+    pos = oracle.replay_positions(g["setups"], g["actions"], games, plies)
+    n = len(pos)
+    env = st.Env(n, seed=2, autoreset=False)
+    env.import_(torch.arange(n), torch.from_numpy(pos).cuda())
+    acts = np.array([g["actions"][games[i], plies[i]] for i in range(n)], np.int16)
+    o = env.step(torch.from_numpy(acts).cuda())
+    env.sync()
+    nxt = oracle.replay_positions(g["setups"], g["actions"], games, plies + 1)
+    after = env.export(torch.arange(n))
+    env.sync()
+    np.testing.assert_array_equal(after.cpu().numpy(), nxt)
+    for i in range(n):
+        moves = oracle.legal_moves(nxt[i])
+        bits = np.unpackbits(o["mask"][i].cpu().numpy(), bitorder="little")
+        assert set(np.nonzero(bits)[0]) == set(moves.tolist())
+
+
+def test_bad_snapshot_is_rejected_without_fault():
+    env = st.Env(4, seed=1)
+    pos = env.export(torch.arange(4))
+    env.sync()
+    bad = pos.clone()
+    bad[0, 0] = 99                 # type code out of range
+    bad[1, 80] = 42                # a piece on a lake
+    bad[2, 245] = 7                # chaser neither 0, 1 nor none
+    env.import_(torch.arange(4), bad)
+    with pytest.raises(st.StrategoError) as ei:
+        env.sync()
+    assert ei.value.code == 8
+    now = env.export(torch.arange(4))
+    env.sync()
+    assert torch.equal(now[:3], pos[:3])
