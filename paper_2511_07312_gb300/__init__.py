@@ -130,8 +130,10 @@ class Env:
         cfg = st_env_config(self.N, int(seed) & 0xFFFFFFFFFFFFFFFF, make_rules(k, cap, flags),
                             AUTORESET if autoreset else 0, int(device), self.stream.cuda_stream)
         h = ctypes.c_void_p()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         _check(lib().st_env_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
+        self.release_to_current()
 
     def close(self):
         if getattr(self, "_h", None):
@@ -149,7 +151,19 @@ class Env:
             return torch.empty(shape, dtype=dtype, device=self.device)
 
     def wait_for_current(self):
+        """The env's stream waits for the caller's current stream (inputs
+        ready, output buffers free)."""
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def release_to_current(self):
+        """The caller's current stream waits for the env's stream (results
+        visible to whatever the caller enqueues next)."""
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _launch(self, fn, *a):
+        self.wait_for_current()
+        _check(fn(*a))
+        self.release_to_current()
 
     def step(self, actions=None, want_mask=True, out=None):
         """One ply in every slot; returns dict(action, reward, done, ply, mask)."""
@@ -157,10 +171,8 @@ class Env:
             out = dict(action=self._empty(self.N, torch.int16), reward=self._empty(self.N, torch.int8),
                        done=self._empty(self.N, torch.uint8), ply=self._empty(self.N, torch.int16),
                        mask=self._empty((self.N, MASK_BYTES), torch.uint8) if want_mask else None)
-        if actions is not None:
-            self.wait_for_current()
-        _check(lib().st_env_step(self._h, _ptr(actions, torch.int16, "actions"), _ptr(out["action"]),
-                                 _ptr(out["reward"]), _ptr(out["done"]), _ptr(out["ply"]), _ptr(out.get("mask"))))
+        self._launch(lib().st_env_step, self._h, _ptr(actions, torch.int16, "actions"), _ptr(out["action"]),
+                     _ptr(out["reward"]), _ptr(out["done"]), _ptr(out["ply"]), _ptr(out.get("mask")))
         return out
 
     def run(self, n_steps, ring_steps=None, want=("action", "reward", "done", "ply", "mask"), out=None):
@@ -172,36 +184,34 @@ class Env:
                        done=self._empty(shp, torch.uint8) if "done" in want else None,
                        ply=self._empty(shp, torch.int16) if "ply" in want else None,
                        mask=self._empty(shp + (MASK_BYTES,), torch.uint8) if "mask" in want else None)
-        _check(lib().st_env_run(self._h, int(n_steps), ring_steps, _ptr(out["action"]), _ptr(out["reward"]),
-                                _ptr(out["done"]), _ptr(out["ply"]), _ptr(out["mask"])))
+        self._launch(lib().st_env_run, self._h, int(n_steps), ring_steps, _ptr(out["action"]), _ptr(out["reward"]),
+                     _ptr(out["done"]), _ptr(out["ply"]), _ptr(out["mask"]))
         return out
 
     def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1):
         _check(lib().st_env_set_launch(self._h, int(warps_per_block), int(blocks_per_sm), int(games_per_fetch)))
 
     def reset(self, setups=None, which=None):
-        self.wait_for_current()
-        _check(lib().st_env_reset(self._h, _ptr(setups, torch.uint8, "setups"), _ptr(which, torch.uint8, "which")))
+        self._launch(lib().st_env_reset, self._h, _ptr(setups, torch.uint8, "setups"),
+                     _ptr(which, torch.uint8, "which"))
 
     def sync(self):
         _check(lib().st_env_sync(self._h))
 
     def stats(self):
         out = self._empty((self.N, 8), torch.int32)
-        _check(lib().st_env_stats(self._h, _ptr(out)))
+        self._launch(lib().st_env_stats, self._h, _ptr(out))
         return out
 
     def export(self, idx):
         idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
         out = self._empty((idx.numel(), POS_BYTES), torch.uint8)
-        self.wait_for_current()
-        _check(lib().st_env_export(self._h, _ptr(idx), idx.numel(), _ptr(out)))
+        self._launch(lib().st_env_export, self._h, _ptr(idx), idx.numel(), _ptr(out))
         return out
 
     def import_(self, idx, pos):
         idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
-        self.wait_for_current()
-        _check(lib().st_env_import(self._h, _ptr(idx), idx.numel(), _ptr(pos, torch.uint8, "positions")))
+        self._launch(lib().st_env_import, self._h, _ptr(idx), idx.numel(), _ptr(pos, torch.uint8, "positions"))
 
 
 def _dev(t, dtype, device):
