@@ -236,6 +236,38 @@ st_status st_obs_encode(const uint8_t* setups, const int16_t* actions, int32_t l
                         uint8_t* item_status, void* stream);
 
 /*
+ * st_obs_encode_static: st_obs_encode for callers that cannot allocate
+ * device memory while they run -- for example a serving or training loop
+ * that fixes its memory budget at start-up and must not call the allocator
+ * afterwards, or a caller running under a custom memory manager that does
+ * not see stream-ordered allocations.  (The paper has no counterpart of
+ * this entry point.)
+ *
+ * Same arguments, outputs and errors as st_obs_encode; the per-item replay
+ * records that st_obs_encode allocates per call (about 1.6 KB per item) live
+ * instead in a fixed array inside this library's device image, sized for
+ * ST_OBS_STATIC_MAX_ITEMS items (about 6.7 MB).  Every GPU on which the
+ * library is loaded holds that array until the process exits.
+ *  - B > ST_OBS_STATIC_MAX_ITEMS is rejected with ST_ERR_INVALID before
+ *    anything is enqueued; split the batch or use st_obs_encode.
+ *  - It never calls cudaMalloc, cudaFree, cudaMallocAsync or any other
+ *    allocating routine.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on that device.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (different streams, or threads, without ordering between them) race
+ *    and may corrupt each other's outputs.  Order them on one stream.
+ *  - Each call writes every record it later reads, so what an earlier call
+ *    left in the array never reaches an output.
+ */
+#define ST_OBS_STATIC_MAX_ITEMS 4096
+st_status st_obs_encode_static(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
+                               const int32_t* game, const int16_t* ply, const int8_t* player, int32_t B,
+                               const st_rules* rules, uint8_t* planes, uint16_t* planes_bf16, uint8_t* mask,
+                               uint8_t* item_status, void* stream);
+
+/*
  * st_belief_sample: K assignments of types to the hidden pieces of the
  * opponent of the player to move in each position, uniform over the
  * assignments consistent with the public history (App. E step 1, with the

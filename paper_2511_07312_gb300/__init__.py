@@ -76,6 +76,7 @@ def _declare(L):
         "st_replay_positions": [vp, vp, i32, i32, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp],
         "st_replay_set_chunk": [i32],
         "st_obs_encode": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
+        "st_obs_encode_static": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
         "st_belief_sample": [vp, i32, i32, u64, vp, vp, vp, vp],
         "st_rollout": [vp, i32, i32, i32, u64, vp, vp, ctypes.POINTER(st_rules), vp, vp, vp],
     }.items():

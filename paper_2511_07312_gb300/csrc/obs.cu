@@ -11,6 +11,7 @@
 // turns the record into the 487 planes, four squares of one channel per lane
 // per store (32-bit uint8 stores and 64-bit bf16 stores, coalesced across the
 // warp).
+#include <mutex>
 #include "engine.cuh"
 #include "features.cuh"
 #include "host_common.h"
@@ -439,6 +440,109 @@ extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions
     if (own_status) cudaFreeAsync(own_status, s);
     if (err != cudaSuccess) {
         stg::set_error("st_obs_encode: launch failed: %s", cudaGetErrorString(err));
+        return ST_ERR_CUDA;
+    }
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// Same computation as st_obs_encode, for callers that must not allocate
+// device memory once they are running.  The per-item replay records live in
+// a fixed array in this library's device image instead of a per-call
+// stream-ordered allocation.  The paper has no counterpart of this entry
+// point.
+
+static __device__ __align__(256) ItemState g_obs_static_items[ST_OBS_STATIC_MAX_ITEMS];
+static __device__ __align__(256) uint8_t g_obs_static_status[ST_OBS_STATIC_MAX_ITEMS];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct StaticScratch {
+    ItemState* items = nullptr;
+    uint8_t* status = nullptr;
+    bool ready = false;
+};
+
+std::mutex g_static_mu;
+StaticScratch g_static[kMaxDevices];
+
+// Device addresses of the static arrays on the current device, looked up
+// once per device.  The host-side names of the arrays are stand-ins, never
+// device addresses; only the looked-up pointers reach a kernel.
+st_status static_scratch(StaticScratch* out)
+{
+    int dev = -1;
+    ST_CUDA(cudaGetDevice(&dev));
+    ST_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "st_obs_encode_static: device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticScratch& s = g_static[dev];
+    if (!s.ready) {
+        void* items = nullptr;
+        void* status = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&items, g_obs_static_items);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&status, g_obs_static_status);
+        if (e != cudaSuccess) {
+            stg::set_error("st_obs_encode_static: cudaGetSymbolAddress failed on device %d: %s", dev,
+                           cudaGetErrorString(e));
+            return ST_ERR_CUDA;
+        }
+        s.items = static_cast<ItemState*>(items);
+        s.status = static_cast<uint8_t*>(status);
+        s.ready = true;
+    }
+    *out = s;
+    return ST_OK;
+}
+
+}  // namespace
+
+extern "C" st_status st_obs_encode_static(const uint8_t* setups, const int16_t* actions, int32_t log_len,
+                                          int32_t num_logs, const int32_t* game, const int16_t* ply,
+                                          const int8_t* player, int32_t B, const st_rules* rules, uint8_t* planes,
+                                          uint16_t* planes_bf16, uint8_t* mask, uint8_t* item_status, void* stream)
+{
+    ST_CHECK_ARG(rules_ok(rules), "st_obs_encode_static: invalid rules");
+    ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_obs_encode_static: negative size");
+    ST_CHECK_ARG(B <= ST_OBS_STATIC_MAX_ITEMS,
+                 "st_obs_encode_static: %d items exceed the fixed scratch of %d items; split the batch or use "
+                 "st_obs_encode", B, ST_OBS_STATIC_MAX_ITEMS);
+    if (B == 0) return ST_OK;
+    ST_CHECK_ARG(setups && actions && game && ply, "st_obs_encode_static: null argument");
+    ST_CHECK_ARG(!planes || ((uintptr_t)planes & 3u) == 0, "st_obs_encode_static: planes must be 4-byte aligned");
+    ST_CHECK_ARG(!planes_bf16 || ((uintptr_t)planes_bf16 & 7u) == 0,
+                 "st_obs_encode_static: planes_bf16 must be 8-byte aligned");
+    ST_CHECK_ARG(!mask || aligned16(mask), "st_obs_encode_static: mask must be 16-byte aligned");
+    StaticScratch sc;
+    const st_status ss = static_scratch(&sc);
+    if (ss != ST_OK) return ss;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool need_planes = planes || planes_bf16;
+    uint8_t* status = item_status ? item_status : (need_planes ? sc.status : nullptr);
+    if (!need_planes && !mask && !status) return ST_OK;
+    // k_replay writes every record and status byte of items 0..B-1 before
+    // k_obs_emit reads them, so nothing left by an earlier call is read and
+    // nothing needs clearing first.
+    ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
+    a.items_per_warp = g_items_per_warp;
+    a.state_out = need_planes ? sc.items : nullptr;
+    a.mask_out = mask;
+    a.status = status;
+    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
+    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
+    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && need_planes) {
+        EmitArgs e{};
+        e.items = sc.items; e.status = status; e.player = player; e.B = B; e.R = a.R;
+        e.planes = planes; e.planes_bf16 = planes_bf16;
+        const int eblocks = (B + kEmitWarps - 1) / kEmitWarps;
+        k_obs_emit<<<eblocks, 32 * kEmitWarps, kEmitWarps * sizeof(EmitSmem), s>>>(e);
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) {
+        stg::set_error("st_obs_encode_static: launch failed: %s", cudaGetErrorString(err));
         return ST_ERR_CUDA;
     }
     return ST_OK;
