@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--wpb", type=int, default=0, help="warps per block (0 = tuned default)")
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="time the persistent step launch only (for profiler captures): no plain path, "
+                        "end-to-end, secondary workloads or CPU baseline")
     return p.parse_args()
 
 
@@ -224,6 +227,15 @@ def main():
     achieved = bytes_per_launch / per_launch_s / 1e9
     clocks = clk.summary()
 
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "games": N, "plies": S, "ms_per_launch": ms / args.steps,
+                              "env_steps_per_s": value, "achieved_GBps": achieved}), flush=True)
+        env.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     extras = {}
     # plain per-ply launch path on the same workload shape (fewer plies)
     plain_plies = 50
@@ -346,9 +358,80 @@ def secondary(st, torch, dev, args):
     ms = t0.elapsed_time(t1) / reps
     tl = tallies.sum(0).cpu().numpy().tolist()
     out["belief_rollout"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K, "depth": D,
+                             "ply_steps_per_s_upper": P * K * D / (ms / 1000),
                              "tallies_win_loss_draw_unfinished": tl}
+    out["serving"] = serving(st, torch, dev, pos.cpu().numpy(), args)
     env.close()
     return out
+
+
+def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0):
+    """Config 5: Poisson arrivals (mean 2,000/s) of search requests, K ~
+    U{16..1024}, depth ~ U{8..64}, from replayed config-1 positions; the
+    continuous-batching server against one launch + sync per request."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    n = int(duration_s * rate)
+    gaps = rng.exponential(1.0 / rate, n)
+    arrive = np.cumsum(gaps)
+    Ks = rng.integers(16, 1025, n)
+    Ds = rng.integers(8, 65, n)
+    which = rng.integers(0, len(positions), n)
+    seed = 11
+
+    def pct(lat):
+        return {"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                "mean_ms": float(np.mean(lat)) * 1e3}
+
+    # served
+    srv = st.Server(device=dev.index, max_requests=512, sample_slots=1 << 18, max_batches=8)
+    tickets = [0] * n
+    t0 = time.perf_counter() + 0.05
+
+    def submitter():
+        for i in range(n):
+            while time.perf_counter() < t0 + arrive[i]:
+                pass
+            tickets[i] = srv.submit(positions[which[i]], int(Ks[i]), int(Ds[i]), seed, i)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = np.zeros(n)
+    first, last = None, 0
+    for i in range(n):
+        _, (sub, adm, done) = srv.wait(tickets[i], 120000)
+        lat[i] = (done - sub) / 1e9
+        first = sub if first is None else min(first, sub)
+        last = max(last, done)
+    span = (last - first) / 1e9
+    stats = srv.stats()
+    srv.close()
+    served = dict(pct(lat), requests_per_s=n / span, samples_per_s=float(Ks.sum()) / span,
+                  batches=stats["batches"], max_batch_requests=stats["max_batch_requests"])
+    # plain: one launch + sync per request, in arrival order
+    pos_h = torch.from_numpy(positions).pin_memory()
+    pos_d = torch.empty((1, positions.shape[1]), dtype=torch.uint8, device=dev)
+    tall = torch.empty((1, 4), dtype=torch.int32, device=dev)
+    tall_h = torch.empty((1, 4), dtype=torch.int32).pin_memory()
+    sid = torch.zeros(1, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    lat2 = np.zeros(n)
+    t0 = time.perf_counter() + 0.05
+    with torch.cuda.stream(s):
+        for i in range(n):
+            while time.perf_counter() < t0 + arrive[i]:
+                pass
+            pos_d.copy_(pos_h[which[i]:which[i] + 1], non_blocking=True)
+            sid.fill_(i)
+            st.rollout(pos_d, int(Ks[i]), int(Ds[i]), seed, stream_ids=sid, out=tall, stream=s)
+            tall_h.copy_(tall, non_blocking=True)
+            s.synchronize()
+            lat2[i] = time.perf_counter() - (t0 + arrive[i])
+    span2 = time.perf_counter() - t0
+    plain = dict(pct(lat2), requests_per_s=n / span2, samples_per_s=float(Ks.sum()) / span2)
+    return {"requests": n, "arrival_rate_per_s": rate, "K_range": [16, 1024], "depth_range": [8, 64],
+            "served": served, "plain_per_request": plain}
 
 
 if __name__ == "__main__":

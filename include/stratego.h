@@ -297,6 +297,64 @@ st_status st_rollout(const st_position* pos, int32_t P, int32_t K, int32_t depth
                      const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
                      int32_t* tallies, uint8_t* item_status, void* stream);
 
+/*
+ * Serving: test-time search requests with continuous batching (App. E: one
+ * search per move; here the search is st_rollout's belief samples and
+ * random rollouts).
+ *
+ * The server owns, from st_serve_create on: max_requests request slots on
+ * the device (root position, root state, counters), sample_slots per-sample
+ * records (sampled hidden types and outcome of each rollout), max_batches
+ * streams, and a scheduler thread.  A submitted request waits in arrival
+ * order until a request slot, K contiguous sample records and a stream are
+ * free (admission by free device memory); every request admitted since the
+ * previous launch goes into one batch (one warp per (request, sample)).
+ * Batches run concurrently, so a request arriving while others run starts at
+ * once instead of at a batch boundary.  A request's result is exactly
+ * st_rollout's tallies for the same position, K, depth, seed and stream id.
+ */
+typedef struct st_server st_server;
+
+typedef struct st_serve_config {
+    int32_t device;              /* CUDA device ordinal */
+    int32_t max_requests;        /* request slots resident at once, 1..65536 */
+    int32_t sample_slots;        /* per-sample records resident at once, 1..2^26 */
+    int32_t max_batches;         /* batches in flight at once (streams), 1..64 */
+    st_rules rules;
+} st_serve_config;
+
+typedef struct st_request {
+    st_position pos;             /* HOST: root position (copied at submit) */
+    int32_t K;                   /* belief samples, 0..sample_slots */
+    int32_t depth;               /* rollout plies, >= 0 */
+    uint64_t seed;               /* Philox key */
+    uint32_t stream_id;          /* Philox counter word 0 (st_rollout's stream_ids[p]) */
+} st_request;
+
+typedef struct st_timing {
+    uint64_t submit_ns;          /* steady-clock times of submit, admission, completion */
+    uint64_t admit_ns;
+    uint64_t done_ns;
+} st_timing;
+
+typedef struct st_serve_stats {
+    int64_t submitted, admitted, completed, batches, max_batch_requests, queued, running;
+} st_serve_stats;
+
+st_status st_serve_create(const st_serve_config* cfg, st_server** out);
+/* Queue a request (all HOST memory); returns a ticket.  ST_ERR_BUSY if the
+ * host queue holds 2^20 requests. */
+st_status st_serve_submit(st_server* srv, const st_request* req, uint64_t* ticket);
+/* ST_OK with tallies[4] (HOST) and timing (HOST, may be NULL) once done, then
+ * the ticket is released; ST_ERR_NOT_READY before; ST_ERR_BAD_POSITION if the
+ * root failed validation (tallies zero); ST_ERR_INVALID for an unknown ticket. */
+st_status st_serve_poll(st_server* srv, uint64_t ticket, int32_t* tallies, st_timing* timing);
+/* As st_serve_poll, blocking up to timeout_ms; ST_ERR_TIMEOUT if not done. */
+st_status st_serve_wait(st_server* srv, uint64_t ticket, int32_t timeout_ms, int32_t* tallies, st_timing* timing);
+st_status st_serve_get_stats(st_server* srv, st_serve_stats* out);
+/* Stops the scheduler, waits for launched batches, frees everything. */
+st_status st_serve_destroy(st_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

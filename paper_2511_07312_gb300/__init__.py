@@ -40,6 +40,29 @@ class st_env_config(ctypes.Structure):
                 ("env_flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
+class st_position(ctypes.Structure):
+    _fields_ = [("raw", ctypes.c_uint8 * POS_BYTES)]
+
+
+class st_request(ctypes.Structure):
+    _fields_ = [("pos", st_position), ("K", ctypes.c_int32), ("depth", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("stream_id", ctypes.c_uint32)]
+
+
+class st_serve_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_requests", ctypes.c_int32), ("sample_slots", ctypes.c_int32),
+                ("max_batches", ctypes.c_int32), ("rules", st_rules)]
+
+
+class st_timing(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
+
+
+class st_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "batches", "max_batch_requests",
+                                               "queued", "running")]
+
+
 _lib = None
 
 
@@ -79,6 +102,12 @@ def _declare(L):
         "st_obs_encode_static": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
         "st_belief_sample": [vp, i32, i32, u64, vp, vp, vp, vp],
         "st_rollout": [vp, i32, i32, i32, u64, vp, vp, ctypes.POINTER(st_rules), vp, vp, vp],
+        "st_serve_create": [ctypes.POINTER(st_serve_config), ctypes.POINTER(vp)],
+        "st_serve_submit": [vp, ctypes.POINTER(st_request), ctypes.POINTER(ctypes.c_uint64)],
+        "st_serve_poll": [vp, ctypes.c_uint64, vp, ctypes.POINTER(st_timing)],
+        "st_serve_wait": [vp, ctypes.c_uint64, i32, vp, ctypes.POINTER(st_timing)],
+        "st_serve_get_stats": [vp, ctypes.POINTER(st_serve_stats)],
+        "st_serve_destroy": [vp],
     }.items():
         if hasattr(L, name):
             fn = getattr(L, name)
@@ -267,3 +296,64 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
                             _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
                             _ptr(tallies), _ptr(status), _stream(stream)))
     return tallies, status
+
+
+class Server:
+    """Search-request server with continuous batching (st_serve_*).
+
+    submit() takes a host position (784 uint8 numpy array or bytes) and
+    returns a ticket; poll()/wait() return (tallies[4] numpy int32, timing)
+    or raise StrategoError (NOT_READY, TIMEOUT, BAD_POSITION)."""
+
+    def __init__(self, device=0, max_requests=256, sample_slots=1 << 16, max_batches=8, k=100, cap=1000,
+                 flags=RULES_ALL):
+        import numpy as np  # noqa: F401
+        cfg = st_serve_config(int(device), int(max_requests), int(sample_slots), int(max_batches),
+                              make_rules(k, cap, flags))
+        h = ctypes.c_void_p()
+        _check(lib().st_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, pos, K, depth, seed, stream_id=0):
+        import numpy as np
+        req = st_request()
+        buf = np.ascontiguousarray(np.frombuffer(bytes(pos), dtype=np.uint8) if isinstance(pos, (bytes, bytearray))
+                                   else np.asarray(pos, dtype=np.uint8))
+        if buf.size != POS_BYTES:
+            raise ValueError("position must be %d bytes" % POS_BYTES)
+        ctypes.memmove(ctypes.addressof(req.pos), buf.ctypes.data, POS_BYTES)
+        req.K, req.depth = int(K), int(depth)
+        req.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        req.stream_id = int(stream_id) & 0xFFFFFFFF
+        t = ctypes.c_uint64()
+        _check(lib().st_serve_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def _result(self, fn, *a):
+        import numpy as np
+        tallies = np.zeros(4, np.int32)
+        tm = st_timing()
+        _check(fn(self._h, *a, tallies.ctypes.data_as(ctypes.c_void_p), ctypes.byref(tm)))
+        return tallies, (tm.submit_ns, tm.admit_ns, tm.done_ns)
+
+    def poll(self, ticket):
+        return self._result(lib().st_serve_poll, ctypes.c_uint64(ticket))
+
+    def wait(self, ticket, timeout_ms=60000):
+        return self._result(lib().st_serve_wait, ctypes.c_uint64(ticket), int(timeout_ms))
+
+    def stats(self):
+        s = st_serve_stats()
+        _check(lib().st_serve_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in st_serve_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().st_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,177 @@
+// rollout.cuh -- shared device code of the search path (App. E "Search",
+// steps 1-2): the hidden-piece plan of a position, one belief sample, the
+// root state of a position kept in HBM, and one warp's rollout from a sample.
+// Used by st_rollout (search.cu) and by the serving engine (serve.cu).
+#pragma once
+#include "engine.cuh"
+#include "snapshot.cuh"
+
+namespace stg {
+
+// Hidden-piece structure of one position, from the player to move.
+struct __align__(16) BeliefPlan {
+    uint8_t known[40];      // type of opponent piece i if public, else 0xFF
+    uint8_t order[40];      // hidden pieces in ascending square order
+    uint8_t is_unmoved[40]; // per entry of order
+    uint8_t movable[40];    // sorted movable multiset still to place
+    int n_hidden, n_unmoved, n_flag, n_imm, n_mov;
+    int opp;
+};
+
+// Single thread.
+__device__ inline void make_plan(const SmemGame* G, BeliefPlan* B)
+{
+    const int opp = 1 - (G->c.ply & 1);
+    int c[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+    int nS = 0;
+    for (int k = 0; k < 40; ++k) {
+        const int p = opp * 40 + k;
+        const uint8_t f = G->c.flags[p];
+        if (!(f & 1) || (f & 2)) { B->known[k] = G->c.type[p]; c[G->c.type[p]]--; }
+        else if (f & 8) { B->known[k] = kScout; nS++; }
+        else B->known[k] = 0xFF;
+    }
+    c[kScout] -= nS;
+    int nh = 0, nu = 0;
+    for (int s = 0; s < 100; ++s) {
+        const uint8_t p = G->board[s];
+        if (p >= kPieces || (int)(p / 40) != opp) continue;
+        const int k = p - 40 * opp;
+        if (B->known[k] != 0xFF) continue;
+        B->order[nh] = (uint8_t)k;
+        B->is_unmoved[nh] = (G->c.flags[p] & 4) ? 0 : 1;
+        nu += B->is_unmoved[nh];
+        nh++;
+    }
+    int nm = 0;
+    for (int t = 0; t <= kMarshal; ++t)
+        for (int j = 0; j < c[t] && nm < 40; ++j) B->movable[nm++] = (uint8_t)t;
+    B->n_hidden = nh;
+    B->n_unmoved = nu;
+    B->n_flag = c[kFlag];
+    B->n_imm = c[kFlag] + c[kBomb];
+    B->n_mov = nm;
+    B->opp = opp;
+}
+
+// One sample (single thread): the types of opponent pieces 0..39.  Draw w is
+// word w%4 of Philox at counter (stream, sample, 0, 3<<24 | w/4).
+__device__ inline void draw_sample(const BeliefPlan* B, uint32_t k0, uint32_t k1, uint32_t stream, uint32_t sample,
+                                   uint8_t* out)
+{
+    uint32_t w = 0;
+    uint4 buf = make_uint4(0, 0, 0, 0);
+    auto next = [&]() -> uint32_t {
+        if ((w & 3) == 0) buf = philox(make_uint4(stream, sample, 0u, (3u << 24) | (w >> 2)), k0, k1);
+        const uint32_t r = (w & 3) == 0 ? buf.x : (w & 3) == 1 ? buf.y : (w & 3) == 2 ? buf.z : buf.w;
+        ++w;
+        return r;
+    };
+    for (int k = 0; k < 40; ++k) out[k] = B->known[k];
+    // 1. immovable pieces onto n_imm of the unmoved hidden pieces (partial Fisher-Yates)
+    uint8_t idx[40], imm[40];
+    const int nu = B->n_unmoved;
+    for (int i = 0; i < nu; ++i) { idx[i] = (uint8_t)i; imm[i] = 0xFF; }
+    for (int i = 0; i < B->n_imm && i < nu; ++i) {
+        const int j = i + (int)uniform_below(next(), (uint32_t)(nu - i));
+        const uint8_t t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+        imm[idx[i]] = (uint8_t)(i < B->n_flag ? kFlag : kBomb);
+    }
+    // 2. the movable multiset over the remaining hidden pieces (full Fisher-Yates)
+    uint8_t arr[40];
+    const int m = B->n_mov;
+    for (int i = 0; i < m; ++i) arr[i] = B->movable[i];
+    for (int i = m - 1; i >= 1; --i) {
+        const int j = (int)uniform_below(next(), (uint32_t)(i + 1));
+        const uint8_t t = arr[i]; arr[i] = arr[j]; arr[j] = t;
+    }
+    int u = 0, nxt = 0;
+    for (int h = 0; h < B->n_hidden; ++h) {
+        const int k = B->order[h];
+        if (B->is_unmoved[h]) {
+            const uint8_t t = imm[u++];
+            if (t != 0xFF) { out[k] = t; continue; }
+        }
+        if (nxt < m) out[k] = arr[nxt];
+        ++nxt;
+    }
+}
+
+// Root of a search: the imported position as the rollout warps need it.
+struct __align__(16) RootState {
+    GameCore c;
+    uint8_t board[112];
+    uint64_t pi[kPiCap];
+    uint16_t ring[kRing];
+    BeliefPlan plan;
+    int32_t bad;
+    int32_t pad[3];
+};
+
+struct __align__(16) RolloutSmem {
+    SmemGame g;
+    uint64_t pi[kPiCap];
+    uint16_t ring[kRing];
+    uint8_t types[48];
+};
+
+// Warp: import snapshot `in` and write its root state (bad != 0 if invalid).
+__device__ inline void build_root(RolloutSmem* S, const st_position* in, RootState* out)
+{
+    const int lane = lane_id();
+    const int bad = import_position(&S->g, in, S->ring, S->pi);
+    if (lane == 0) {
+        out->bad = bad;
+        if (!bad) make_plan(&S->g, &out->plan);
+    }
+    if (bad) return;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(&S->g);   // core + board
+        uint4* dst = reinterpret_cast<uint4*>(out);
+        for (int i = lane; i < (288 + 112) / 16; i += 32) dst[i] = src[i];
+    }
+    for (int i = lane; i < kRing; i += 32) out->ring[i] = S->ring[i];
+    for (int i = lane; i < S->g.c.n_pi; i += 32) out->pi[i] = S->pi[i];
+}
+
+// Warp: one rollout of `depth` random plies from root R with sample `k`
+// (types given, or drawn from R->plan).  Returns the tally slot: 0 win,
+// 1 loss, 2 draw for the player to move at the root, 3 unfinished.
+__device__ inline int rollout_one(RolloutSmem* S, const RootState* R, const uint8_t* types, int depth, uint32_t k0,
+                                  uint32_t k1, uint32_t stream, uint32_t k, const Rules& Rl)
+{
+    const int lane = lane_id();
+    SmemGame* G = &S->g;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(R);
+        uint4* dst = reinterpret_cast<uint4*>(G);
+        for (int i = lane; i < (288 + 112) / 16; i += 32) dst[i] = src[i];
+        const uint4* rs = reinterpret_cast<const uint4*>(R->ring);
+        uint4* rd = reinterpret_cast<uint4*>(S->ring);
+        for (int i = lane; i < kRing * 2 / 16; i += 32) rd[i] = rs[i];
+    }
+    __syncwarp();
+    const int npi = G->c.n_pi;
+    for (int i = lane; i < npi; i += 32) S->pi[i] = R->pi[i];
+    const int searcher = G->c.ply & 1, opp = 1 - searcher;
+    if (types) {
+        for (int i = lane; i < 40; i += 32) S->types[i] = types[i];
+    } else if (lane == 0) {
+        draw_sample(&R->plan, k0, k1, stream, k, S->types);
+    }
+    __syncwarp();
+    for (int i = lane; i < 40; i += 32) G->c.type[opp * 40 + i] = S->types[i];
+    __syncwarp();
+    int n = gen_moves(G, searcher, Rl.flags, false, true, S->ring, S->pi);
+    int code = 0, winner = -1;
+    if (n == 0) start_end(G, Rl, S->ring, S->pi, code, winner);
+    for (int d = 0; !code && d < depth; ++d) {
+        const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
+        const int a = select_action(G, uniform_below(w.x, (uint32_t)n));
+        apply_move(G, a, S->ring, S->pi);
+        check_end(G, Rl, S->ring, S->pi, code, winner, n);
+    }
+    return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
+}
+
+}  // namespace stg
