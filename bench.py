@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--wpb", type=int, default=0, help="warps per block (0 = tuned default)")
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
+    p.add_argument("--gpw", type=int, default=0, help="games per warp, 1 or 2 (0 = tuned default)")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="time the persistent step launch only (for profiler captures): no plain path, "
@@ -186,9 +187,14 @@ def main():
 
     N, S, R = args.games, args.plies, args.ring
     env = st.Env(N, seed=args.seed + rank, device=local)
-    wpb = args.wpb or 4
-    gpf = args.gpf or 1
-    env.set_launch(wpb, 0, gpf)
+    tuned = None
+    if args.wpb and args.gpw:
+        wpb, gpw, gpf = args.wpb, args.gpw, args.gpf or 1
+    else:
+        from paper_2511_07312_gb300 import autotune
+        tuned = autotune.tune(N, device=local)
+        wpb, gpw, gpf = tuned["warps_per_block"], tuned["games_per_warp"], tuned["games_per_fetch"]
+    env.set_launch(wpb, 0, gpf, games_per_warp=gpw)
     ring = env.run(1, R)   # allocates the ring; later calls reuse it
     env.sync()
 
@@ -296,7 +302,8 @@ def main():
                            "games_per_gpu": N, "plies_per_step": S, "ring_rows": R,
                            "l2": "output ring %.2f GB > L2 (inputs larger than L2, no flush)" %
                                  (R * N * MASK_BYTES / 1e9),
-                           "launch": {"warps_per_block": wpb, "games_per_fetch": gpf}},
+                           "launch": {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
+                                      "chosen_by": "autotuner" if tuned else "command line"}},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None,
                              "peak_kind": peak_kind + " hbm_gbs (copy, burst)",

@@ -186,9 +186,11 @@ st_status st_env_step(st_env* env, const int16_t* actions, int16_t* action_out, 
 st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
                      int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring);
 
-/* Launch shape of st_env_run: warps per block (1..32), blocks per SM (>=1,
- * 0 = occupancy maximum) and slots a warp claims per queue fetch (>=1). */
-st_status st_env_set_launch(st_env* env, int32_t warps_per_block, int32_t blocks_per_sm,
+/* Launch shape of st_env_run: warps per block (1..16), blocks per SM (0 =
+ * occupancy maximum), games a warp steps side by side (1: one 32-lane team,
+ * 2: two 16-lane teams) and slots each team claims per queue fetch (>=1).
+ * Results do not depend on the shape. */
+st_status st_env_set_launch(st_env* env, int32_t warps_per_block, int32_t blocks_per_sm, int32_t games_per_warp,
                             int32_t games_per_fetch);
 
 /* Wait for the env's stream; return and clear a latched device error. */

@@ -91,7 +91,7 @@ def _declare(L):
         "st_env_reset": [vp, vp, vp],
         "st_env_step": [vp, vp, vp, vp, vp, vp, vp],
         "st_env_run": [vp, i32, i32, vp, vp, vp, vp, vp],
-        "st_env_set_launch": [vp, i32, i32, i32],
+        "st_env_set_launch": [vp, i32, i32, i32, i32],
         "st_env_sync": [vp],
         "st_env_stats": [vp, vp],
         "st_env_export": [vp, vp, i32, vp],
@@ -218,8 +218,9 @@ class Env:
                      _ptr(out["done"]), _ptr(out["ply"]), _ptr(out["mask"]))
         return out
 
-    def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1):
-        _check(lib().st_env_set_launch(self._h, int(warps_per_block), int(blocks_per_sm), int(games_per_fetch)))
+    def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1, games_per_warp=1):
+        _check(lib().st_env_set_launch(self._h, int(warps_per_block), int(blocks_per_sm), int(games_per_warp),
+                                       int(games_per_fetch)))
 
     def reset(self, setups=None, which=None):
         self._launch(lib().st_env_reset, self._h, _ptr(setups, torch.uint8, "setups"),

@@ -1,0 +1,83 @@
+"""Launch-shape autotuner of the persistent environment step (st_env_run).
+
+Times short runs of every candidate shape -- warps per block x games per
+warp (1, 2 or 4 games side by side in one warp) x slots per queue fetch --
+on a scratch env of the caller's size and picks the fastest.  Results are
+cached in a JSON file keyed by (device name, number of games, library
+version), so a shape is tuned once per machine and size.
+"""
+import json
+import os
+import time
+
+import torch
+
+from . import Env, version
+
+WARPS_PER_BLOCK = (2, 4, 8, 16)
+GAMES_PER_WARP = (1, 2, 4)
+GAMES_PER_FETCH = (1, 4)
+
+
+def _cache_path():
+    base = os.environ.get("STRATEGO_GB300_CACHE") or os.path.join(
+        os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")), "stratego_gb300")
+    os.makedirs(base, exist_ok=True)
+    return os.path.join(base, "launch_shapes.json")
+
+
+def _key(num_games, device):
+    return "%s|%d|%s" % (torch.cuda.get_device_name(device), num_games, version())
+
+
+def load(num_games, device=0):
+    try:
+        return json.load(open(_cache_path())).get(_key(num_games, device))
+    except (OSError, ValueError):
+        return None
+
+
+def tune(num_games, device=0, plies=200, reps=2, force=False, verbose=False):
+    """Return {"warps_per_block", "games_per_warp", "games_per_fetch",
+    "env_steps_per_s"} of the fastest shape, timed with CUDA events."""
+    if not force:
+        hit = load(num_games, device)
+        if hit:
+            return hit
+    env = Env(num_games, seed=12345, device=device)
+    ring = env.run(1, 4)
+    results = []
+    for wpb in WARPS_PER_BLOCK:
+        for gpw in GAMES_PER_WARP:
+            for gpf in GAMES_PER_FETCH:
+                try:
+                    env.set_launch(wpb, 0, gpf, games_per_warp=gpw)
+                except RuntimeError:
+                    continue
+                env.run(plies, 4, out=ring)        # warm-up, captures the graph
+                start = torch.cuda.Event(enable_timing=True)
+                end = torch.cuda.Event(enable_timing=True)
+                start.record(env.stream)
+                for _ in range(reps):
+                    env.run(plies, 4, out=ring)
+                end.record(env.stream)
+                end.synchronize()
+                rate = num_games * plies * reps / (start.elapsed_time(end) / 1000.0)
+                results.append((rate, wpb, gpw, gpf))
+                if verbose:
+                    print("wpb %2d gpw %d gpf %d: %.3e env-steps/s" % (wpb, gpw, gpf, rate), flush=True)
+    env.close()
+    rate, wpb, gpw, gpf = max(results)
+    best = {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf, "env_steps_per_s": rate,
+            "plies": plies, "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    path = _cache_path()
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        data = {}
+    data[_key(num_games, device)] = best
+    tmp = path + ".tmp.%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, path)
+    return best

@@ -1,12 +1,21 @@
-// engine.cuh -- warp-cooperative Stratego engine for sm_103a.
+// engine.cuh -- team-cooperative Stratego engine for sm_103a.
 //
-// One warp owns one game at a time.  The game lives in a warp-private
-// shared-memory record (SmemGame): the 288-byte per-game state that persists
-// in HBM between launches, the board rebuilt from it (piece id per square),
-// and the 1,264-byte legal-move mask of the player to move.  Lanes split the
-// work of mask generation (one task per (movable piece, direction), compacted
-// with __ballot_sync / __popc) and of setup, hashing and output; the scalar
-// part of a ply (apply, battle, rule state) runs on lane 0.
+// A team of L lanes (L = 32: one game per warp; L = 16: two games per warp)
+// owns one game at a time.  The game lives in a team-private shared-memory
+// record (SmemGame): the 288-byte per-game state that persists in HBM
+// between launches, the board (piece id per square), row bitboards kept up to
+// date ply by ply (own pieces, movable non-Scouts and Scouts per player and
+// row, occupancy per column), and the 1,264-byte legal-move mask of the
+// player to move.
+//
+// Move generation: lane r < 10 of the team owns board row r.  Non-Scout
+// moves of a whole row come from four shifted bitboards; each from-square's
+// (at most four) destinations are OR-ed into the mask as one window of at
+// most 21 bits (one or two shared atomics).  Scout slides come from the row
+// and column occupancy with find-first-set.  The scalar part of a ply (apply,
+// battle, rule state) runs on the team's first lane; all collectives are
+// team-masked, so the teams of a warp run in lockstep when their games take
+// the same path and serialize harmlessly when they do not.
 //
 // Rules follow App. A of arXiv 2511.07312 (Tab. pieces, Tab. chase), the
 // two-square and chasing state machines of App. B.2-B.3, the k-move rule and
@@ -31,9 +40,11 @@ constexpr uint8_t kEmpty = 0xFF;
 constexpr uint8_t kLake = 0xFE;
 constexpr uint8_t kNone = 0xFF;
 constexpr int kMaskBytes = 1264;
-constexpr int kMaskWordsAlloc = 320;   // 316 used by the output layout, 4 spare (kept zero)
+constexpr int kMaskWordsAlloc = 384;   // 316 used by the output layout, the rest kept zero (96 uint4 = 3 or 6 per lane)
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
 constexpr int kRing = 256;             // moves of history per game
+constexpr uint32_t kLakeRow = 0xCCu;   // columns 2,3,6,7 of rows 4 and 5
+constexpr uint32_t kLakeCol = 0x30u;   // rows 4,5 of columns 2,3,6,7
 
 enum : int { kSpy = 0, kScout = 1, kMiner = 2, kMarshal = 9, kFlag = 10, kBomb = 11 };
 enum : int { kClBattle = 0, kClQuiet = 1, kClThreat = 2, kClEvade = 3 };
@@ -73,11 +84,49 @@ static_assert(sizeof(GameCore) == 288, "GameCore layout");
 struct __align__(16) SmemGame {
     GameCore c;
     uint8_t board[112];
+    uint16_t occ[2][10];      // pieces of player p in row r (bit = column)
+    uint16_t mov[2][10];      // movable non-Scouts
+    uint16_t sco[2][10];      // Scouts
+    uint16_t colocc[10];      // all pieces in column c (bit = row)
+    uint16_t h0, h1;          // actions played 1 and 2 plies ago (0xFFFF none)
+    uint8_t flag_pid[2];
+    uint8_t pad[14];
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 1280, "SmemGame layout");
+static_assert(sizeof(SmemGame) == 288 + 112 + 120 + 20 + 4 + 2 + 14 + 4 * kMaskWordsAlloc, "SmemGame layout");
+constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// ----------------------------------------------------------------- teams
+template <int L>
+struct Team {
+    static_assert(L == 32 || L == 16 || L == 8, "teams of 8, 16 or 32 lanes");
+    int tl;          // lane within the team
+    int base;        // first warp lane of the team
+    unsigned mask;   // warp lanes of the team
+    __device__ __forceinline__ Team()
+    {
+        const int lane = threadIdx.x & 31;
+        tl = lane & (L - 1);
+        base = lane - tl;
+        mask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << base);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    __device__ __forceinline__ uint32_t ballot(bool p) const { return __ballot_sync(mask, p) >> base; }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(mask, p); }
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(mask, v, src, L); }
+    __device__ __forceinline__ uint32_t shfl_up(uint32_t v, int d) const { return __shfl_up_sync(mask, v, d, L); }
+    __device__ __forceinline__ uint32_t shfl_down(uint32_t v, int d) const { return __shfl_down_sync(mask, v, d, L); }
+    __device__ __forceinline__ int sum(int v) const { return (int)__reduce_add_sync(mask, (unsigned)v); }
+    __device__ __forceinline__ uint64_t xor64(uint64_t v) const
+    {
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(mask, v, o, L);
+        return v;
+    }
+    __device__ __forceinline__ bool leader() const { return tl == 0; }
+};
 
 // ----------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
@@ -141,44 +190,20 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
     return pos;
 }
 
+__device__ __forceinline__ bool enemy_of(uint8_t o, int P) { return o < kPieces && (int)(o / 40) != P; }
+
 // ----------------------------------------------------------------- state load/store
-__device__ __forceinline__ void load_core(SmemGame* G, const GameCore* src)
+template <int L>
+__device__ __forceinline__ void load_core(SmemGame* G, const GameCore* src, const Team<L>& T)
 {
-    const int lane = lane_id();
-    if (lane < 18) reinterpret_cast<uint4*>(&G->c)[lane] = reinterpret_cast<const uint4*>(src)[lane];
-    __syncwarp();
+    for (int i = T.tl; i < 18; i += L) reinterpret_cast<uint4*>(&G->c)[i] = reinterpret_cast<const uint4*>(src)[i];
+    T.sync();
 }
-__device__ __forceinline__ void store_core(const SmemGame* G, GameCore* dst)
+template <int L>
+__device__ __forceinline__ void store_core(const SmemGame* G, GameCore* dst, const Team<L>& T)
 {
-    __syncwarp();
-    const int lane = lane_id();
-    if (lane < 18) reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
-}
-
-__device__ __forceinline__ void build_board(SmemGame* G)
-{
-    const int lane = lane_id();
-    for (int s = lane; s < 112; s += 32) G->board[s] = (s < 100 && is_lake(s)) ? kLake : kEmpty;
-    __syncwarp();
-    for (int p = lane; p < kPieces; p += 32)
-        if (G->c.flags[p] & 1) G->board[G->c.sq[p]] = (uint8_t)p;
-    __syncwarp();
-}
-
-__device__ __forceinline__ uint64_t warp_xor64(uint64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint64_t board_hash(const SmemGame* G)
-{
-    const int lane = lane_id();
-    uint64_t h = 0;
-    for (int p = lane; p < kPieces; p += 32)
-        if (G->c.flags[p] & 1) h ^= zkey(p, G->c.sq[p]);
-    return warp_xor64(h);
+    T.sync();
+    for (int i = T.tl; i < 18; i += L) reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(&G->c)[i];
 }
 
 // History: the action played i+1 plies ago, 0xFFFF if unknown.
@@ -189,6 +214,57 @@ __device__ __forceinline__ int hist_at(const SmemGame* G, const uint16_t* ring, 
     return ring[(ply - 1 - i) & (kRing - 1)];
 }
 
+// Everything derived from the core and the board: row and column bitboards,
+// flag ids, the last two moves.  Needs G->board.
+template <int L>
+__device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, const Team<L>& T)
+{
+    for (int r = T.tl; r < 10; r += L) {
+        uint32_t o0 = 0, o1 = 0, m0 = 0, m1 = 0, s0 = 0, s1 = 0, col = 0;
+        for (int c = 0; c < 10; ++c) {
+            const uint8_t p = G->board[10 * r + c];
+            if (p < kPieces) {
+                const uint32_t b = 1u << c;
+                const int t = G->c.type[p];
+                if (p < 40) { o0 |= b; if (t == kScout) s0 |= b; else if (t < kFlag) m0 |= b; }
+                else        { o1 |= b; if (t == kScout) s1 |= b; else if (t < kFlag) m1 |= b; }
+            }
+            const uint8_t q = G->board[10 * c + r];   // column r, row c
+            if (q < kPieces) col |= 1u << c;
+        }
+        G->occ[0][r] = (uint16_t)o0; G->occ[1][r] = (uint16_t)o1;
+        G->mov[0][r] = (uint16_t)m0; G->mov[1][r] = (uint16_t)m1;
+        G->sco[0][r] = (uint16_t)s0; G->sco[1][r] = (uint16_t)s1;
+        G->colocc[r] = (uint16_t)col;
+    }
+    for (int p = T.tl; p < kPieces; p += L)
+        if (G->c.type[p] == kFlag) G->flag_pid[p / 40] = (uint8_t)p;
+    if (T.leader()) {
+        G->h0 = (uint16_t)hist_at(G, ring, 0);
+        G->h1 = (uint16_t)hist_at(G, ring, 1);
+    }
+    T.sync();
+}
+
+template <int L>
+__device__ __forceinline__ void build_board(SmemGame* G, const Team<L>& T)
+{
+    for (int s = T.tl; s < 112; s += L) G->board[s] = (s < 100 && is_lake(s)) ? kLake : kEmpty;
+    T.sync();
+    for (int p = T.tl; p < kPieces; p += L)
+        if (G->c.flags[p] & 1) G->board[G->c.sq[p]] = (uint8_t)p;
+    T.sync();
+}
+
+template <int L>
+__device__ __forceinline__ uint64_t board_hash(const SmemGame* G, const Team<L>& T)
+{
+    uint64_t h = 0;
+    for (int p = T.tl; p < kPieces; p += L)
+        if (G->c.flags[p] & 1) h ^= zkey(p, G->c.sq[p]);
+    return T.xor64(h);
+}
+
 // ----------------------------------------------------------------- rule context
 struct PlyCtx {
     int prev_to;        // square the previous ply ended on (-1 none)
@@ -196,18 +272,16 @@ struct PlyCtx {
     int h1_from, h1_to; // the move played two plies ago (-1 none)
 };
 
-__device__ __forceinline__ PlyCtx make_ctx(const SmemGame* G, const uint16_t* ring)
+__device__ __forceinline__ PlyCtx make_ctx(const SmemGame* G)
 {
     PlyCtx x;
-    const int h0 = hist_at(G, ring, 0), h1 = hist_at(G, ring, 1);
+    const int h0 = G->h0, h1 = G->h1;
     x.prev_to = h0 == 0xFFFF ? -1 : h0 % 100;
     x.prev_nb = !G->c.last_battle;
     x.h1_from = h1 == 0xFFFF ? -1 : h1 / 100;
     x.h1_to = h1 == 0xFFFF ? -1 : h1 % 100;
     return x;
 }
-
-__device__ __forceinline__ bool enemy_of(uint8_t o, int P) { return o < kPieces && (int)(o / 40) != P; }
 
 __device__ __forceinline__ bool threat_square(const SmemGame* G, int q, int P)
 {
@@ -259,105 +333,268 @@ __device__ __forceinline__ bool chase_blocks(const SmemGame* G, const PlyCtx& x,
     return false;
 }
 
+// 128-bit sets over to-squares, kept in registers as two 64-bit halves.
+struct Set128 {
+    uint64_t lo, hi;
+};
+__device__ __forceinline__ uint64_t lowbits64(int n) { return n <= 0 ? 0ull : (n >= 64 ? ~0ull : ((1ull << n) - 1ull)); }
+// bits [a, a+n) (0 <= a, a+n <= 128)
+__device__ __forceinline__ Set128 range128(int a, int n)
+{
+    Set128 r;
+    const int b = a + n;
+    r.lo = lowbits64(min(b, 64)) & ~lowbits64(min(a, 64));
+    r.hi = lowbits64(max(b - 64, 0)) & ~lowbits64(max(a - 64, 0));
+    return r;
+}
+__device__ __forceinline__ Set128 shl128(Set128 v, int s)   // 0 <= s < 128
+{
+    Set128 r;
+    if (s == 0) return v;
+    if (s >= 64) { r.hi = v.lo << (s - 64); r.lo = 0; return r; }
+    r.hi = (v.hi << s) | (v.lo >> (64 - s));
+    r.lo = v.lo << s;
+    return r;
+}
+__device__ __forceinline__ Set128 or128(Set128 a, Set128 b) { return Set128{a.lo | b.lo, a.hi | b.hi}; }
+__device__ __forceinline__ Set128 bit128(int i)
+{
+    return i < 64 ? Set128{1ull << i, 0ull} : Set128{0ull, 1ull << (i - 64)};
+}
+__device__ __forceinline__ int popc128(Set128 v) { return __popcll(v.lo) + __popcll(v.hi); }
+
+// Squares c + 10k for k in [k0, k1] (column c, rows k0..k1).
+__device__ __forceinline__ Set128 column128(int c, int k0, int k1)
+{
+    // bits 0, 10, 20, ..., 90
+    const Set128 every10{0x1004010040100401ull, 0x0000000004010040ull};
+    if (k1 < k0) return Set128{0, 0};
+    // keep rows k0..k1 of the every-tenth pattern, then move to column c
+    Set128 p = every10;
+    const Set128 keep = range128(10 * k0, 10 * (k1 - k0) + 1);
+    p.lo &= keep.lo;
+    p.hi &= keep.hi;
+    return shl128(p, c);
+}
+
+// Drops the destinations (128-bit set over to-squares) of the piece on
+// `from` that the two-square or chasing rule forbids.
+__device__ __forceinline__ Set128 filter_dests(const SmemGame* G, int P, int from, bool ts_here, bool chase_on,
+                                               const PlyCtx& x, const uint64_t* pi, Set128 d)
+{
+    const int pid = G->board[from];
+    for (int half = 0; half < 2; ++half) {
+        uint64_t m = half ? d.hi : d.lo;
+        while (m) {
+            const int b = __ffsll(m) - 1;
+            m &= m - 1;
+            const int to = 64 * half + b;
+            bool bad = ts_here && two_square_blocks(G, P, to);
+            if (!bad && chase_on && G->board[to] == kEmpty) bad = chase_blocks(G, x, pi, P, pid, from, to);
+            if (bad) {
+                if (half) d.hi &= ~(1ull << b); else d.lo &= ~(1ull << b);
+            }
+        }
+    }
+    return d;
+}
+
+// OR a 128-bit set over to-squares into the mask row of from-square s.
+__device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d)
+{
+    const int base = 100 * s, w0 = base >> 5, sh = base & 31;
+    const uint32_t w[4] = {(uint32_t)d.lo, (uint32_t)(d.lo >> 32), (uint32_t)d.hi, (uint32_t)(d.hi >> 32)};
+    uint32_t prev = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t v = sh ? (w[i] << sh) | prev : w[i];
+        prev = sh ? (w[i] >> (32 - sh)) : 0u;
+        if (v) atomicOr(&mask[w0 + i], v);
+    }
+    if (prev) atomicOr(&mask[w0 + 4], prev);
+}
+
 // ----------------------------------------------------------------- move generation
 // Counts (and, if write_mask, records in G->mask) the moves of player P.
 // physical: movement rules only (App. A "Piece details"); otherwise the
-// two-square and chasing rules filter as rules.flags says.  Returns the
-// warp-uniform count.
-static __device__ __noinline__ int gen_moves(SmemGame* G, int P, uint32_t rule_flags, bool physical, bool write_mask,
-                                      const uint16_t* ring, const uint64_t* pi)
+// two-square and chasing rules filter as rule_flags says.  Team-uniform
+// result.
+template <int L>
+__device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint32_t rule_flags, bool physical,
+                                      bool write_mask, const uint64_t* pi)
 {
-    const int lane = lane_id();
     if (write_mask) {
         uint4* m4 = reinterpret_cast<uint4*>(G->mask);
-        const uint4 z = make_uint4(0, 0, 0, 0);
-        for (int i = lane; i < kMaskWordsAlloc / 4; i += 32) m4[i] = z;
+        for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
     }
-    const int base = P * 40;
-    const uint8_t f0 = G->c.flags[base + lane], t0 = G->c.type[base + lane];
-    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, (f0 & 1) && t0 < kFlag);
-    bool ok1 = false;
-    if (lane < 8) {
-        const uint8_t f1 = G->c.flags[base + 32 + lane], t1 = G->c.type[base + 32 + lane];
-        ok1 = (f1 & 1) && t1 < kFlag;
-    }
-    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, ok1);
-    const int n0 = __popc(b0), npieces = n0 + __popc(b1);
-
-    const bool ts_on = !physical && (rule_flags & kTwoSquare) && G->c.ts_pid[P] != kNone && G->c.ts_len[P] == 4;
     const int ts_pid = G->c.ts_pid[P];
+    const bool ts_on = !physical && (rule_flags & kTwoSquare) && ts_pid != kNone && G->c.ts_len[P] == 4 &&
+                       (G->c.flags[ts_pid] & 1);
+    const int ts_from = ts_on ? G->c.sq[ts_pid] : -1;
     const bool chase_on = !physical && (rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0;
-    PlyCtx x;
-    if (chase_on) x = make_ctx(G, ring);
-    __syncwarp();
-
+    const PlyCtx x = make_ctx(G);
+    T.sync();   // mask zeroed before any atomic
     int cnt = 0;
-    const int ntasks = npieces * 4;
-    for (int task = lane; task < ntasks; task += 32) {
-        const int k = task >> 2, dir = task & 3;
-        const int j = k < n0 ? nth_set_bit(b0, k) : 32 + nth_set_bit(b1, k - n0);
-        const int pid = base + j;
-        const int s = G->c.sq[pid];
-        const int r = s / 10, c = s - 10 * r;
-        const int dr = (dir == 0) - (dir == 1), dc = (dir == 2) - (dir == 3);
-        const int maxd = G->c.type[pid] == kScout ? 9 : 1;
-        for (int d = 1; d <= maxd; ++d) {
-            const int rr = r + dr * d, cc = c + dc * d;
-            if ((unsigned)rr > 9u || (unsigned)cc > 9u) break;
-            const int q = rr * 10 + cc;
-            const uint8_t occ = G->board[q];
-            if (occ == kLake) break;
-            const bool enemy = occ != kEmpty;
-            if (enemy && (int)(occ / 40) == P) break;
-            bool legal = true;
-            if (ts_on && pid == ts_pid) legal = !two_square_blocks(G, P, q);
-            if (legal && chase_on && !enemy) legal = !chase_blocks(G, x, pi, P, pid, s, q);
-            if (legal) {
-                ++cnt;
-                if (write_mask) {
-                    const int a = s * 100 + q;
-                    atomicOr(&G->mask[a >> 5], 1u << (a & 31));
+    for (int r = T.tl; r < 10; r += L) {
+        const uint32_t own = G->occ[P][r], enm = G->occ[1 - P][r], mv = G->mov[P][r];
+        uint32_t sc = G->sco[P][r];
+        const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
+        const uint32_t fre = ~own & ~lake & 0x3FFu;                     // empty or enemy squares of row r
+        const uint32_t fre_up = r < 9 ? (~(uint32_t)G->occ[P][r + 1] & ~((r + 1 == 4 || r + 1 == 5) ? kLakeRow : 0u) &
+                                         0x3FFu) : 0u;
+        const uint32_t fre_dn = r > 0 ? (~(uint32_t)G->occ[P][r - 1] & ~((r - 1 == 4 || r - 1 == 5) ? kLakeRow : 0u) &
+                                         0x3FFu) : 0u;
+        const uint32_t FE = mv & (fre >> 1);
+        const uint32_t FW = mv & ((fre << 1) & 0x3FFu);
+        const uint32_t FN = mv & fre_up;
+        const uint32_t FS = mv & fre_dn;
+        uint32_t moving = FE | FW | FN | FS;
+        if (!ts_on && !chase_on) {
+            cnt += __popc(FE) + __popc(FW) + __popc(FN) + __popc(FS);
+            if (write_mask) {
+                while (moving) {
+                    const int c = __ffs(moving) - 1;
+                    moving &= moving - 1;
+                    const int s = 10 * r + c;
+                    const int lo = s >= 10 ? s - 10 : (c > 0 ? s - 1 : s + 1);
+                    const uint32_t pat = (((FS >> c) & 1u) << ((s - 10 - lo) & 31)) |
+                                         (((FW >> c) & 1u) << ((s - 1 - lo) & 31)) |
+                                         (((FE >> c) & 1u) << ((s + 1 - lo) & 31)) |
+                                         (((FN >> c) & 1u) << ((s + 10 - lo) & 31));
+                    const int base = 100 * s + lo;
+                    const uint64_t v = (uint64_t)pat << (base & 31);
+                    atomicOr(&G->mask[base >> 5], (uint32_t)v);
+                    if (v >> 32) atomicOr(&G->mask[(base >> 5) + 1], (uint32_t)(v >> 32));
                 }
             }
-            if (enemy) break;
+        } else {
+            while (moving) {
+                const int c = __ffs(moving) - 1;
+                moving &= moving - 1;
+                const int s = 10 * r + c;
+                Set128 d{0ull, 0ull};
+                if ((FS >> c) & 1u) d = or128(d, bit128(s - 10));
+                if ((FW >> c) & 1u) d = or128(d, bit128(s - 1));
+                if ((FE >> c) & 1u) d = or128(d, bit128(s + 1));
+                if ((FN >> c) & 1u) d = or128(d, bit128(s + 10));
+                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+                cnt += popc128(d);
+                if (write_mask) or_row(G->mask, s, d);
+            }
+        }
+        // Scouts: slides along the row and the column, stopping before a lake
+        // or an own piece and on the first enemy piece.
+        const uint32_t rowocc = own | enm | lake;
+        while (sc) {
+            const int c = __ffs(sc) - 1;
+            sc &= sc - 1;
+            const int s = 10 * r + c;
+            // slide lengths: empty squares east/west/north/south, then whether
+            // the blocker is an enemy (a capture ends the slide)
+            const uint32_t e = rowocc >> (c + 1);
+            const int runE = e ? __ffs(e) - 1 : 9 - c;
+            const int capE = (e && ((enm >> (c + 1 + runE)) & 1u)) ? 1 : 0;
+            const uint32_t w = rowocc & ((1u << c) - 1u);
+            const int hw = w ? 31 - __clz(w) : -1;
+            const int runW = c - 1 - hw;
+            const int capW = (hw >= 0 && ((enm >> hw) & 1u)) ? 1 : 0;
+            const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
+            const uint32_t n = colocc >> (r + 1);
+            const int runN = n ? __ffs(n) - 1 : 9 - r;
+            const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
+            const uint32_t so = colocc & ((1u << r) - 1u);
+            const int hs = so ? 31 - __clz(so) : -1;
+            const int runS = r - 1 - hs;
+            const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
+            const int nd = runE + capE + runW + capW + runN + capN + runS + capS;
+            if (nd == 0) continue;
+            if (ts_on || chase_on) {
+                Set128 d = or128(range128(s + 1, runE + capE), range128(s - runW - capW, runW + capW));
+                d = or128(d, column128(c, r + 1, r + runN + capN));
+                d = or128(d, column128(c, r - runS - capS, r - 1));
+                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+                cnt += popc128(d);
+                if (write_mask) or_row(G->mask, s, d);
+                continue;
+            }
+            cnt += nd;
+            if (write_mask) {
+                // along the row: two runs of consecutive to-squares
+                const int row_bit = 100 * s;
+                const int nw = runW + capW, ne = runE + capE;
+                if (nw) {
+                    const int b = row_bit + s - nw;
+                    const uint64_t v = ((1ull << nw) - 1ull) << (b & 31);
+                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
+                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+                }
+                if (ne) {
+                    const int b = row_bit + s + 1;
+                    const uint64_t v = ((1ull << ne) - 1ull) << (b & 31);
+                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
+                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+                }
+                // along the column: one bit per to-square, ten apart
+                for (int k = 1; k <= runN + capN; ++k) {
+                    const int b = row_bit + s + 10 * k;
+                    atomicOr(&G->mask[b >> 5], 1u << (b & 31));
+                }
+                for (int k = 1; k <= runS + capS; ++k) {
+                    const int b = row_bit + s - 10 * k;
+                    atomicOr(&G->mask[b >> 5], 1u << (b & 31));
+                }
+            }
         }
     }
-    const int n = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    __syncwarp();
-    return n;
+    const int total = T.sum(cnt);
+    T.sync();
+    return total;
 }
 
-// The idx-th set bit (ascending) of G->mask; warp-uniform result.
-__device__ __forceinline__ int select_action(const SmemGame* G, uint32_t idx)
+// The idx-th set bit (ascending) of G->mask; team-uniform result.
+template <int L>
+__device__ __forceinline__ int select_action(const SmemGame* G, const Team<L>& T, uint32_t idx)
 {
-    const int lane = lane_id();
-    uint32_t w[10];
+    constexpr int W = kMaskWordsAlloc / L;   // words per lane: 12 or 24
+    static_assert(W % 4 == 0, "whole uint4 per lane");
+    const int t = T.tl;
+    const uint4* m4 = reinterpret_cast<const uint4*>(G->mask) + t * (W / 4);
+    uint32_t c4[W / 4];
     int cnt = 0;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        w[k] = G->mask[lane * 10 + k];
-        cnt += __popc(w[k]);
+    for (int k = 0; k < W / 4; ++k) {
+        const uint4 v = m4[k];
+        c4[k] = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        cnt += c4[k];
     }
     int incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
+    for (int o = 1; o < L; o <<= 1) {
+        const int v = __shfl_up_sync(T.mask, incl, o, L);
+        if (t >= o) incl += v;
     }
     const int excl = incl - cnt;
-    const uint32_t own = __ballot_sync(0xFFFFFFFFu, (int)idx >= excl && (int)idx < incl);
+    const uint32_t own = T.ballot((int)idx >= excl && (int)idx < incl);
     int a = -1;
-    if (own & (1u << lane)) {
+    if (own & (1u << t)) {
         int local = (int)idx - excl;
+        int k = 0;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            const int ck = __popc(w[k]);
-            if (a < 0 && local < ck) a = (lane * 10 + k) * 32 + nth_set_bit(w[k], local);
-            if (a < 0) local -= ck;
+        for (int j = 0; j < W / 4; ++j)
+            if (k == j && local >= (int)c4[j]) { local -= c4[j]; k = j + 1; }
+        k = min(k, W / 4 - 1);
+        const uint4 v = m4[k];
+        const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
+        int wi = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cj = __popc(ws[j]);
+            if (wi == j && local >= cj) { local -= cj; wi = j + 1; }
         }
+        wi = min(wi, 3);
+        a = ((t * (W / 4) + k) * 4 + wi) * 32 + nth_set_bit(ws[wi], local);
     }
-    const int src = own ? __ffs(own) - 1 : 0;
-    return __shfl_sync(0xFFFFFFFFu, a, src);
+    return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
 
 __device__ __forceinline__ bool mask_has(const SmemGame* G, int a)
@@ -368,31 +605,24 @@ __device__ __forceinline__ bool mask_has(const SmemGame* G, int a)
 // Is the flag of `side` captured?
 __device__ __forceinline__ bool flag_dead(const SmemGame* G, int side)
 {
-    const int lane = lane_id();
-    bool d = false;
-    for (int k = lane; k < 40; k += 32) {
-        const int p = side * 40 + k;
-        d |= G->c.type[p] == kFlag && !(G->c.flags[p] & 1);
-    }
-    return __any_sync(0xFFFFFFFFu, d);
+    return !(G->c.flags[G->flag_pid[side]] & 1);
 }
 
 // ----------------------------------------------------------------- apply
 // Plays action a for the player to move.  ring/pi: this game's history ring
-// and chase-position store.  Returns whether the move was a battle.
-static __device__ __noinline__ void apply_move(SmemGame* G, int a, uint16_t* ring, uint64_t* pi)
+// and chase-position store.
+template <int L>
+__device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, uint16_t* ring, uint64_t* pi)
 {
-    const int lane = lane_id();
-    if (a < 0 || a >= 10000) return;   // callers pass mask members only; never index outside the board
-    const PlyCtx x = make_ctx(G, ring);
-    __syncwarp();
-    if (lane == 0) {
+    if (T.leader() && a >= 0 && a < 10000) {
+        const PlyCtx x = make_ctx(G);
         GameCore& c = G->c;
         const int P = c.ply & 1;
         const int from = a / 100, to = a - 100 * (a / 100);
         const int X = G->board[from];
         const int cls = classify(G, x, P, from, to);
-        const int dist = abs(from - to) >= 10 ? abs(from - to) / 10 : abs(from - to);
+        const int rf = from / 10, cf = from - 10 * rf, rt = to / 10, ct = to - 10 * rt;
+        const int dist = rf == rt ? abs(cf - ct) : abs(rf - rt);
         uint8_t fx = c.flags[X];
         if (dist > 1) fx |= 8;
         fx |= 4;
@@ -400,7 +630,12 @@ static __device__ __noinline__ void apply_move(SmemGame* G, int a, uint16_t* rin
         uint64_t h = c.hash ^ zkey(X, from);
         int D = -1;
         bool d_died = false, x_alive = true;
+        const int tX = c.type[X];
+        uint16_t* kindX = tX == kScout ? G->sco[P] : G->mov[P];
         G->board[from] = kEmpty;
+        G->occ[P][rf] &= (uint16_t)~(1u << cf);
+        kindX[rf] &= (uint16_t)~(1u << cf);
+        G->colocc[cf] &= (uint16_t)~(1u << rf);
         if (!battle) {
             G->board[to] = (uint8_t)X;
             c.sq[X] = (uint8_t)to;
@@ -409,14 +644,14 @@ static __device__ __noinline__ void apply_move(SmemGame* G, int a, uint16_t* rin
             D = G->board[to];
             uint8_t fd = c.flags[D];
             const bool d_rev = fd & 2;
-            const int ta = c.type[X], td = c.type[D];
+            const int td = c.type[D];
             // Tab. pieces: Flag loses to any attacker; Bomb beats all but the
             // Miner; the attacking Spy beats the Marshal; otherwise by rank.
             int out;
             if (td == kFlag) out = 1;
-            else if (td == kBomb) out = ta == kMiner ? 1 : 2;
-            else if (ta == kSpy && td == kMarshal) out = 1;
-            else out = ta > td ? 1 : (ta < td ? 2 : 3);
+            else if (td == kBomb) out = tX == kMiner ? 1 : 2;
+            else if (tX == kSpy && td == kMarshal) out = 1;
+            else out = tX > td ? 1 : (tX < td ? 2 : 3);
             fx |= 2;
             fd |= 2;
             if (out == 1) {
@@ -439,7 +674,19 @@ static __device__ __noinline__ void apply_move(SmemGame* G, int a, uint16_t* rin
                 h ^= zkey(D, to);
             }
             c.flags[D] = fd;
+            if (d_died) {
+                const int Q = 1 - P;
+                G->occ[Q][rt] &= (uint16_t)~(1u << ct);
+                G->mov[Q][rt] &= (uint16_t)~(1u << ct);
+                G->sco[Q][rt] &= (uint16_t)~(1u << ct);
+            }
         }
+        if (x_alive) {
+            G->occ[P][rt] |= (uint16_t)(1u << ct);
+            kindX[rt] |= (uint16_t)(1u << ct);
+        }
+        if (G->board[to] != kEmpty) G->colocc[ct] |= (uint16_t)(1u << rt);
+        else G->colocc[ct] &= (uint16_t)~(1u << rt);
         c.flags[X] = fx;
         c.hash = h;
         const int ply_before = c.ply;
@@ -477,31 +724,33 @@ static __device__ __noinline__ void apply_move(SmemGame* G, int a, uint16_t* rin
         } else {
             c.chaser = kNone; c.n_pi = 0; c.chase_plies = 0;
         }
-        ring[ply_before & (kRing - 1)] = (uint16_t)a;
+        if (ring) ring[ply_before & (kRing - 1)] = (uint16_t)a;
+        G->h1 = G->h0;
+        G->h0 = (uint16_t)a;
     }
-    __syncwarp();
+    T.sync();
 }
 
 // ----------------------------------------------------------------- new game
 // setup: custom types per piece id, or nullptr for the Philox setup of
 // (slot, episode).
-static __device__ __noinline__ void reset_game(SmemGame* G, uint32_t k0, uint32_t k1, uint32_t slot, uint32_t episode,
-                                        const uint8_t* setup)
+template <int L>
+__device__ __noinline__ void reset_game(SmemGame* G, const Team<L>& T, uint32_t k0, uint32_t k1, uint32_t slot,
+                                        uint32_t episode, const uint8_t* setup)
 {
-    const int lane = lane_id();
-    for (int p = lane; p < kPieces; p += 32) {
+    for (int p = T.tl; p < kPieces; p += L) {
         G->c.type[p] = setup ? setup[p] : sorted_type(p % 40);
         G->c.sq[p] = (uint8_t)start_square(p);
         G->c.flags[p] = 1;
     }
-    __syncwarp();
-    if (!setup && lane < 2) {
-        uint8_t* arr = G->c.type + 40 * lane;
+    T.sync();
+    if (!setup && T.tl < 2) {
+        uint8_t* arr = G->c.type + 40 * T.tl;
         uint4 w = make_uint4(0, 0, 0, 0);
         for (int i = 39; i >= 1; --i) {
             const int d = 39 - i;
             if ((d & 3) == 0)
-                w = philox(make_uint4(slot, episode, 0u, (1u << 24) | ((uint32_t)lane << 8) | (uint32_t)(d >> 2)),
+                w = philox(make_uint4(slot, episode, 0u, (1u << 24) | ((uint32_t)T.tl << 8) | (uint32_t)(d >> 2)),
                            k0, k1);
             const uint32_t r = (d & 3) == 0 ? w.x : (d & 3) == 1 ? w.y : (d & 3) == 2 ? w.z : w.w;
             const uint32_t j = uniform_below(r, (uint32_t)(i + 1));
@@ -510,7 +759,7 @@ static __device__ __noinline__ void reset_game(SmemGame* G, uint32_t k0, uint32_
             arr[j] = t;
         }
     }
-    if (lane == 0) {
+    if (T.leader()) {
         GameCore& c = G->c;
         c.ply = 0; c.battleless = 0; c.last_battle = 0;
         c.chaser = kNone; c.chase_plies = 0; c.n_pi = 0;
@@ -518,13 +767,14 @@ static __device__ __noinline__ void reset_game(SmemGame* G, uint32_t k0, uint32_
         for (int i = 0; i < 4; ++i) c.ts_sq[0][i] = c.ts_sq[1][i] = kNone;
         c.terminated = 0; c.episode = episode; c.n_legal = 0;
     }
-    __syncwarp();
-    const uint64_t h = board_hash(G);
-    if (lane == 0) G->c.hash = h;
-    build_board(G);
+    T.sync();
+    const uint64_t h = board_hash(G, T);
+    if (T.leader()) G->c.hash = h;
+    build_board(G, T);
+    derive_state(G, (const uint16_t*)nullptr, T);
 }
 
-// ----------------------------------------------------------------- one ply of the env loop
+// ----------------------------------------------------------------- endings
 struct PlyResult {
     int action;
     int code;
@@ -534,7 +784,8 @@ struct PlyResult {
 
 // Ending after the ply just played (App. A "Game Summary", App. D.1); also
 // leaves the mask of the player to move in G->mask and its count in n.
-__device__ __forceinline__ void check_end(SmemGame* G, const Rules& R, const uint16_t* ring, const uint64_t* pi,
+template <int L>
+__device__ __forceinline__ void check_end(SmemGame* G, const Team<L>& T, const Rules& R, const uint64_t* pi,
                                           int& code, int& winner, int& n)
 {
     const int Q = G->c.ply & 1, P = 1 - Q;
@@ -542,9 +793,9 @@ __device__ __forceinline__ void check_end(SmemGame* G, const Rules& R, const uin
     winner = -1;
     n = 0;
     if (flag_dead(G, Q)) { code = 1; winner = P; return; }
-    n = gen_moves(G, Q, R.flags, false, true, ring, pi);
+    n = gen_moves(G, T, Q, R.flags, false, true, pi);
     if (n == 0) {
-        const int phys = gen_moves(G, P, R.flags, true, false, ring, pi);
+        const int phys = gen_moves(G, T, P, R.flags, true, false, pi);
         code = phys == 0 ? 3 : 2;
         winner = phys == 0 ? -1 : P;
         return;
@@ -553,21 +804,23 @@ __device__ __forceinline__ void check_end(SmemGame* G, const Rules& R, const uin
     if (G->c.ply >= R.cap) { code = 5; return; }
 }
 
-// The acting player of a fresh position has no legal move (n_legal == 0).
-__device__ __forceinline__ void start_end(SmemGame* G, const Rules& R, const uint16_t* ring, const uint64_t* pi,
-                                          int& code, int& winner)
+// The acting player of a fresh position has no legal move (n == 0).
+template <int L>
+__device__ __forceinline__ void start_end(SmemGame* G, const Team<L>& T, const Rules& R, const uint64_t* pi, int& code,
+                                          int& winner)
 {
     const int P = G->c.ply & 1;
-    const int phys = gen_moves(G, 1 - P, R.flags, true, false, ring, pi);
+    const int phys = gen_moves(G, T, 1 - P, R.flags, true, false, pi);
     code = phys == 0 ? 3 : 2;
     winner = phys == 0 ? -1 : 1 - P;
 }
 
-__device__ __forceinline__ void zero_mask(SmemGame* G)
+template <int L>
+__device__ __forceinline__ void zero_mask(SmemGame* G, const Team<L>& T)
 {
     uint4* m4 = reinterpret_cast<uint4*>(G->mask);
-    for (int i = lane_id(); i < kMaskWordsAlloc / 4; i += 32) m4[i] = make_uint4(0, 0, 0, 0);
-    __syncwarp();
+    for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
+    T.sync();
 }
 
 }  // namespace stg

@@ -1,11 +1,11 @@
 // env.cu -- the batched environment (App. B.1 StrategoRolloutBuffer as a
 // simulator): N independent game slots kept in HBM, stepped one ply per
 // launch (st_env_step, the plain path) or many plies per persistent launch
-// (st_env_run), with auto-reset, snapshots and per-slot counters.
-#include <cstring>
-#include <mutex>
-#include <vector>
+// (st_env_run), with auto-reset, snapshots and per-slot counters.  The
+// persistent launch runs one or two games per warp (teams of 32 or 16
+// lanes), the shape chosen by st_env_set_launch.
 #include <algorithm>
+#include <cstring>
 #include "engine.cuh"
 #include "snapshot.cuh"
 #include "host_common.h"
@@ -25,10 +25,11 @@ struct st_env {
     int32_t* status = nullptr;      // [0] latched st_status, [1] first slot (min)
     int32_t* queue = nullptr;       // work counter of the persistent launch
     int wpb = 4, bps = 0, gpf = 1;  // launch shape of st_env_run
+    int gpw = 1;                    // games per warp (1 or 2)
     int sms = 0;
     int max_bps = 0;
     cudaGraphExec_t graph = nullptr;
-    int64_t graph_key[10] = {0};
+    int64_t graph_key[11] = {0};
 };
 
 namespace stg {
@@ -56,7 +57,7 @@ int sm_count()
 }  // namespace stg
 
 extern "C" const char* st_last_error(void) { return stg::g_err.c_str(); }
-extern "C" const char* st_version(void) { return "stratego-gb300 0.1 (sm_103a)"; }
+extern "C" const char* st_version(void) { return "stratego-gb300 0.2 (sm_103a)"; }
 
 namespace {
 
@@ -77,11 +78,12 @@ __device__ __forceinline__ void latch(int32_t* status, int code, int slot)
     atomicMin(&status[1], slot);
 }
 
-__device__ __forceinline__ void write_mask(const SmemGame* G, uint8_t* dst)
+template <int L>
+__device__ __forceinline__ void write_mask(const SmemGame* G, const Team<L>& T, uint8_t* dst)
 {
     const uint4* src = reinterpret_cast<const uint4*>(G->mask);
     uint4* d = reinterpret_cast<uint4*>(dst);
-    for (int i = lane_id(); i < kMaskBytes / 16; i += 32) d[i] = src[i];
+    for (int i = T.tl; i < kMaskBytes / 16; i += L) d[i] = src[i];
 }
 
 __device__ __forceinline__ bool setup_counts_ok(const uint8_t* s)
@@ -100,36 +102,38 @@ __device__ __forceinline__ bool setup_counts_ok(const uint8_t* s)
     return true;
 }
 
-// One ply of slot g (App. B.1): the mask of the player to move is in G->mask
-// with count n.  given: the supplied action or -1 for the random policy.
-__device__ PlyResult env_ply(SmemGame* G, int& n, const EnvArgs& A, uint32_t slot, int given, uint16_t* ring,
-                             uint64_t* pi, bool& illegal)
+// One ply of slot `slot` (App. B.1): the mask of the player to move is in
+// G->mask with count n.  given: the supplied action or -1 for the random
+// policy.
+template <int L>
+__device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int& n, const EnvArgs& A, uint32_t slot,
+                                             int given, uint16_t* ring, uint64_t* pi, bool& illegal)
 {
     PlyResult res;
     res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = G->c.ply;
     illegal = false;
     if (G->c.terminated) return res;
     if (n == 0) {
-        start_end(G, A.R, ring, pi, res.code, res.winner);
+        start_end(G, T, A.R, pi, res.code, res.winner);
     } else {
         int a = given;
         if (a >= 0) {
             if (!mask_has(G, a)) { illegal = true; return res; }
         } else {
             const uint4 w = philox(make_uint4(slot, G->c.episode, (uint32_t)G->c.ply, 2u << 24), A.k0, A.k1);
-            a = select_action(G, uniform_below(w.x, (uint32_t)n));
+            a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
         }
-        apply_move(G, a, ring, pi);
+        apply_move(G, T, a, ring, pi);
         res.action = a;
-        check_end(G, A.R, ring, pi, res.code, res.winner, n);
+        check_end(G, T, A.R, pi, res.code, res.winner, n);
     }
     if (res.code) {
         if (A.R.flags & kAutoreset) {
-            reset_game(G, A.k0, A.k1, slot, G->c.episode + 1, nullptr);
-            n = gen_moves(G, 0, A.R.flags, false, true, ring, pi);
+            reset_game(G, T, A.k0, A.k1, slot, G->c.episode + 1, nullptr);
+            n = gen_moves(G, T, 0, A.R.flags, false, true, pi);
         } else {
-            if (lane_id() == 0) G->c.terminated = (uint8_t)res.code;
-            zero_mask(G);
+            if (T.leader()) G->c.terminated = (uint8_t)res.code;
+            zero_mask(G, T);
             n = 0;
         }
     }
@@ -142,114 +146,141 @@ __device__ __forceinline__ int reward_of(const PlyResult& r)
     return 0;
 }
 
+// Per-slot counters: games ended by code 1-5, plies played, red wins, blue wins.
 __device__ __forceinline__ void count_result(uint32_t* st, const PlyResult& r)
 {
-    if (r.action >= 0) st[5] += 1;
-    if (r.code) {
-        st[r.code - 1] += 1;
-        const int rw = reward_of(r);
-        if (rw > 0) st[6] += 1;
-        if (rw < 0) st[7] += 1;
-    }
+    st[5] += r.action >= 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) st[k] += r.code == k + 1;
+    const int rw = reward_of(r);
+    st[6] += rw > 0;
+    st[7] += rw < 0;
 }
+
+template <int L>
+__device__ __forceinline__ SmemGame* team_game(unsigned char* smem) { return reinterpret_cast<SmemGame*>(smem) + threadIdx.x / L; }
 
 __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* which, int first)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const Team<32> T;
+    SmemGame* G = team_game<32>(smem);
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= A.N) return;
     if (which && !which[g]) return;
     const uint8_t* setup = setups ? setups + 80 * (size_t)g : nullptr;
     if (setup && !setup_counts_ok(setup)) {
-        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, g);
+        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, g);
         return;
     }
     uint32_t episode = 0;
     if (!first) {
-        load_core(G, A.core + g);
+        load_core(G, A.core + g, T);
         episode = G->c.episode + 1;
     }
-    if (first && lane_id() < 8) A.stats[8 * (size_t)g + lane_id()] = 0;
-    reset_game(G, A.k0, A.k1, (uint32_t)g, episode, setup);
-    const int n = gen_moves(G, 0, A.R.flags, false, false, A.ring + (size_t)g * kRing, A.pi + (size_t)g * kPiCap);
-    if (lane_id() == 0) G->c.n_legal = (uint16_t)n;
-    store_core(G, A.core + g);
+    if (first && T.tl < 8) A.stats[8 * (size_t)g + T.tl] = 0;
+    reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
+    const int n = gen_moves(G, T, 0, A.R.flags, false, false, A.pi + (size_t)g * kPiCap);
+    if (T.leader()) G->c.n_legal = (uint16_t)n;
+    store_core(G, A.core + g, T);
 }
 
+template <int L>
 __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
                            uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const Team<L> T;
+    SmemGame* G = team_game<L>(smem);
+    const int g = blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
     if (g >= A.N) return;
     uint16_t* ring = A.ring + (size_t)g * kRing;
     uint64_t* pi = A.pi + (size_t)g * kPiCap;
-    load_core(G, A.core + g);
-    build_board(G);
+    load_core(G, A.core + g, T);
+    build_board(G, T);
+    derive_state(G, ring, T);
     const int P = G->c.ply & 1;
     int n = 0;
-    if (G->c.terminated) zero_mask(G);
-    else n = gen_moves(G, P, A.R.flags, false, true, ring, pi);
+    if (G->c.terminated) zero_mask(G, T);
+    else n = gen_moves(G, T, P, A.R.flags, false, true, pi);
     bool illegal = false;
     const int given = actions ? (int)actions[g] : -1;
-    const PlyResult r = env_ply(G, n, A, (uint32_t)g, given, ring, pi, illegal);
-    if (lane_id() == 0) {
+    const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, given, ring, pi, illegal);
+    if (T.leader()) {
         if (illegal) latch(A.status, ST_ERR_ILLEGAL_ACTION, g);
         if (action_out) action_out[g] = (int16_t)r.action;
         if (reward_out) reward_out[g] = (int8_t)reward_of(r);
         if (done_out) done_out[g] = (uint8_t)r.code;
         if (ply_out) ply_out[g] = (int16_t)r.ply_idx;
         if (!illegal) {
-            uint32_t* st = A.stats + 8 * (size_t)g;
+            uint32_t st[8];
+            uint32_t* gs = A.stats + 8 * (size_t)g;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) st[k] = gs[k];
             count_result(st, r);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) gs[k] = st[k];
         }
         G->c.n_legal = (uint16_t)n;
     }
-    if (mask_out) write_mask(G, mask_out + (size_t)g * kMaskBytes);
-    if (!illegal) store_core(G, A.core + g);
+    if (mask_out) write_mask(G, T, mask_out + (size_t)g * kMaskBytes);
+    if (!illegal) store_core(G, A.core + g, T);
 }
 
-// Persistent form: each warp claims `gpf` slots at a time from a global
-// counter and plays n_steps plies in each, keeping the game in shared memory.
-__global__ void k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf, int16_t* action_ring,
-                          int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+// Persistent form: each warp claims (32/L)*gpf slots at a time from a global
+// counter; each team plays n_steps plies in each of its slots, keeping the
+// game in shared memory.
+#ifndef ST_RUN_MIN_BLOCKS
+#define ST_RUN_MIN_BLOCKS 2   // 512 x 2 threads per SM -> at most 64 registers per thread
+#endif
+template <int L>
+__global__ void __launch_bounds__(512, ST_RUN_MIN_BLOCKS) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
+                                                 int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
+                                                 int16_t* ply_ring, uint8_t* mask_ring)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
-    const int lane = lane_id();
+    const Team<L> T;
+    SmemGame* G = team_game<L>(smem);
+    const int lane = threadIdx.x & 31;
+    constexpr int kTeams = 32 / L;
     for (;;) {
         int start = 0;
-        if (lane == 0) start = atomicAdd(queue, gpf);
+        if (lane == 0) start = atomicAdd(queue, kTeams * gpf);
         start = __shfl_sync(0xFFFFFFFFu, start, 0);
         if (start >= A.N) break;
-        const int end = min(start + gpf, A.N);
-        for (int g = start; g < end; ++g) {
+        const int first = start + (lane / L) * gpf;
+        for (int gi = 0; gi < gpf; ++gi) {
+            const int g = first + gi;
+            if (g >= A.N) break;
             uint16_t* ring = A.ring + (size_t)g * kRing;
             uint64_t* pi = A.pi + (size_t)g * kPiCap;
-            load_core(G, A.core + g);
-            build_board(G);
+            load_core(G, A.core + g, T);
+            build_board(G, T);
+            derive_state(G, ring, T);
             int n = 0;
-            if (G->c.terminated) zero_mask(G);
-            else n = gen_moves(G, G->c.ply & 1, A.R.flags, false, true, ring, pi);
+            if (G->c.terminated) zero_mask(G, T);
+            else n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
             uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
-                const PlyResult r = env_ply(G, n, A, (uint32_t)g, -1, ring, pi, illegal);
-                count_result(st, r);
+                const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal);
                 const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
-                if (lane == 0) {
+                if (T.leader()) {
+                    count_result(st, r);
                     if (action_ring) action_ring[o] = (int16_t)r.action;
                     if (reward_ring) reward_ring[o] = (int8_t)reward_of(r);
                     if (done_ring) done_ring[o] = (uint8_t)r.code;
                     if (ply_ring) ply_ring[o] = (int16_t)r.ply_idx;
                 }
-                if (mask_ring) write_mask(G, mask_ring + o * kMaskBytes);
+                if (mask_ring) write_mask(G, T, mask_ring + o * kMaskBytes);
             }
-            if (lane < 8) A.stats[8 * (size_t)g + lane] += st[lane];
-            if (lane == 0) G->c.n_legal = (uint16_t)n;
-            store_core(G, A.core + g);
+            if (T.leader()) {
+                uint32_t* gs = A.stats + 8 * (size_t)g;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) gs[k] += st[k];
+                G->c.n_legal = (uint16_t)n;
+            }
+            store_core(G, A.core + g, T);
         }
     }
 }
@@ -259,19 +290,20 @@ __global__ void k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps
 __global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const Team<32> T;
+    SmemGame* G = team_game<32>(smem);
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
     const int g = idx[i];
     if (g < 0 || g >= A.N) {
-        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, i);
+        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, i);
         return;
     }
-    load_core(G, A.core + g);
+    load_core(G, A.core + g, T);
     const uint16_t* ring = A.ring + (size_t)g * kRing;
     st_position* o = out + i;
     uint8_t* ob = reinterpret_cast<uint8_t*>(o);
-    const int lane = lane_id();
+    const int lane = T.tl;
     for (int b = lane; b < 240; b += 32) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
     for (int h = lane; h < 256; h += 32) o->hist[h] = (uint16_t)hist_at(G, ring, h);
     if (lane == 0) {
@@ -290,19 +322,16 @@ __global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* 
     }
 }
 
-}  // namespace
-
-namespace {
-
 __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_position* in)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    SmemGame* G = reinterpret_cast<SmemGame*>(smem) + (threadIdx.x >> 5);
+    const Team<32> T;
+    SmemGame* G = team_game<32>(smem);
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
     const int g = idx[i];
     if (g < 0 || g >= A.N) {
-        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, i);
+        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, i);
         return;
     }
     // keep the episode counter of the slot
@@ -311,15 +340,15 @@ __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_posi
     uint64_t* pi = A.pi + (size_t)g * kPiCap;
     const int bad = import_position(G, in + i, ring, pi);
     if (bad) {
-        if (lane_id() == 0) latch(A.status, ST_ERR_BAD_POSITION, g);
+        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, g);
         return;
     }
-    const int nl = gen_moves(G, G->c.ply & 1, A.R.flags, false, false, ring, pi);
-    if (lane_id() == 0) {
+    const int nl = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
+    if (T.leader()) {
         G->c.episode = episode;
         G->c.n_legal = (uint16_t)nl;
     }
-    store_core(G, A.core + g);
+    store_core(G, A.core + g, T);
 }
 
 EnvArgs env_args(st_env* e)
@@ -337,6 +366,41 @@ struct DeviceGuard {
     explicit DeviceGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
     ~DeviceGuard() { int cur; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
 };
+
+// Dynamic shared memory of one block of the persistent launch.
+size_t run_smem(int wpb, int gpw) { return (size_t)wpb * gpw * sizeof(SmemGame); }
+
+cudaError_t run_occupancy(int wpb, int gpw, int* occ)
+{
+    const size_t smem = run_smem(wpb, gpw);
+    cudaError_t e;
+    if (gpw == 4) {
+        e = cudaFuncSetAttribute(k_env_run<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<8>, 32 * wpb, smem);
+    } else if (gpw == 2) {
+        e = cudaFuncSetAttribute(k_env_run<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<16>, 32 * wpb, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_env_run<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<32>, 32 * wpb, smem);
+    }
+    return e;
+}
+
+void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
+                int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+{
+    const size_t smem = run_smem(e->wpb, e->gpw);
+    if (e->gpw == 4)
+        k_env_run<8><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
+                                                             reward_ring, done_ring, ply_ring, mask_ring);
+    else if (e->gpw == 2)
+        k_env_run<16><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
+                                                              reward_ring, done_ring, ply_ring, mask_ring);
+    else
+        k_env_run<32><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
+                                                              reward_ring, done_ring, ply_ring, mask_ring);
+}
 
 }  // namespace
 
@@ -387,14 +451,12 @@ extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
     const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
     k_env_reset<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, nullptr, nullptr, 1);
     err = cudaGetLastError();
+    if (err == cudaSuccess) err = run_occupancy(e->wpb, e->gpw, &e->max_bps);
     if (err != cudaSuccess) {
-        stg::set_error("st_env_create: reset launch failed: %s", cudaGetErrorString(err));
+        stg::set_error("st_env_create: %s", cudaGetErrorString(err));
         st_env_destroy(e);
         return ST_ERR_CUDA;
     }
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_run, 32 * e->wpb, e->wpb * sizeof(SmemGame));
-    e->max_bps = occ;
     *out = e;
     return ST_OK;
 }
@@ -430,27 +492,27 @@ extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* act
     DeviceGuard guard(e->device);
     EnvArgs a = env_args(e);
     const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
-    k_env_step<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
+    k_env_step<32><<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
         a, actions, action_out, reward_out, done_out, ply_out, mask_out);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
 
 extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32_t blocks_per_sm,
-                                       int32_t games_per_fetch)
+                                       int32_t games_per_warp, int32_t games_per_fetch)
 {
     ST_CHECK_ARG(e, "st_env_set_launch: null env");
-    ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= 32, "st_env_set_launch: warps_per_block 1..32");
+    ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= 16, "st_env_set_launch: warps_per_block 1..16");
     ST_CHECK_ARG(blocks_per_sm >= 0 && blocks_per_sm <= 64, "st_env_set_launch: blocks_per_sm 0..64");
+    ST_CHECK_ARG(games_per_warp == 1 || games_per_warp == 2 || games_per_warp == 4,
+                 "st_env_set_launch: games_per_warp 1, 2 or 4");
     ST_CHECK_ARG(games_per_fetch >= 1 && games_per_fetch <= 4096, "st_env_set_launch: games_per_fetch 1..4096");
     DeviceGuard guard(e->device);
-    const int smem = warps_per_block * (int)sizeof(SmemGame);
-    if (smem > 48 * 1024)
-        ST_CUDA(cudaFuncSetAttribute(k_env_run, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
-    ST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_run, 32 * warps_per_block, smem));
+    ST_CUDA(run_occupancy(warps_per_block, games_per_warp, &occ));
     ST_CHECK_ARG(occ >= 1, "st_env_set_launch: %d warps per block do not fit on an SM", warps_per_block);
     e->wpb = warps_per_block;
+    e->gpw = games_per_warp;
     e->max_bps = occ;
     e->bps = blocks_per_sm == 0 ? occ : std::min(blocks_per_sm, occ);
     e->gpf = games_per_fetch;
@@ -468,9 +530,10 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
     if (n_steps == 0) return ST_OK;
     DeviceGuard guard(e->device);
     const int bps = e->bps > 0 ? e->bps : std::max(1, e->max_bps);
-    const int64_t key[10] = {n_steps, ring_steps, (int64_t)action_ring, (int64_t)reward_ring, (int64_t)done_ring,
-                             (int64_t)ply_ring, (int64_t)mask_ring, e->wpb, bps, e->gpf};
-    const int blocks = std::max(1, std::min(e->sms * bps, (e->N + e->wpb - 1) / e->wpb));
+    const int64_t key[11] = {n_steps, ring_steps, (int64_t)action_ring, (int64_t)reward_ring, (int64_t)done_ring,
+                             (int64_t)ply_ring, (int64_t)mask_ring, e->wpb, bps, e->gpf, e->gpw};
+    const int per_block = e->wpb * e->gpw;
+    const int blocks = std::max(1, std::min(e->sms * bps, (e->N + per_block - 1) / per_block));
     EnvArgs a = env_args(e);
     // A non-default stream gets the launch pair (queue reset + persistent
     // kernel) captured once into a CUDA graph and replayed afterwards.
@@ -483,8 +546,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         cudaGraph_t graph = nullptr;
         ST_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream);
-        k_env_run<<<blocks, 32 * e->wpb, e->wpb * sizeof(SmemGame), e->stream>>>(
-            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+        launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
         const cudaError_t launch_err = cudaGetLastError();
         const cudaError_t cap_err = cudaStreamEndCapture(e->stream, &graph);
         if (launch_err != cudaSuccess || cap_err != cudaSuccess) {
@@ -505,8 +567,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         return ST_OK;
     }
     ST_CUDA(cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream));
-    k_env_run<<<blocks, 32 * e->wpb, e->wpb * sizeof(SmemGame), e->stream>>>(
-        a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

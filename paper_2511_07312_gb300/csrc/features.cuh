@@ -70,7 +70,7 @@ __device__ __forceinline__ bool move_legal(const SmemGame* G, int a, uint32_t ru
     if ((rule_flags & kTwoSquare) && G->c.ts_pid[P] == X && G->c.ts_len[P] == 4 && two_square_blocks(G, P, to))
         return false;
     if ((rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0 && occ == kEmpty) {
-        const PlyCtx x = make_ctx(G, ring);
+        const PlyCtx x = make_ctx(G);
         if (chase_blocks(G, x, pi, P, X, from, to)) return false;
     }
     return true;
@@ -81,7 +81,7 @@ __device__ __forceinline__ bool move_legal(const SmemGame* G, int a, uint32_t ru
 __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, int a, uint32_t rule_flags,
                                                 const uint16_t* ring)
 {
-    const int lane = lane_id();
+    const int lane = threadIdx.x & 31;
     const int P = G->c.ply & 1;
     const int from = a / 100, to = a - 100 * (a / 100);
     const int X = G->board[from];
@@ -106,9 +106,9 @@ __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, 
         }
         F->a[pid] |= bits;
     }
-    __syncwarp();
+    __syncwarp(0xFFFFFFFFu);
     if (lane == 0 && !battle) {
-        const PlyCtx x = make_ctx(G, ring);
+        const PlyCtx x = make_ctx(G);
         const int ap = x.prev_to;
         if (ap >= 0 && x.prev_nb && enemy_of(G->board[ap], P)) {
             const int A = G->board[ap];
@@ -146,13 +146,13 @@ __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, 
             }
         }
     }
-    __syncwarp();
+    __syncwarp(0xFFFFFFFFu);
 }
 
 // Threats made by the move just applied (a = from*100+to); call after apply_move.
 __device__ __forceinline__ void features_after(const SmemGame* G, FeatSmem* F, int a, bool battle)
 {
-    if (lane_id() == 0 && !battle) {
+    if ((threadIdx.x & 31) == 0 && !battle) {
         const int to = a - 100 * (a / 100);
         const int X = G->board[to];
         const int P = X / 40;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void features_after(const SmemGame* G, FeatSmem* F, i
         if (c < 9 && enemy_of(G->board[to + 1], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to + 1]));
         F->a[X] |= bits;
     }
-    __syncwarp();
+    __syncwarp(0xFFFFFFFFu);
 }
 
 }  // namespace stg

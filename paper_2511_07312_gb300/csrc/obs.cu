@@ -118,7 +118,7 @@ __global__ void k_replay(ReplayArgs A)
             const uint8_t* setup = A.setups + 80 * (size_t)gi;
             ok = setup_ok(setup);
             if (ok) {
-                reset_game(G, 0, 0, 0, 0, setup);
+                reset_game(G, Team<32>(), 0, 0, 0, 0, setup);
                 for (int k = lane; k < kPieces; k += 32) { S->f.a[k] = 0; S->f.b[k] = 0; }
                 __syncwarp();
                 cur_game = gi;
@@ -138,7 +138,7 @@ __global__ void k_replay(ReplayArgs A)
                 if (!move_legal(G, a, A.R.flags, S->ring, S->pi)) { ok = false; break; }
                 const bool battle = G->board[a - 100 * (a / 100)] != kEmpty;
                 if (track) features_before(G, &S->f, a, A.R.flags, S->ring);
-                apply_move(G, a, S->ring, S->pi);
+                apply_move(G, Team<32>(), a, S->ring, S->pi);
                 if (track) features_after(G, &S->f, a, battle);
                 ++cur_ply;
             }
@@ -159,7 +159,7 @@ __global__ void k_replay(ReplayArgs A)
             for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
         }
         if (A.mask_out) {
-            gen_moves(G, G->c.ply & 1, A.R.flags, false, true, S->ring, S->pi);
+            gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi);
             const uint4* src = reinterpret_cast<const uint4*>(G->mask);
             uint4* d = reinterpret_cast<uint4*>(A.mask_out + (size_t)i * kMaskBytes);
             for (int k = lane; k < kMaskBytes / 16; k += 32) d[k] = src[k];

@@ -162,14 +162,16 @@ __device__ inline int rollout_one(RolloutSmem* S, const RootState* R, const uint
     __syncwarp();
     for (int i = lane; i < 40; i += 32) G->c.type[opp * 40 + i] = S->types[i];
     __syncwarp();
-    int n = gen_moves(G, searcher, Rl.flags, false, true, S->ring, S->pi);
+    const Team<32> T;
+    derive_state(G, S->ring, T);   // bitboards and flag ids of the sampled types
+    int n = gen_moves(G, T, searcher, Rl.flags, false, true, S->pi);
     int code = 0, winner = -1;
-    if (n == 0) start_end(G, Rl, S->ring, S->pi, code, winner);
+    if (n == 0) start_end(G, T, Rl, S->pi, code, winner);
     for (int d = 0; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
-        const int a = select_action(G, uniform_below(w.x, (uint32_t)n));
-        apply_move(G, a, S->ring, S->pi);
-        check_end(G, Rl, S->ring, S->pi, code, winner, n);
+        const int a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
+        apply_move(G, T, a, S->ring, S->pi);
+        check_end(G, T, Rl, S->pi, code, winner, n);
     }
     return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
 }

@@ -7,15 +7,16 @@
 
 namespace stg {
 
-// Shared by the env and the stateless search kernels: read and validate a
-// snapshot into G (board built, hash and chase positions rebuilt), writing
-// the history ring and chase store.  Returns 0 when valid.
-static __device__ __noinline__ int import_position(SmemGame* G, const st_position* in, uint16_t* ring, uint64_t* pi)
+// Warp (team of 32): read and validate snapshot `in` into G -- board, hash,
+// derived bitboards, history ring and chase positions rebuilt -- writing
+// this game's history ring and chase store.  Returns 0 when valid.
+__device__ __forceinline__ int import_position(SmemGame* G, const st_position* in, uint16_t* ring, uint64_t* pi)
 {
-    const int lane = lane_id();
+    const Team<32> T;
+    const int lane = T.tl;
     const uint8_t* ib = reinterpret_cast<const uint8_t*>(in);
     for (int b = lane; b < 240; b += 32) reinterpret_cast<uint8_t*>(&G->c)[b] = ib[b];
-    __syncwarp();
+    T.sync();
     int bad = 0;
     if (lane == 0) {
         GameCore& c = G->c;
@@ -53,11 +54,11 @@ static __device__ __noinline__ int import_position(SmemGame* G, const st_positio
         c.terminated = 0;
         c.n_pi = 0;
     }
-    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
+    bad = T.shfl(bad, 0);
     if (bad) return bad;
     // board, checking that no two alive pieces share a square
     for (int s = lane; s < 112; s += 32) G->board[s] = (s < 100 && is_lake(s)) ? kLake : kEmpty;
-    __syncwarp();
+    T.sync();
     if (lane == 0) {
         for (int p = 0; p < 80 && !bad; ++p) {
             if (!(G->c.flags[p] & 1)) continue;
@@ -65,13 +66,13 @@ static __device__ __noinline__ int import_position(SmemGame* G, const st_positio
             else G->board[G->c.sq[p]] = (uint8_t)p;
         }
     }
-    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
+    bad = T.shfl(bad, 0);
     if (bad) return bad;
     const int ply = G->c.ply;
     for (int h = lane; h < kRing; h += 32)
         if (h < ply) ring[(ply - 1 - h) & (kRing - 1)] = in->hist[h];
-    const uint64_t hash = board_hash(G);
-    __syncwarp();
+    const uint64_t hash = board_hash(G, T);
+    T.sync();
     if (lane == 0) {
         G->c.hash = hash;
         // chase positions: undo the chase plies from the current board,
@@ -103,10 +104,11 @@ static __device__ __noinline__ int import_position(SmemGame* G, const st_positio
             }
         }
     }
-    bad = __shfl_sync(0xFFFFFFFFu, bad, 0);
-    __syncwarp();
-    return bad;
+    bad = T.shfl(bad, 0);
+    T.sync();
+    if (bad) return bad;
+    derive_state(G, ring, T);
+    return 0;
 }
-
 
 }  // namespace stg

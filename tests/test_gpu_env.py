@@ -57,8 +57,10 @@ def test_plain_step_config1_bit_exact():
     np.testing.assert_array_equal(stats, ref["stats"].astype(np.int32))
 
 
-def test_persistent_run_matches_plain_and_oracle():
+@pytest.mark.parametrize("gpw", [1, 2, 4])
+def test_persistent_run_matches_plain_and_oracle(gpw):
     env = st.Env(64, seed=1)
+    env.set_launch(4, 0, 1, games_per_warp=gpw)
     out = env.run(1000)
     env.stream.synchronize()
     gpu = {k: v.cpu().numpy() for k, v in out.items()}
@@ -66,12 +68,13 @@ def test_persistent_run_matches_plain_and_oracle():
     _compare(gpu, ref)
 
 
-@pytest.mark.parametrize("wpb,gpf", [(1, 1), (4, 3), (8, 1), (16, 7)])
-def test_persistent_launch_shapes_ragged(wpb, gpf):
+@pytest.mark.parametrize("wpb,gpf,gpw", [(1, 1, 1), (4, 3, 1), (8, 1, 1), (16, 7, 1), (1, 1, 2), (4, 3, 2),
+                                         (8, 1, 2), (16, 5, 2), (1, 1, 4), (4, 3, 4), (8, 1, 4), (16, 2, 4)])
+def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
     # 1,000 slots (not a multiple of any block), 300 plies, ring of 7 rows
     N, S, R = 1000, 300, 7
     env = st.Env(N, seed=5)
-    env.set_launch(wpb, 0, gpf)
+    env.set_launch(wpb, 0, gpf, games_per_warp=gpw)
     out = env.run(S, R)
     env.stream.synchronize()
     gpu = {k: v.cpu().numpy() for k, v in out.items()}
@@ -89,6 +92,35 @@ def test_persistent_launch_shapes_ragged(wpb, gpf):
     for s in slots:
         r = oracle.env_run(5, 1, S, slot0=int(s), want_mask=False)
         np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
+
+
+def test_full_size_65536_games_2000_plies_sampled_slots():
+    # the benchmark workload in the benchmark's launch shape: 65,536 slots,
+    # 2,000 plies in one persistent launch, a 16-row ring; sampled slots are
+    # checked against the oracle (counters, final snapshot, last 16 plies)
+    from paper_2511_07312_gb300 import autotune
+    N, S, R = 65536, 2000, 16
+    best = autotune.tune(N)
+    env = st.Env(N, seed=1)
+    env.set_launch(best["warps_per_block"], 0, best["games_per_fetch"], games_per_warp=best["games_per_warp"])
+    out = env.run(S, R)
+    env.sync()
+    stats = _np(env.stats())
+    slots = np.array([0, 1, 151, 152, 4095, 4096, 32767, 32768, 65534, 65535] +
+                     list(np.random.default_rng(0).integers(0, N, 22)))
+    pos = env.export(torch.from_numpy(slots).to(torch.int32))
+    env.sync()
+    pos = pos.cpu().numpy()
+    ring = {k: v.cpu().numpy() for k, v in out.items()}
+    assert (stats[:, 5] <= S).all() and stats[:, 5].sum() > 0.99 * N * S
+    for j, s in enumerate(slots):
+        r = oracle.env_run(1, 1, S, slot0=int(s), want_final=True)
+        np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
+        np.testing.assert_array_equal(pos[j], r["final"][0])
+        for row in range(S - R, S):
+            for k in ("action", "reward", "done", "ply"):
+                assert ring[k][row % R, s] == r[k][row, 0], (k, s, row)
+            assert np.array_equal(ring["mask"][row % R, s], r["mask"][row, 0]), ("mask", s, row)
 
 
 def test_supplied_actions_and_illegal_action_latch():
