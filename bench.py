@@ -118,6 +118,37 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources_sha256():
+    import glob
+    import hashlib
+    root = os.path.join(ROOT, "paper_2511_07312_gb300", "csrc")
+    h = hashlib.sha256()
+    files = glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh")) + \
+        glob.glob(os.path.join(root, "*.h"))
+    for f in sorted(files):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic_per_env_step():
+    """DRAM bytes per env-step of the step kernel from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "k_env_run_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        parts = line.strip().split(":", 1)
+        if len(parts) == 2 and parts[0] in ("sources_sha256", "traffic_bytes_per_env_step"):
+            vals[parts[0]] = parts[1].strip()
+    if vals.get("sources_sha256") != kernel_sources_sha256() or "traffic_bytes_per_env_step" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_env_step"])
+
+
 # ---------------------------------------------------------------- oracle on the host
 
 def oracle_env_rate(seed, plies, budget_s=12.0, chunk=64):
@@ -298,14 +329,18 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
                 "data": "synthetic",
                 "config": {"workload": "65,536 random-policy Stratego games, auto-reset, 2,000 plies per slot "
-                                       "per step (configs[1])",
+                                       "per step",
                            "games_per_gpu": N, "plies_per_step": S, "ring_rows": R,
                            "l2": "output ring %.2f GB > L2 (inputs larger than L2, no flush)" %
                                  (R * N * MASK_BYTES / 1e9),
                            "launch": {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
                                       "chosen_by": "autotuner" if tuned else "command line"}},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak,
+                             "traffic": (None if measured_traffic_per_env_step() is None
+                                         else measured_traffic_per_env_step() * float(N) * S),
+                             "traffic_note": "ncu dram__bytes_read.sum+dram__bytes_write.sum per launch, scaled "
+                                             "from a 16,384 x 100 capture (profiles/k_env_run_traffic.md)",
                              "peak_kind": peak_kind + " hbm_gbs (copy, burst)",
                              "algorithmic_bytes_per_env_step": BYTES_PER_ENV_STEP, "kernel": "k_env_run"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
@@ -317,10 +352,11 @@ def main():
 
 
 def secondary(st, torch, dev, args):
-    """Configs 3 and 4: observation planes and belief-sample rollouts."""
+    """Observation planes of 16,384 replayed positions, belief-sample
+    rollouts of 4,096 positions, and the serving workload."""
     import numpy as np
     out = {}
-    # config 1 trajectories, played on the GPU: 64 games to their end
+    # 64 random-policy games (seed 1) played on the GPU to their end or the 1,000-ply cap
     G = 64
     env = st.Env(G, seed=1, autoreset=False, device=dev.index)
     setups = env.export(torch.arange(G))[:, :80].contiguous()
@@ -350,7 +386,7 @@ def secondary(st, torch, dev, args):
     byts = B * (487 * 100 * 3 + MASK_BYTES)
     out["obs_encode"] = {"positions_per_s": B / (ms / 1000), "ms": ms, "GB_per_s_written": byts / (ms / 1000) / 1e9,
                          "positions": B, "bytes_written_per_position": 487 * 100 * 3 + MASK_BYTES}
-    # config 4: 4,096 positions x 256 samples x depth 32
+    # belief-sample rollouts: 4,096 positions x 256 samples x depth 32
     P, K, D = 4096, 256, 32
     sel = np.linspace(0, B - 1, P).astype(np.int64)
     pos, status = st.replay_positions(setups, acts, gi[sel].contiguous(), pl[sel].contiguous())
@@ -373,8 +409,8 @@ def secondary(st, torch, dev, args):
 
 
 def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0):
-    """Config 5: Poisson arrivals (mean 2,000/s) of search requests, K ~
-    U{16..1024}, depth ~ U{8..64}, from replayed config-1 positions; the
+    """Serving: Poisson arrivals (mean 2,000/s) of search requests, K ~
+    U{16..1024}, depth ~ U{8..64}, from positions of the 64 replayed games; the
     continuous-batching server against one launch + sync per request."""
     import numpy as np
     rng = np.random.default_rng(5)

@@ -47,7 +47,7 @@ def _compare(gpu, ref, slots=None, steps=None):
         assert mism.size == 0, "mask differs first at (step, slot) %s" % (mism[0],)
 
 
-def test_plain_step_config1_bit_exact():
+def test_plain_step_64_games_1000_plies_bit_exact():
     # 64 games, seed 1, to the end or the 1000-ply cap, auto-reset afterwards
     env = st.Env(64, seed=1)
     gpu = _plain_steps(env, 1000)
