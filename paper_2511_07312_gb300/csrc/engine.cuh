@@ -42,6 +42,7 @@ constexpr uint8_t kNone = 0xFF;
 constexpr int kMaskBytes = 1264;
 constexpr int kMaskWordsAlloc = 384;   // 316 used by the output layout, the rest kept zero (96 uint4 = 3 or 6 per lane)
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
+constexpr int kPiWords = 2 * kPiCap;   // each: hash of the chaser's pieces, hash of the chased side's pieces
 constexpr int kRing = 256;             // moves of history per game
 constexpr uint32_t kLakeRow = 0xCCu;   // columns 2,3,6,7 of rows 4 and 5
 constexpr uint32_t kLakeCol = 0x30u;   // rows 4,5 of columns 2,3,6,7
@@ -76,8 +77,7 @@ struct __align__(16) GameCore {
     uint16_t n_legal;
     uint32_t episode;
     uint32_t pad1;
-    uint64_t hash;          // XOR of zkey(pid, square) over alive pieces
-    uint64_t pad2;
+    uint64_t hash_side[2];  // per side: XOR of zkey(pid, square) over its alive pieces
 };
 static_assert(sizeof(GameCore) == 288, "GameCore layout");
 
@@ -90,7 +90,8 @@ struct __align__(16) SmemGame {
     uint16_t colocc[10];      // all pieces in column c (bit = row)
     uint16_t h0, h1;          // actions played 1 and 2 plies ago (0xFFFF none)
     uint8_t flag_pid[2];
-    uint8_t pad[14];
+    uint8_t row_cnt[10];      // moves per from-row in G->mask (written with the mask)
+    uint8_t pad[4];
     uint32_t mask[kMaskWordsAlloc];
 };
 static_assert(sizeof(SmemGame) == 288 + 112 + 120 + 20 + 4 + 2 + 14 + 4 * kMaskWordsAlloc, "SmemGame layout");
@@ -217,8 +218,11 @@ __device__ __forceinline__ int hist_at(const SmemGame* G, const uint16_t* ring, 
 // Everything derived from the core and the board: row and column bitboards,
 // flag ids, the last two moves.  Needs G->board.
 template <int L>
-__device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, const Team<L>& T)
+__device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, Team<L>)
 {
+    // out-of-line engine functions rebuild the team from the lane id rather
+    // than reading the caller's copy through memory
+    const Team<L> T;
     for (int r = T.tl; r < 10; r += L) {
         uint32_t o0 = 0, o1 = 0, m0 = 0, m1 = 0, s0 = 0, s1 = 0, col = 0;
         for (int c = 0; c < 10; ++c) {
@@ -256,12 +260,15 @@ __device__ __forceinline__ void build_board(SmemGame* G, const Team<L>& T)
     T.sync();
 }
 
+// Hash of the alive pieces of `side` (pieces 40*side .. 40*side+39).
 template <int L>
-__device__ __forceinline__ uint64_t board_hash(const SmemGame* G, const Team<L>& T)
+__device__ __forceinline__ uint64_t side_hash(const SmemGame* G, const Team<L>& T, int side)
 {
     uint64_t h = 0;
-    for (int p = T.tl; p < kPieces; p += L)
+    for (int k = T.tl; k < 40; k += L) {
+        const int p = 40 * side + k;
         if (G->c.flags[p] & 1) h ^= zkey(p, G->c.sq[p]);
+    }
     return T.xor64(h);
 }
 
@@ -321,16 +328,33 @@ __device__ __forceinline__ bool two_square_blocks(const SmemGame* G, int P, int 
     return lo < hi;
 }
 
+// Would P's move of `pid` recreate a position reached after one of P's
+// threats in the current chase?  Chase positions are stored as (hash of the
+// chaser's pieces, hash of the chased side's pieces).
 __device__ __forceinline__ bool chase_blocks(const SmemGame* G, const PlyCtx& x, const uint64_t* pi, int P,
                                              int pid, int from, int to)
 {
     if (classify(G, x, P, from, to) != kClThreat) return false;
     if (from == x.h1_to && to == x.h1_from) return false;
-    const uint64_t h = G->c.hash ^ zkey(pid, from) ^ zkey(pid, to);
+    const uint64_t mine = G->c.hash_side[P] ^ zkey(pid, from) ^ zkey(pid, to);
+    const uint64_t theirs = G->c.hash_side[1 - P];
     const int n = G->c.n_pi;
     for (int i = 0; i < n; ++i)
-        if (pi[i] == h) return true;
+        if (pi[2 * i] == mine && pi[2 * i + 1] == theirs) return true;
     return false;
+}
+
+// Can any of P's moves be chase-blocked?  A move of P changes only P's
+// pieces, so a stored chase position can be recreated only if the chased
+// side's pieces stand exactly where they stood then.  Team-uniform.
+template <int L>
+__device__ __forceinline__ bool chase_live(const SmemGame* G, const Team<L>& T, const uint64_t* pi, int P)
+{
+    const uint64_t theirs = G->c.hash_side[1 - P];
+    const int n = G->c.n_pi;
+    bool hit = false;
+    for (int i = T.tl; i < n; i += L) hit |= pi[2 * i + 1] == theirs;
+    return T.any(hit);
 }
 
 // 128-bit sets over to-squares, kept in registers as two 64-bit halves.
@@ -420,9 +444,10 @@ __device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d)
 // two-square and chasing rules filter as rule_flags says.  Team-uniform
 // result.
 template <int L>
-__device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint32_t rule_flags, bool physical,
+__device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule_flags, bool physical,
                                       bool write_mask, const uint64_t* pi)
 {
+    const Team<L> T;
     if (write_mask) {
         uint4* m4 = reinterpret_cast<uint4*>(G->mask);
         for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
@@ -431,11 +456,13 @@ __device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint
     const bool ts_on = !physical && (rule_flags & kTwoSquare) && ts_pid != kNone && G->c.ts_len[P] == 4 &&
                        (G->c.flags[ts_pid] & 1);
     const int ts_from = ts_on ? G->c.sq[ts_pid] : -1;
-    const bool chase_on = !physical && (rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0;
+    const bool chase_on = !physical && (rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0 &&
+                          chase_live(G, T, pi, P);
     const PlyCtx x = make_ctx(G);
     T.sync();   // mask zeroed before any atomic
     int cnt = 0;
     for (int r = T.tl; r < 10; r += L) {
+        const int cnt_before_row = cnt;
         const uint32_t own = G->occ[P][r], enm = G->occ[1 - P][r], mv = G->mov[P][r];
         uint32_t sc = G->sco[P][r];
         const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
@@ -449,8 +476,23 @@ __device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint
         const uint32_t FN = mv & fre_up;
         const uint32_t FS = mv & fre_dn;
         uint32_t moving = FE | FW | FN | FS;
-        if (!ts_on && !chase_on) {
-            cnt += __popc(FE) + __popc(FW) + __popc(FN) + __popc(FS);
+        if (!chase_on) {
+            // the piece under the two-square rule (if on this row) is the
+            // only one whose destinations need a filter
+            const uint32_t ts_bit = (ts_on && ts_from / 10 == r) ? (1u << (ts_from % 10)) : 0u;
+            if (moving & ts_bit) {
+                const int c = ts_from % 10, s = ts_from;
+                Set128 d{0ull, 0ull};
+                if ((FS >> c) & 1u) d = or128(d, bit128(s - 10));
+                if ((FW >> c) & 1u) d = or128(d, bit128(s - 1));
+                if ((FE >> c) & 1u) d = or128(d, bit128(s + 1));
+                if ((FN >> c) & 1u) d = or128(d, bit128(s + 10));
+                d = filter_dests(G, P, s, true, false, x, pi, d);
+                cnt += popc128(d);
+                if (write_mask) or_row(G->mask, s, d);
+                moving &= ~ts_bit;
+            }
+            cnt += __popc(FE & ~ts_bit) + __popc(FW & ~ts_bit) + __popc(FN & ~ts_bit) + __popc(FS & ~ts_bit);
             if (write_mask) {
                 while (moving) {
                     const int c = __ffs(moving) - 1;
@@ -508,7 +550,7 @@ __device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint
             const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
             const int nd = runE + capE + runW + capW + runN + capN + runS + capS;
             if (nd == 0) continue;
-            if (ts_on || chase_on) {
+            if (chase_on || s == ts_from) {
                 Set128 d = or128(range128(s + 1, runE + capE), range128(s - runW - capW, runW + capW));
                 d = or128(d, column128(c, r + 1, r + runN + capN));
                 d = or128(d, column128(c, r - runS - capS, r - 1));
@@ -545,27 +587,43 @@ __device__ __noinline__ int gen_moves(SmemGame* G, const Team<L>& T, int P, uint
                 }
             }
         }
+        if (write_mask) G->row_cnt[r] = (uint8_t)(cnt - cnt_before_row);
     }
     const int total = T.sum(cnt);
     T.sync();
     return total;
 }
 
-// The idx-th set bit (ascending) of G->mask; team-uniform result.
+// The idx-th set bit (ascending) of G->mask; team-uniform result.  Board
+// row r's from-squares own the consecutive actions [1000r, 1000r+1000), so
+// the per-row counts written with the mask pick the row first and only that
+// row's 32-33 mask words are scanned.
 template <int L>
-__device__ __forceinline__ int select_action(const SmemGame* G, const Team<L>& T, uint32_t idx)
+__device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
 {
-    constexpr int W = kMaskWordsAlloc / L;   // words per lane: 12 or 24
-    static_assert(W % 4 == 0, "whole uint4 per lane");
+    const Team<L> T;
+    int local = (int)idx, row = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const int c = G->row_cnt[r];
+        if (row == r && local >= c) { local -= c; row = r + 1; }
+    }
+    row = min(row, 9);
+    const int b0 = 1000 * row, b1 = b0 + 1000;           // the row's bits: [b0, b1)
+    const int w0 = b0 >> 5, w1 = (b1 - 1) >> 5;           // its words, inclusive
+    const int nw = w1 - w0 + 1;                            // 32 or 33
+    constexpr int C = (33 + L - 1) / L;                    // words per lane
     const int t = T.tl;
-    const uint4* m4 = reinterpret_cast<const uint4*>(G->mask) + t * (W / 4);
-    uint32_t c4[W / 4];
+    uint32_t w[C];
     int cnt = 0;
 #pragma unroll
-    for (int k = 0; k < W / 4; ++k) {
-        const uint4 v = m4[k];
-        c4[k] = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        cnt += c4[k];
+    for (int j = 0; j < C; ++j) {
+        const int wi = t * C + j;
+        uint32_t v = wi < nw ? G->mask[w0 + wi] : 0u;
+        if (wi == 0) v &= ~0u << (b0 & 31);                             // bits of the previous row
+        if (wi == nw - 1 && (b1 & 31)) v &= (1u << (b1 & 31)) - 1u;     // bits of the next row
+        w[j] = v;
+        cnt += __popc(v);
     }
     int incl = cnt;
 #pragma unroll
@@ -574,25 +632,21 @@ __device__ __forceinline__ int select_action(const SmemGame* G, const Team<L>& T
         if (t >= o) incl += v;
     }
     const int excl = incl - cnt;
-    const uint32_t own = T.ballot((int)idx >= excl && (int)idx < incl);
+    const uint32_t own = T.ballot(local >= excl && local < incl);
     int a = -1;
     if (own & (1u << t)) {
-        int local = (int)idx - excl;
-        int k = 0;
+        int k = local - excl;
+        int j = 0;
 #pragma unroll
-        for (int j = 0; j < W / 4; ++j)
-            if (k == j && local >= (int)c4[j]) { local -= c4[j]; k = j + 1; }
-        k = min(k, W / 4 - 1);
-        const uint4 v = m4[k];
-        const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
-        int wi = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = __popc(ws[j]);
-            if (wi == j && local >= cj) { local -= cj; wi = j + 1; }
+        for (int i = 0; i < C; ++i) {
+            const int ci = __popc(w[i]);
+            if (j == i && k >= ci) { k -= ci; j = i + 1; }
         }
-        wi = min(wi, 3);
-        a = ((t * (W / 4) + k) * 4 + wi) * 32 + nth_set_bit(ws[wi], local);
+        j = min(j, C - 1);
+        uint32_t wj = w[0];
+#pragma unroll
+        for (int i = 1; i < C; ++i) if (j == i) wj = w[i];
+        a = (w0 + t * C + j) * 32 + nth_set_bit(wj, k);
     }
     return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
@@ -612,8 +666,9 @@ __device__ __forceinline__ bool flag_dead(const SmemGame* G, int side)
 // Plays action a for the player to move.  ring/pi: this game's history ring
 // and chase-position store.
 template <int L>
-__device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, uint16_t* ring, uint64_t* pi)
+__device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* ring, uint64_t* pi)
 {
+    const Team<L> T;
     if (T.leader() && a >= 0 && a < 10000) {
         const PlyCtx x = make_ctx(G);
         GameCore& c = G->c;
@@ -627,7 +682,8 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
         if (dist > 1) fx |= 8;
         fx |= 4;
         const bool battle = G->board[to] != kEmpty;
-        uint64_t h = c.hash ^ zkey(X, from);
+        uint64_t h = c.hash_side[P] ^ zkey(X, from);   // mover's pieces
+        uint64_t hq = c.hash_side[1 - P];               // the other side's pieces
         int D = -1;
         bool d_died = false, x_alive = true;
         const int tX = c.type[X];
@@ -659,7 +715,8 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
                 d_died = true;
                 G->board[to] = (uint8_t)X;
                 c.sq[X] = (uint8_t)to;
-                h ^= zkey(D, to) ^ zkey(X, to);
+                h ^= zkey(X, to);
+                hq ^= zkey(D, to);
             } else if (out == 2) {
                 fx = (uint8_t)((fx & 0x0E) | ((d_rev ? 1 : 3) << 4));
                 c.sq[X] = (uint8_t)to;
@@ -671,7 +728,7 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
                 d_died = true;
                 x_alive = false;
                 G->board[to] = kEmpty;
-                h ^= zkey(D, to);
+                hq ^= zkey(D, to);
             }
             c.flags[D] = fd;
             if (d_died) {
@@ -688,7 +745,8 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
         if (G->board[to] != kEmpty) G->colocc[ct] |= (uint16_t)(1u << rt);
         else G->colocc[ct] &= (uint16_t)~(1u << rt);
         c.flags[X] = fx;
-        c.hash = h;
+        c.hash_side[P] = h;
+        c.hash_side[1 - P] = hq;
         const int ply_before = c.ply;
         c.battleless = battle ? 0 : (int16_t)(c.battleless + 1);
         c.last_battle = battle ? 1 : 0;
@@ -717,7 +775,7 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
         // chase state
         if (cls == kClThreat) {
             if (c.chaser != P) { c.chaser = (uint8_t)P; c.n_pi = 0; c.chase_plies = 0; }
-            if (c.n_pi < kPiCap) { pi[c.n_pi] = h; c.n_pi += 1; }
+            if (c.n_pi < kPiCap) { pi[2 * c.n_pi] = h; pi[2 * c.n_pi + 1] = hq; c.n_pi += 1; }
             c.chase_plies += 1;
         } else if (cls == kClEvade && c.chaser == 1 - P) {
             c.chase_plies += 1;
@@ -735,9 +793,10 @@ __device__ __noinline__ void apply_move(SmemGame* G, const Team<L>& T, int a, ui
 // setup: custom types per piece id, or nullptr for the Philox setup of
 // (slot, episode).
 template <int L>
-__device__ __noinline__ void reset_game(SmemGame* G, const Team<L>& T, uint32_t k0, uint32_t k1, uint32_t slot,
+__device__ __noinline__ void reset_game(SmemGame* G, Team<L>, uint32_t k0, uint32_t k1, uint32_t slot,
                                         uint32_t episode, const uint8_t* setup)
 {
+    const Team<L> T;
     for (int p = T.tl; p < kPieces; p += L) {
         G->c.type[p] = setup ? setup[p] : sorted_type(p % 40);
         G->c.sq[p] = (uint8_t)start_square(p);
@@ -768,8 +827,8 @@ __device__ __noinline__ void reset_game(SmemGame* G, const Team<L>& T, uint32_t 
         c.terminated = 0; c.episode = episode; c.n_legal = 0;
     }
     T.sync();
-    const uint64_t h = board_hash(G, T);
-    if (T.leader()) G->c.hash = h;
+    const uint64_t h0 = side_hash(G, T, 0), h1 = side_hash(G, T, 1);
+    if (T.leader()) { G->c.hash_side[0] = h0; G->c.hash_side[1] = h1; }
     build_board(G, T);
     derive_state(G, (const uint16_t*)nullptr, T);
 }

@@ -180,7 +180,7 @@ __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* whi
     }
     if (first && T.tl < 8) A.stats[8 * (size_t)g + T.tl] = 0;
     reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
-    const int n = gen_moves(G, T, 0, A.R.flags, false, false, A.pi + (size_t)g * kPiCap);
+    const int n = gen_moves(G, T, 0, A.R.flags, false, false, A.pi + (size_t)g * kPiWords);
     if (T.leader()) G->c.n_legal = (uint16_t)n;
     store_core(G, A.core + g, T);
 }
@@ -195,7 +195,7 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     const int g = blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
     if (g >= A.N) return;
     uint16_t* ring = A.ring + (size_t)g * kRing;
-    uint64_t* pi = A.pi + (size_t)g * kPiCap;
+    uint64_t* pi = A.pi + (size_t)g * kPiWords;
     load_core(G, A.core + g, T);
     build_board(G, T);
     derive_state(G, ring, T);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(512, ST_RUN_MIN_BLOCKS) k_env_run(EnvArgs A, i
             const int g = first + gi;
             if (g >= A.N) break;
             uint16_t* ring = A.ring + (size_t)g * kRing;
-            uint64_t* pi = A.pi + (size_t)g * kPiCap;
+            uint64_t* pi = A.pi + (size_t)g * kPiWords;
             load_core(G, A.core + g, T);
             build_board(G, T);
             derive_state(G, ring, T);
@@ -337,7 +337,7 @@ __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_posi
     // keep the episode counter of the slot
     const uint32_t episode = A.core[g].episode;
     uint16_t* ring = A.ring + (size_t)g * kRing;
-    uint64_t* pi = A.pi + (size_t)g * kPiCap;
+    uint64_t* pi = A.pi + (size_t)g * kPiWords;
     const int bad = import_position(G, in + i, ring, pi);
     if (bad) {
         if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, g);
@@ -428,7 +428,7 @@ extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
     cudaError_t err = cudaSuccess;
     err = cudaMalloc(&e->core, N * sizeof(GameCore));
     if (err == cudaSuccess) err = cudaMalloc(&e->ring, N * kRing * sizeof(uint16_t));
-    if (err == cudaSuccess) err = cudaMalloc(&e->pi, N * kPiCap * sizeof(uint64_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->pi, N * kPiWords * sizeof(uint64_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->stats, N * 8 * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->status, 2 * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->queue, sizeof(int32_t));

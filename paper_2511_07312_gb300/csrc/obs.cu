@@ -37,7 +37,7 @@ static_assert(sizeof(ItemState) == 288 + 64 + 1280, "ItemState layout");
 struct __align__(16) ReplaySmem {
     SmemGame g;
     FeatSmem f;
-    uint64_t pi[kPiCap];
+    uint64_t pi[kPiWords];
     uint16_t ring[kRing];
 };
 
@@ -362,7 +362,7 @@ ReplayArgs replay_args(const uint8_t* setups, const int16_t* actions, int32_t lo
     return a;
 }
 
-int g_items_per_warp = 4;
+int g_items_per_warp = 8;   // fastest measured on GB300 for 16,384 items of 64 logs
 
 }  // namespace
 

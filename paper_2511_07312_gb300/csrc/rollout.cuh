@@ -101,7 +101,7 @@ __device__ inline void draw_sample(const BeliefPlan* B, uint32_t k0, uint32_t k1
 struct __align__(16) RootState {
     GameCore c;
     uint8_t board[112];
-    uint64_t pi[kPiCap];
+    uint64_t pi[kPiWords];
     uint16_t ring[kRing];
     BeliefPlan plan;
     int32_t bad;
@@ -110,7 +110,7 @@ struct __align__(16) RootState {
 
 struct __align__(16) RolloutSmem {
     SmemGame g;
-    uint64_t pi[kPiCap];
+    uint64_t pi[kPiWords];
     uint16_t ring[kRing];
     uint8_t types[48];
 };
@@ -131,38 +131,39 @@ __device__ inline void build_root(RolloutSmem* S, const st_position* in, RootSta
         for (int i = lane; i < (288 + 112) / 16; i += 32) dst[i] = src[i];
     }
     for (int i = lane; i < kRing; i += 32) out->ring[i] = S->ring[i];
-    for (int i = lane; i < S->g.c.n_pi; i += 32) out->pi[i] = S->pi[i];
+    for (int i = lane; i < 2 * S->g.c.n_pi; i += 32) out->pi[i] = S->pi[i];
 }
 
-// Warp: one rollout of `depth` random plies from root R with sample `k`
+// Team: one rollout of `depth` random plies from root R with sample `k`
 // (types given, or drawn from R->plan).  Returns the tally slot: 0 win,
 // 1 loss, 2 draw for the player to move at the root, 3 unfinished.
-__device__ inline int rollout_one(RolloutSmem* S, const RootState* R, const uint8_t* types, int depth, uint32_t k0,
-                                  uint32_t k1, uint32_t stream, uint32_t k, const Rules& Rl)
+template <int L>
+__device__ __forceinline__ int rollout_one(RolloutSmem* S, const Team<L>& T, const RootState* R, const uint8_t* types,
+                                           int depth, uint32_t k0, uint32_t k1, uint32_t stream, uint32_t k,
+                                           const Rules& Rl)
 {
-    const int lane = lane_id();
+    const int lane = T.tl;
     SmemGame* G = &S->g;
     {
         const uint4* src = reinterpret_cast<const uint4*>(R);
         uint4* dst = reinterpret_cast<uint4*>(G);
-        for (int i = lane; i < (288 + 112) / 16; i += 32) dst[i] = src[i];
+        for (int i = lane; i < (288 + 112) / 16; i += L) dst[i] = src[i];
         const uint4* rs = reinterpret_cast<const uint4*>(R->ring);
         uint4* rd = reinterpret_cast<uint4*>(S->ring);
-        for (int i = lane; i < kRing * 2 / 16; i += 32) rd[i] = rs[i];
+        for (int i = lane; i < kRing * 2 / 16; i += L) rd[i] = rs[i];
     }
-    __syncwarp();
+    T.sync();
     const int npi = G->c.n_pi;
-    for (int i = lane; i < npi; i += 32) S->pi[i] = R->pi[i];
+    for (int i = lane; i < 2 * npi; i += L) S->pi[i] = R->pi[i];
     const int searcher = G->c.ply & 1, opp = 1 - searcher;
     if (types) {
-        for (int i = lane; i < 40; i += 32) S->types[i] = types[i];
+        for (int i = lane; i < 40; i += L) S->types[i] = types[i];
     } else if (lane == 0) {
         draw_sample(&R->plan, k0, k1, stream, k, S->types);
     }
-    __syncwarp();
-    for (int i = lane; i < 40; i += 32) G->c.type[opp * 40 + i] = S->types[i];
-    __syncwarp();
-    const Team<32> T;
+    T.sync();
+    for (int i = lane; i < 40; i += L) G->c.type[opp * 40 + i] = S->types[i];
+    T.sync();
     derive_state(G, S->ring, T);   // bitboards and flag ids of the sampled types
     int n = gen_moves(G, T, searcher, Rl.flags, false, true, S->pi);
     int code = 0, winner = -1;

@@ -20,7 +20,7 @@ namespace {
 
 struct __align__(16) BeliefSmem {
     SmemGame g;
-    uint64_t pi[kPiCap];
+    uint64_t pi[kPiWords];
     uint16_t ring[kRing];
     BeliefPlan plan;
     int bad;
@@ -59,7 +59,9 @@ __global__ void k_belief(const st_position* pos, int P, int K, uint32_t k0, uint
 }
 
 constexpr int kRootWarps = 4;
-constexpr int kFlatWarps = 8;
+constexpr int kFlatLanes = 8;                              // one rollout per 8-lane team
+constexpr int kFlatWarps = 2;
+constexpr int kFlatTeams = 32 * kFlatWarps / kFlatLanes;   // rollouts per block
 
 __global__ void k_roots(const st_position* pos, int P, RootState* roots, uint8_t* status)
 {
@@ -75,16 +77,17 @@ __global__ void k_rollout_flat(const RootState* roots, int P, int K, int depth, 
                                const uint32_t* stream_ids, const uint8_t* types_in, Rules Rl, int32_t* tallies)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
-    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const Team<kFlatLanes> T;
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + threadIdx.x / kFlatLanes;
+    const long long u = (long long)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes;
     if (u >= (long long)P * K) return;
     const int p = (int)(u / K), k = (int)(u - (long long)p * K);
     const RootState* R = roots + p;
     if (R->bad) return;
     const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
     const uint8_t* t = types_in ? types_in + ((size_t)p * K + k) * 40 : nullptr;
-    const int slot = rollout_one(S, R, t, depth, k0, k1, stream, (uint32_t)k, Rl);
-    if (lane_id() == 0) atomicAdd(&tallies[4 * (size_t)p + slot], 1);
+    const int slot = rollout_one(S, T, R, t, depth, k0, k1, stream, (uint32_t)k, Rl);
+    if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + slot], 1);
 }
 
 }  // namespace
@@ -126,8 +129,8 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
     }
     if (err == cudaSuccess && K > 0) {
         const long long units = (long long)P * K;
-        const long long fb = (units + kFlatWarps - 1) / kFlatWarps;
-        k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatWarps * sizeof(RolloutSmem), s>>>(
+        const long long fb = (units + kFlatTeams - 1) / kFlatTeams;
+        k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(RolloutSmem), s>>>(
             roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, types, r, tallies);
         err = cudaGetLastError();
     }

@@ -86,13 +86,16 @@ __global__ void k_serve_roots(const BatchEntry* entries, int n, const Staged* st
     }
 }
 
+constexpr int kServeLanes = 8;   // one rollout per 8-lane team
+
 __global__ void k_serve_rollouts(const BatchEntry* entries, int n, long long units, const RootState* roots,
                                  ReqDesc* descs, SampleRec* samples, Rules Rl, volatile int32_t* host_tallies,
                                  volatile uint32_t* host_done)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
-    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const Team<kServeLanes> T;
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + threadIdx.x / kServeLanes;
+    const long long u = (long long)blockIdx.x * (blockDim.x / kServeLanes) + threadIdx.x / kServeLanes;
     if (u >= units) return;
     // the batch entry holding unit u
     int lo = 0, hi = n - 1;
@@ -105,12 +108,12 @@ __global__ void k_serve_rollouts(const BatchEntry* entries, int n, long long uni
     ReqDesc* d = descs + slot;
     const int k = (int)(u - entries[lo].unit_begin);
     const bool bad = R->bad != 0;
-    const int lane = lane_id();
+    const int lane = T.tl;
     if (!bad) {
-        const int outcome = rollout_one(S, R, nullptr, d->depth, d->k0, d->k1, d->stream, (uint32_t)k, Rl);
+        const int outcome = rollout_one(S, T, R, nullptr, d->depth, d->k0, d->k1, d->stream, (uint32_t)k, Rl);
         SampleRec* rec = samples + d->sample_base + k;
-        if (lane < 10)
-            reinterpret_cast<uint32_t*>(rec->types)[lane] = reinterpret_cast<const uint32_t*>(S->types)[lane];
+        for (int i = lane; i < 10; i += kServeLanes)
+            reinterpret_cast<uint32_t*>(rec->types)[i] = reinterpret_cast<const uint32_t*>(S->types)[i];
         if (lane == 0) {
             rec->outcome = (int8_t)outcome;
             atomicAdd(&d->tallies[outcome], 1);
@@ -129,7 +132,8 @@ __global__ void k_serve_rollouts(const BatchEntry* entries, int n, long long uni
     }
 }
 
-constexpr int kServeWarps = 8;
+constexpr int kServeWarps = 2;
+constexpr int kServeTeams = 32 * kServeWarps / kServeLanes;   // rollouts per block
 
 uint64_t now_ns()
 {
@@ -318,8 +322,8 @@ bool schedule_once(st_server* s, std::unique_lock<std::mutex>& lk)
         err = cudaGetLastError();
     }
     if (err == cudaSuccess && units > 0) {
-        const long long fb = (units + kServeWarps - 1) / kServeWarps;
-        k_serve_rollouts<<<(unsigned)fb, 32 * kServeWarps, kServeWarps * sizeof(RolloutSmem), str>>>(
+        const long long fb = (units + kServeTeams - 1) / kServeTeams;
+        k_serve_rollouts<<<(unsigned)fb, 32 * kServeWarps, kServeTeams * sizeof(RolloutSmem), str>>>(
             s->entries_dev + (size_t)b * R, n, units, s->roots, s->descs, s->samples, s->rules, s->host_tallies_dev,
             s->host_done_dev);
         err = cudaGetLastError();

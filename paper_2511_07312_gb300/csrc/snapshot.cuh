@@ -71,37 +71,40 @@ __device__ __forceinline__ int import_position(SmemGame* G, const st_position* i
     const int ply = G->c.ply;
     for (int h = lane; h < kRing; h += 32)
         if (h < ply) ring[(ply - 1 - h) & (kRing - 1)] = in->hist[h];
-    const uint64_t hash = board_hash(G, T);
+    const uint64_t hash0 = side_hash(G, T, 0), hash1 = side_hash(G, T, 1);
     T.sync();
     if (lane == 0) {
-        G->c.hash = hash;
+        G->c.hash_side[0] = hash0;
+        G->c.hash_side[1] = hash1;
         // chase positions: undo the chase plies from the current board,
-        // hashing the position after each of the chaser's plies
-        if (G->c.chaser != kNone) {
+        // recording (chaser's hash, chased side's hash) after each of the
+        // chaser's plies, oldest first
+        const int chaser = G->c.chaser;
+        if (chaser != kNone) {
+            int nt = 0;
+            for (int i = 0; i < G->c.chase_plies; ++i) nt += ((ply - 1 - i) & 1) == chaser;
+            if (nt > kPiCap) bad = 11;
             uint8_t b[100];
             for (int s = 0; s < 100; ++s) b[s] = G->board[s];
-            uint64_t h = hash;
-            uint64_t tmp[kPiCap];
-            int nt = 0;
+            uint64_t h[2] = {hash0, hash1};
+            int j = 0;
             for (int i = 0; i < G->c.chase_plies && !bad; ++i) {
                 const int mover = (ply - 1 - i) & 1;
                 const int a = in->hist[i];
                 if (a == 0xFFFF) { bad = 10; break; }
-                if (mover == G->c.chaser) {
-                    if (nt >= kPiCap) { bad = 11; break; }
-                    tmp[nt++] = h;
+                if (mover == chaser) {
+                    const int at = nt - 1 - j++;
+                    pi[2 * at] = h[chaser];
+                    pi[2 * at + 1] = h[1 - chaser];
                 }
                 const int f = a / 100, t = a % 100;
                 if (f >= 100 || b[t] >= kPieces || b[f] != kEmpty || is_lake(f)) { bad = 12; break; }
                 const int p = b[t];
                 b[f] = (uint8_t)p;
                 b[t] = kEmpty;
-                h ^= zkey(p, t) ^ zkey(p, f);
+                h[p / 40] ^= zkey(p, t) ^ zkey(p, f);
             }
-            if (!bad) {
-                for (int i = 0; i < nt; ++i) pi[i] = tmp[nt - 1 - i];
-                G->c.n_pi = (uint8_t)nt;
-            }
+            if (!bad) G->c.n_pi = (uint8_t)nt;
         }
     }
     bad = T.shfl(bad, 0);
