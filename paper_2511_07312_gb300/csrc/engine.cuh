@@ -1,21 +1,22 @@
 // engine.cuh -- team-cooperative Stratego engine for sm_103a.
 //
-// A team of L lanes (L = 32: one game per warp; L = 16: two games per warp)
-// owns one game at a time.  The game lives in a team-private shared-memory
-// record (SmemGame): the 288-byte per-game state that persists in HBM
-// between launches, the board (piece id per square), row bitboards kept up to
-// date ply by ply (own pieces, movable non-Scouts and Scouts per player and
-// row, occupancy per column), and the 1,264-byte legal-move mask of the
-// player to move.
+// A team of L lanes (L = 32, 16 or 8: one, two or four games per warp) owns
+// one game at a time.  The game lives in a team-private shared-memory record
+// (SmemGame): the 288-byte per-game state that persists in HBM between
+// launches, the board (piece id per square), 128-bit square sets kept up to
+// date ply by ply (own pieces, movable non-Scouts and Scouts per player),
+// occupancy per column, and the 1,264-byte legal-move mask of the player to
+// move.
 //
-// Move generation: lane r < 10 of the team owns board row r.  Non-Scout
-// moves of a whole row come from four shifted bitboards; each from-square's
-// (at most four) destinations are OR-ed into the mask as one window of at
-// most 21 bits (one or two shared atomics).  Scout slides come from the row
-// and column occupancy with find-first-set.  The scalar part of a ply (apply,
-// battle, rule state) runs on the team's first lane; all collectives are
-// team-masked, so the teams of a warp run in lockstep when their games take
-// the same path and serialize harmlessly when they do not.
+// Move generation: non-Scout moves of the whole board come from four shifted
+// square sets; lane j of the team records those of its segment of 13, 7 or 4
+// from-squares (L = 8, 16, 32), each from-square's (at most four)
+// destinations OR-ed into the mask as one window of at most 21 bits (one or
+// two shared atomics).  Each Scout takes one lane; its slides come from the
+// row and column occupancy with find-first-set.  The scalar part of a ply
+// (apply, battle, rule state) runs on the team's first lane; all collectives
+// are team-masked, so the teams of a warp run in lockstep when their games
+// take the same path and serialize harmlessly when they do not.
 //
 // Rules follow App. A of arXiv 2511.07312 (Tab. pieces, Tab. chase), the
 // two-square and chasing state machines of App. B.2-B.3, the k-move rule and
@@ -40,7 +41,8 @@ constexpr uint8_t kEmpty = 0xFF;
 constexpr uint8_t kLake = 0xFE;
 constexpr uint8_t kNone = 0xFF;
 constexpr int kMaskBytes = 1264;
-constexpr int kMaskWordsAlloc = 384;   // 316 used by the output layout, the rest kept zero (96 uint4 = 3 or 6 per lane)
+constexpr int kMaskWordsAlloc = 320;   // 316 used by the output layout, the rest kept zero
+constexpr int kSegMax = 25;            // from-square segments (one per lane; 25 of 4 squares for 32 lanes)
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
 constexpr int kPiWords = 2 * kPiCap;   // each: hash of the chaser's pieces, hash of the chased side's pieces
 constexpr int kRing = 256;             // moves of history per game
@@ -81,20 +83,25 @@ struct __align__(16) GameCore {
 };
 static_assert(sizeof(GameCore) == 288, "GameCore layout");
 
+// Square sets: bit s of a 128-bit set is square s; word 0 holds squares
+// 0-63, word 1 squares 64-99.
 struct __align__(16) SmemGame {
     GameCore c;
     uint8_t board[112];
-    uint16_t occ[2][10];      // pieces of player p in row r (bit = column)
-    uint16_t mov[2][10];      // movable non-Scouts
-    uint16_t sco[2][10];      // Scouts
+    uint64_t bocc[2][2];      // pieces of player p
+    uint64_t bmov[2][2];      // movable non-Scouts of player p
+    uint64_t bsco[2][2];      // Scouts of player p
     uint16_t colocc[10];      // all pieces in column c (bit = row)
     uint16_t h0, h1;          // actions played 1 and 2 plies ago (0xFFFF none)
     uint8_t flag_pid[2];
-    uint8_t row_cnt[10];      // moves per from-row in G->mask (written with the mask)
-    uint8_t pad[4];
+    uint8_t scout_pid[2][8];  // the Scouts of each side in piece-id order (kNone after the last)
+    uint8_t pad[2];
+    uint32_t seg_cnt[kSegMax];// moves per from-square segment in G->mask (written with the mask)
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 120 + 20 + 4 + 2 + 14 + 4 * kMaskWordsAlloc, "SmemGame layout");
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 4 * kMaskWordsAlloc,
+              "SmemGame layout");
+static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
@@ -215,34 +222,50 @@ __device__ __forceinline__ int hist_at(const SmemGame* G, const uint16_t* ring, 
     return ring[(ply - 1 - i) & (kRing - 1)];
 }
 
-// Everything derived from the core and the board: row and column bitboards,
-// flag ids, the last two moves.  Needs G->board.
+__device__ __forceinline__ void bb_set(uint64_t* b, int s) { b[s >> 6] |= 1ull << (s & 63); }
+__device__ __forceinline__ void bb_clr(uint64_t* b, int s) { b[s >> 6] &= ~(1ull << (s & 63)); }
+
+// Everything derived from the core and the board: square sets per player,
+// column occupancy, flag ids, Scout lists, the last two moves.  Needs
+// G->board.  Each side has at most 8 Scouts (Tab. pieces; setups, imported
+// positions and belief samples keep the piece counts).
 template <int L>
 __device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, Team<L>)
 {
     // out-of-line engine functions rebuild the team from the lane id rather
     // than reading the caller's copy through memory
     const Team<L> T;
-    for (int r = T.tl; r < 10; r += L) {
-        uint32_t o0 = 0, o1 = 0, m0 = 0, m1 = 0, s0 = 0, s1 = 0, col = 0;
-        for (int c = 0; c < 10; ++c) {
-            const uint8_t p = G->board[10 * r + c];
-            if (p < kPieces) {
-                const uint32_t b = 1u << c;
-                const int t = G->c.type[p];
-                if (p < 40) { o0 |= b; if (t == kScout) s0 |= b; else if (t < kFlag) m0 |= b; }
-                else        { o1 |= b; if (t == kScout) s1 |= b; else if (t < kFlag) m1 |= b; }
-            }
-            const uint8_t q = G->board[10 * c + r];   // column r, row c
-            if (q < kPieces) col |= 1u << c;
-        }
-        G->occ[0][r] = (uint16_t)o0; G->occ[1][r] = (uint16_t)o1;
-        G->mov[0][r] = (uint16_t)m0; G->mov[1][r] = (uint16_t)m1;
-        G->sco[0][r] = (uint16_t)s0; G->sco[1][r] = (uint16_t)s1;
-        G->colocc[r] = (uint16_t)col;
+    uint64_t* sets = &G->bocc[0][0];   // bocc, bmov, bsco: 12 words
+    for (int i = T.tl; i < 12; i += L) sets[i] = 0;
+    T.sync();
+    for (int p = T.tl; p < kPieces; p += L) {
+        const int t = G->c.type[p], side = p / 40;
+        if (t == kFlag) G->flag_pid[side] = (uint8_t)p;
+        if (!(G->c.flags[p] & 1)) continue;
+        const int s = G->c.sq[p];
+        const unsigned long long b = 1ull << (s & 63);
+        atomicOr(reinterpret_cast<unsigned long long*>(&G->bocc[side][s >> 6]), b);
+        if (t == kScout) atomicOr(reinterpret_cast<unsigned long long*>(&G->bsco[side][s >> 6]), b);
+        else if (t < kFlag) atomicOr(reinterpret_cast<unsigned long long*>(&G->bmov[side][s >> 6]), b);
     }
-    for (int p = T.tl; p < kPieces; p += L)
-        if (G->c.type[p] == kFlag) G->flag_pid[p / 40] = (uint8_t)p;
+    for (int side = 0; side < 2; ++side) {
+        int n = 0;
+        for (int k0 = 0; k0 < 40; k0 += L) {
+            const int k = k0 + T.tl;
+            const bool is = k < 40 && G->c.type[40 * side + k] == kScout;
+            const uint32_t b = T.ballot(is);
+            const int rank = n + __popc(b & ((1u << T.tl) - 1u));
+            if (is && rank < 8) G->scout_pid[side][rank] = (uint8_t)(40 * side + k);
+            n += __popc(b);
+        }
+        for (int i = n + T.tl; i < 8; i += L) G->scout_pid[side][i] = kNone;
+    }
+    for (int c = T.tl; c < 10; c += L) {
+        uint32_t col = 0;
+        for (int r = 0; r < 10; ++r)
+            if (G->board[10 * r + c] < kPieces) col |= 1u << r;
+        G->colocc[c] = (uint16_t)col;
+    }
     if (T.leader()) {
         G->h0 = (uint16_t)hist_at(G, ring, 0);
         G->h1 = (uint16_t)hist_at(G, ring, 1);
@@ -438,19 +461,66 @@ __device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d)
     if (prev) atomicOr(&mask[w0 + 4], prev);
 }
 
+// ----------------------------------------------------------------- square sets
+constexpr uint64_t col_bits(int c, int half)
+{
+    uint64_t v = 0;
+    for (int r = 0; r < 10; ++r) {
+        const int s = 10 * r + c;
+        if ((s >> 6) == half) v |= 1ull << (s & 63);
+    }
+    return v;
+}
+constexpr uint64_t kLakesLo = (1ull << 42) | (1ull << 43) | (1ull << 46) | (1ull << 47) | (1ull << 52) |
+                              (1ull << 53) | (1ull << 56) | (1ull << 57);   // the lakes are squares < 64
+constexpr uint64_t kValidHi = (1ull << 36) - 1ull;                         // squares 64-99
+constexpr uint64_t kCol0Lo = col_bits(0, 0), kCol0Hi = col_bits(0, 1);
+constexpr uint64_t kCol9Lo = col_bits(9, 0), kCol9Hi = col_bits(9, 1);
+
+__device__ __forceinline__ Set128 ld128(const uint64_t* p) { return Set128{p[0], p[1]}; }
+__device__ __forceinline__ Set128 and128(Set128 a, Set128 b) { return Set128{a.lo & b.lo, a.hi & b.hi}; }
+// square s+k of the result is square s of the input (k = 1, 10) and back
+__device__ __forceinline__ Set128 up1(Set128 a) { return Set128{a.lo << 1, (a.hi << 1) | (a.lo >> 63)}; }
+__device__ __forceinline__ Set128 dn1(Set128 a) { return Set128{(a.lo >> 1) | (a.hi << 63), a.hi >> 1}; }
+__device__ __forceinline__ Set128 up10(Set128 a) { return Set128{a.lo << 10, (a.hi << 10) | (a.lo >> 54)}; }
+__device__ __forceinline__ Set128 dn10(Set128 a) { return Set128{(a.lo >> 10) | (a.hi << 54), a.hi >> 10}; }
+// w (< 32) bits of x starting at square off (0 <= off < 128)
+__device__ __forceinline__ uint32_t bits_at(Set128 x, int off, int w)
+{
+    const uint64_t v = off >= 64 ? (x.hi >> (off - 64)) : (off == 0 ? x.lo : ((x.lo >> off) | (x.hi << (64 - off))));
+    return (uint32_t)v & ((1u << w) - 1u);
+}
+
+// From-square segments: lane j of a team of L lanes owns squares
+// [kSegW*j, kSegW*j + kSegW) (13, 7 or 4 squares for L = 8, 16, 32).
+template <int L> struct Seg {
+    static constexpr int W = (kSquares + L - 1) / L;
+    static constexpr int N = (kSquares + W - 1) / W;
+    static_assert(N <= kSegMax && N <= L, "segments");
+};
+
 // ----------------------------------------------------------------- move generation
-// Counts (and, if write_mask, records in G->mask) the moves of player P.
-// physical: movement rules only (App. A "Piece details"); otherwise the
-// two-square and chasing rules filter as rule_flags says.  Team-uniform
-// result.
+// Counts (and, if write_mask, records in G->mask and G->seg_cnt) the moves of
+// player P.  physical: movement rules only (App. A "Piece details");
+// otherwise the two-square and chasing rules filter as rule_flags says.
+// Team-uniform result.
+//
+// Non-Scout moves come from four shifted square sets over the whole board;
+// each lane records those of its own segment, one window of at most 21 mask
+// bits per from-square (to-squares s-10, s-1, s+1, s+10 are bits 101s-10,
+// 101s-1, 101s+1, 101s+10).  Scouts take one lane each.  Destinations that
+// a rule may forbid (those of the piece under the two-square rule; all moves
+// while a chase position can recur) go through filter_dests.
 template <int L>
 __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule_flags, bool physical,
                                       bool write_mask, const uint64_t* pi)
 {
     const Team<L> T;
+    constexpr int SW = Seg<L>::W, NS = Seg<L>::N;
     if (write_mask) {
         uint4* m4 = reinterpret_cast<uint4*>(G->mask);
         for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
+        if (T.tl < NS) G->seg_cnt[T.tl] = 0;
     }
     const int ts_pid = G->c.ts_pid[P];
     const bool ts_on = !physical && (rule_flags & kTwoSquare) && ts_pid != kNone && G->c.ts_len[P] == 4 &&
@@ -460,160 +530,138 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                           chase_live(G, T, pi, P);
     const PlyCtx x = make_ctx(G);
     T.sync();   // mask zeroed before any atomic
+    const Set128 own = ld128(G->bocc[P]), enm = ld128(G->bocc[1 - P]), mv = ld128(G->bmov[P]);
+    // empty or enemy squares
+    const Set128 fre{~own.lo & ~kLakesLo, ~own.hi & kValidHi};
+    const Set128 FE = and128(and128(mv, dn1(fre)), Set128{~kCol9Lo, ~kCol9Hi});
+    const Set128 FW = and128(and128(mv, up1(fre)), Set128{~kCol0Lo, ~kCol0Hi});
+    const Set128 FN = and128(mv, dn10(fre));
+    const Set128 FS = and128(mv, up10(fre));
+    const int off = SW * T.tl;
+    uint32_t fe = bits_at(FE, off, SW), fw = bits_at(FW, off, SW);
+    uint32_t fn = bits_at(FN, off, SW), fs = bits_at(FS, off, SW);
+    uint32_t moving = fe | fw | fn | fs;
     int cnt = 0;
-    for (int r = T.tl; r < 10; r += L) {
-        const int cnt_before_row = cnt;
-        const uint32_t own = G->occ[P][r], enm = G->occ[1 - P][r], mv = G->mov[P][r];
-        uint32_t sc = G->sco[P][r];
-        const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
-        const uint32_t fre = ~own & ~lake & 0x3FFu;                     // empty or enemy squares of row r
-        const uint32_t fre_up = r < 9 ? (~(uint32_t)G->occ[P][r + 1] & ~((r + 1 == 4 || r + 1 == 5) ? kLakeRow : 0u) &
-                                         0x3FFu) : 0u;
-        const uint32_t fre_dn = r > 0 ? (~(uint32_t)G->occ[P][r - 1] & ~((r - 1 == 4 || r - 1 == 5) ? kLakeRow : 0u) &
-                                         0x3FFu) : 0u;
-        const uint32_t FE = mv & (fre >> 1);
-        const uint32_t FW = mv & ((fre << 1) & 0x3FFu);
-        const uint32_t FN = mv & fre_up;
-        const uint32_t FS = mv & fre_dn;
-        uint32_t moving = FE | FW | FN | FS;
-        if (!chase_on) {
-            // the piece under the two-square rule (if on this row) is the
-            // only one whose destinations need a filter
-            const uint32_t ts_bit = (ts_on && ts_from / 10 == r) ? (1u << (ts_from % 10)) : 0u;
-            if (moving & ts_bit) {
-                const int c = ts_from % 10, s = ts_from;
-                Set128 d{0ull, 0ull};
-                if ((FS >> c) & 1u) d = or128(d, bit128(s - 10));
-                if ((FW >> c) & 1u) d = or128(d, bit128(s - 1));
-                if ((FE >> c) & 1u) d = or128(d, bit128(s + 1));
-                if ((FN >> c) & 1u) d = or128(d, bit128(s + 10));
-                d = filter_dests(G, P, s, true, false, x, pi, d);
-                cnt += popc128(d);
-                if (write_mask) or_row(G->mask, s, d);
-                moving &= ~ts_bit;
-            }
-            cnt += __popc(FE & ~ts_bit) + __popc(FW & ~ts_bit) + __popc(FN & ~ts_bit) + __popc(FS & ~ts_bit);
-            if (write_mask) {
-                while (moving) {
-                    const int c = __ffs(moving) - 1;
-                    moving &= moving - 1;
-                    const int s = 10 * r + c;
-                    const int lo = s >= 10 ? s - 10 : (c > 0 ? s - 1 : s + 1);
-                    const uint32_t pat = (((FS >> c) & 1u) << ((s - 10 - lo) & 31)) |
-                                         (((FW >> c) & 1u) << ((s - 1 - lo) & 31)) |
-                                         (((FE >> c) & 1u) << ((s + 1 - lo) & 31)) |
-                                         (((FN >> c) & 1u) << ((s + 10 - lo) & 31));
-                    const int base = 100 * s + lo;
-                    const uint64_t v = (uint64_t)pat << (base & 31);
-                    atomicOr(&G->mask[base >> 5], (uint32_t)v);
-                    if (v >> 32) atomicOr(&G->mask[(base >> 5) + 1], (uint32_t)(v >> 32));
-                }
-            }
-        } else {
+    if (chase_on) {
+        while (moving) {
+            const int c = __ffs(moving) - 1;
+            moving &= moving - 1;
+            const int s = off + c;
+            Set128 d{0ull, 0ull};
+            if ((fs >> c) & 1u) d = or128(d, bit128(s - 10));
+            if ((fw >> c) & 1u) d = or128(d, bit128(s - 1));
+            if ((fe >> c) & 1u) d = or128(d, bit128(s + 1));
+            if ((fn >> c) & 1u) d = or128(d, bit128(s + 10));
+            d = filter_dests(G, P, s, s == ts_from, true, x, pi, d);
+            cnt += popc128(d);
+            if (write_mask) or_row(G->mask, s, d);
+        }
+    } else {
+        // the piece under the two-square rule (if in this segment) is the only
+        // one whose destinations need a filter
+        const uint32_t ts_bit = (ts_from >= off && ts_from < off + SW) ? (1u << (ts_from - off)) : 0u;
+        if (moving & ts_bit) {
+            const int c = ts_from - off, s = ts_from;
+            Set128 d{0ull, 0ull};
+            if ((fs >> c) & 1u) d = or128(d, bit128(s - 10));
+            if ((fw >> c) & 1u) d = or128(d, bit128(s - 1));
+            if ((fe >> c) & 1u) d = or128(d, bit128(s + 1));
+            if ((fn >> c) & 1u) d = or128(d, bit128(s + 10));
+            d = filter_dests(G, P, s, true, false, x, pi, d);
+            cnt += popc128(d);
+            if (write_mask) or_row(G->mask, s, d);
+            moving &= ~ts_bit;
+            fe &= ~ts_bit; fw &= ~ts_bit; fn &= ~ts_bit; fs &= ~ts_bit;
+        }
+        cnt += __popc(fe) + __popc(fw) + __popc(fn) + __popc(fs);
+        if (write_mask) {
             while (moving) {
                 const int c = __ffs(moving) - 1;
                 moving &= moving - 1;
-                const int s = 10 * r + c;
-                Set128 d{0ull, 0ull};
-                if ((FS >> c) & 1u) d = or128(d, bit128(s - 10));
-                if ((FW >> c) & 1u) d = or128(d, bit128(s - 1));
-                if ((FE >> c) & 1u) d = or128(d, bit128(s + 1));
-                if ((FN >> c) & 1u) d = or128(d, bit128(s + 10));
-                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
-                cnt += popc128(d);
-                if (write_mask) or_row(G->mask, s, d);
+                const int s = off + c;
+                uint32_t pat = ((fs >> c) & 1u) | (((fw >> c) & 1u) << 9) | (((fe >> c) & 1u) << 11) |
+                               (((fn >> c) & 1u) << 20);
+                int base = 101 * s - 10;
+                if (s == 0) { pat >>= 10; base = 0; }   // square 0 has no south or west move
+                const uint64_t v = (uint64_t)pat << (base & 31);
+                atomicOr(&G->mask[base >> 5], (uint32_t)v);
+                if (v >> 32) atomicOr(&G->mask[(base >> 5) + 1], (uint32_t)(v >> 32));
             }
         }
-        // Scouts: slides along the row and the column, stopping before a lake
-        // or an own piece and on the first enemy piece.
-        const uint32_t rowocc = own | enm | lake;
-        while (sc) {
-            const int c = __ffs(sc) - 1;
-            sc &= sc - 1;
-            const int s = 10 * r + c;
-            // slide lengths: empty squares east/west/north/south, then whether
-            // the blocker is an enemy (a capture ends the slide)
-            const uint32_t e = rowocc >> (c + 1);
-            const int runE = e ? __ffs(e) - 1 : 9 - c;
-            const int capE = (e && ((enm >> (c + 1 + runE)) & 1u)) ? 1 : 0;
-            const uint32_t w = rowocc & ((1u << c) - 1u);
-            const int hw = w ? 31 - __clz(w) : -1;
-            const int runW = c - 1 - hw;
-            const int capW = (hw >= 0 && ((enm >> hw) & 1u)) ? 1 : 0;
-            const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
-            const uint32_t n = colocc >> (r + 1);
-            const int runN = n ? __ffs(n) - 1 : 9 - r;
-            const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
-            const uint32_t so = colocc & ((1u << r) - 1u);
-            const int hs = so ? 31 - __clz(so) : -1;
-            const int runS = r - 1 - hs;
-            const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
-            const int nd = runE + capE + runW + capW + runN + capN + runS + capS;
-            if (nd == 0) continue;
-            if (chase_on || s == ts_from) {
+    }
+    if (write_mask && cnt && T.tl < NS) atomicAdd(&G->seg_cnt[T.tl], (uint32_t)cnt);
+    // Scouts, one per lane: slides along the row and the column, stopping
+    // before a lake or an own piece and on the first enemy piece.
+    int cnt_sc = 0;
+    const int spid = T.tl < 8 ? G->scout_pid[P][T.tl] : kNone;
+    if (spid != kNone && (G->c.flags[spid] & 1)) {
+        const int s = G->c.sq[spid], r = s / 10, c = s - 10 * r;
+        const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
+        const uint32_t enr = bits_at(enm, 10 * r, 10);
+        const uint32_t rowocc = bits_at(own, 10 * r, 10) | enr | lake;
+        // slide lengths: empty squares east/west/north/south, then whether
+        // the blocker is an enemy (a capture ends the slide)
+        const uint32_t e = rowocc >> (c + 1);
+        const int runE = e ? __ffs(e) - 1 : 9 - c;
+        const int capE = (e && ((enr >> (c + 1 + runE)) & 1u)) ? 1 : 0;
+        const uint32_t w = rowocc & ((1u << c) - 1u);
+        const int hw = w ? 31 - __clz(w) : -1;
+        const int runW = c - 1 - hw;
+        const int capW = (hw >= 0 && ((enr >> hw) & 1u)) ? 1 : 0;
+        const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
+        const uint32_t n = colocc >> (r + 1);
+        const int runN = n ? __ffs(n) - 1 : 9 - r;
+        const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
+        const uint32_t so = colocc & ((1u << r) - 1u);
+        const int hs = so ? 31 - __clz(so) : -1;
+        const int runS = r - 1 - hs;
+        const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
+        const int nd = runE + capE + runW + capW + runN + capN + runS + capS;
+        if (nd) {
+            if (write_mask || chase_on || s == ts_from) {
                 Set128 d = or128(range128(s + 1, runE + capE), range128(s - runW - capW, runW + capW));
                 d = or128(d, column128(c, r + 1, r + runN + capN));
                 d = or128(d, column128(c, r - runS - capS, r - 1));
-                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
-                cnt += popc128(d);
-                if (write_mask) or_row(G->mask, s, d);
-                continue;
-            }
-            cnt += nd;
-            if (write_mask) {
-                // along the row: two runs of consecutive to-squares
-                const int row_bit = 100 * s;
-                const int nw = runW + capW, ne = runE + capE;
-                if (nw) {
-                    const int b = row_bit + s - nw;
-                    const uint64_t v = ((1ull << nw) - 1ull) << (b & 31);
-                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
-                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+                if (chase_on || s == ts_from) d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+                cnt_sc = popc128(d);
+                if (write_mask) {
+                    or_row(G->mask, s, d);
+                    if (cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
                 }
-                if (ne) {
-                    const int b = row_bit + s + 1;
-                    const uint64_t v = ((1ull << ne) - 1ull) << (b & 31);
-                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
-                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
-                }
-                // along the column: one bit per to-square, ten apart
-                for (int k = 1; k <= runN + capN; ++k) {
-                    const int b = row_bit + s + 10 * k;
-                    atomicOr(&G->mask[b >> 5], 1u << (b & 31));
-                }
-                for (int k = 1; k <= runS + capS; ++k) {
-                    const int b = row_bit + s - 10 * k;
-                    atomicOr(&G->mask[b >> 5], 1u << (b & 31));
-                }
+            } else {
+                cnt_sc = nd;
             }
         }
-        if (write_mask) G->row_cnt[r] = (uint8_t)(cnt - cnt_before_row);
     }
-    const int total = T.sum(cnt);
+    const int total = T.sum(cnt + cnt_sc);
     T.sync();
     return total;
 }
 
-// The idx-th set bit (ascending) of G->mask; team-uniform result.  Board
-// row r's from-squares own the consecutive actions [1000r, 1000r+1000), so
-// the per-row counts written with the mask pick the row first and only that
-// row's 32-33 mask words are scanned.
+// The idx-th set bit (ascending) of G->mask; team-uniform result.  The
+// from-squares of segment j own the consecutive actions
+// [100*W*j, 100*W*(j+1)), so the per-segment counts written with the mask
+// pick the segment first and only its mask words are scanned.
 template <int L>
 __device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
 {
     const Team<L> T;
-    int local = (int)idx, row = 0;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const int c = G->row_cnt[r];
-        if (row == r && local >= c) { local -= c; row = r + 1; }
-    }
-    row = min(row, 9);
-    const int b0 = 1000 * row, b1 = b0 + 1000;           // the row's bits: [b0, b1)
-    const int w0 = b0 >> 5, w1 = (b1 - 1) >> 5;           // its words, inclusive
-    const int nw = w1 - w0 + 1;                            // 32 or 33
-    constexpr int C = (33 + L - 1) / L;                    // words per lane
+    constexpr int SW = Seg<L>::W, NS = Seg<L>::N;
     const int t = T.tl;
+    const int cs = t < NS ? (int)G->seg_cnt[t] : 0;
+    int cincl = cs;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const int v = __shfl_up_sync(T.mask, cincl, o, L);
+        if (t >= o) cincl += v;
+    }
+    const uint32_t segs = T.ballot((int)idx >= cincl - cs && (int)idx < cincl);
+    const int g = segs ? __ffs(segs) - 1 : 0;
+    const int local = (int)idx - T.shfl(cincl - cs, g);
+    const int b0 = 100 * SW * g, b1 = min(b0 + 100 * SW, 100 * kSquares);   // the segment's bits: [b0, b1)
+    const int w0 = b0 >> 5, w1 = (b1 - 1) >> 5;                              // its words, inclusive
+    const int nw = w1 - w0 + 1;
+    constexpr int C = (100 * SW / 32 + 2 + L - 1) / L;                       // words per lane
     uint32_t w[C];
     int cnt = 0;
 #pragma unroll
@@ -687,10 +735,10 @@ __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* r
         int D = -1;
         bool d_died = false, x_alive = true;
         const int tX = c.type[X];
-        uint16_t* kindX = tX == kScout ? G->sco[P] : G->mov[P];
+        uint64_t* kindX = tX == kScout ? G->bsco[P] : G->bmov[P];
         G->board[from] = kEmpty;
-        G->occ[P][rf] &= (uint16_t)~(1u << cf);
-        kindX[rf] &= (uint16_t)~(1u << cf);
+        bb_clr(G->bocc[P], from);
+        bb_clr(kindX, from);
         G->colocc[cf] &= (uint16_t)~(1u << rf);
         if (!battle) {
             G->board[to] = (uint8_t)X;
@@ -733,14 +781,14 @@ __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* r
             c.flags[D] = fd;
             if (d_died) {
                 const int Q = 1 - P;
-                G->occ[Q][rt] &= (uint16_t)~(1u << ct);
-                G->mov[Q][rt] &= (uint16_t)~(1u << ct);
-                G->sco[Q][rt] &= (uint16_t)~(1u << ct);
+                bb_clr(G->bocc[Q], to);
+                bb_clr(G->bmov[Q], to);
+                bb_clr(G->bsco[Q], to);
             }
         }
         if (x_alive) {
-            G->occ[P][rt] |= (uint16_t)(1u << ct);
-            kindX[rt] |= (uint16_t)(1u << ct);
+            bb_set(G->bocc[P], to);
+            bb_set(kindX, to);
         }
         if (G->board[to] != kEmpty) G->colocc[ct] |= (uint16_t)(1u << rt);
         else G->colocc[ct] &= (uint16_t)~(1u << rt);
