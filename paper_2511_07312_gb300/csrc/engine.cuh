@@ -597,17 +597,16 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
     if (spid != kNone && (G->c.flags[spid] & 1)) {
         const int s = G->c.sq[spid], r = s / 10, c = s - 10 * r;
         const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
-        const uint32_t enr = bits_at(enm, 10 * r, 10);
-        const uint32_t rowocc = bits_at(own, 10 * r, 10) | enr | lake;
+        const uint32_t rowocc = bits_at(Set128{own.lo | enm.lo, own.hi | enm.hi}, 10 * r, 10) | lake;
         // slide lengths: empty squares east/west/north/south, then whether
         // the blocker is an enemy (a capture ends the slide)
         const uint32_t e = rowocc >> (c + 1);
         const int runE = e ? __ffs(e) - 1 : 9 - c;
-        const int capE = (e && ((enr >> (c + 1 + runE)) & 1u)) ? 1 : 0;
+        const int capE = (e && enemy_of(G->board[s + runE + 1], P)) ? 1 : 0;
         const uint32_t w = rowocc & ((1u << c) - 1u);
         const int hw = w ? 31 - __clz(w) : -1;
         const int runW = c - 1 - hw;
-        const int capW = (hw >= 0 && ((enr >> hw) & 1u)) ? 1 : 0;
+        const int capW = (hw >= 0 && enemy_of(G->board[10 * r + hw], P)) ? 1 : 0;
         const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
         const uint32_t n = colocc >> (r + 1);
         const int runN = n ? __ffs(n) - 1 : 9 - r;
@@ -616,22 +615,31 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
         const int hs = so ? 31 - __clz(so) : -1;
         const int runS = r - 1 - hs;
         const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
-        const int nd = runE + capE + runW + capW + runN + capN + runS + capS;
-        if (nd) {
-            if (write_mask || chase_on || s == ts_from) {
-                Set128 d = or128(range128(s + 1, runE + capE), range128(s - runW - capW, runW + capW));
-                d = or128(d, column128(c, r + 1, r + runN + capN));
-                d = or128(d, column128(c, r - runS - capS, r - 1));
-                if (chase_on || s == ts_from) d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
-                cnt_sc = popc128(d);
-                if (write_mask) {
-                    or_row(G->mask, s, d);
-                    if (cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
-                }
-            } else {
-                cnt_sc = nd;
+        const int ne = runE + capE, nw = runW + capW, nn = runN + capN, ns = runS + capS;
+        cnt_sc = ne + nw + nn + ns;
+        if (cnt_sc && (chase_on || s == ts_from)) {
+            Set128 d = or128(range128(s + 1, ne), range128(s - nw, nw));
+            d = or128(d, column128(c, r + 1, r + nn));
+            d = or128(d, column128(c, r - ns, r - 1));
+            d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+            cnt_sc = popc128(d);
+            if (write_mask) or_row(G->mask, s, d);
+        } else if (cnt_sc && write_mask) {
+            // along the row: to-squares s-nw .. s+ne except s, one run of mask
+            // bits around bit 101s
+            const int b = 101 * s - nw;
+            const uint64_t v = (((1ull << (nw + ne + 1)) - 1ull) & ~(1ull << nw)) << (b & 31);
+            if (v) {
+                atomicOr(&G->mask[b >> 5], (uint32_t)v);
+                if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+            }
+            // along the column: to-squares s+10k, mask bits 101s+10k
+            for (int k = -ns; k <= nn; ++k) {
+                const int m = 101 * s + 10 * k;
+                if (k) atomicOr(&G->mask[m >> 5], 1u << (m & 31));
             }
         }
+        if (write_mask && cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
     }
     const int total = T.sum(cnt + cnt_sc);
     T.sync();
