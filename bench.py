@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--wpb", type=int, default=0, help="warps per block (0 = tuned default)")
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
-    p.add_argument("--gpw", type=int, default=0, help="games per warp, 1 or 2 (0 = tuned default)")
+    p.add_argument("--gpw", type=int, default=0, help="games per warp, 1, 2, 4 or 8 (0 = tuned default)")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="time the persistent step launch only (for profiler captures): no plain path, "

@@ -187,8 +187,8 @@ st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* 
                      int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring);
 
 /* Launch shape of st_env_run: warps per block (1..16), blocks per SM (0 =
- * occupancy maximum), games a warp steps side by side (1: one 32-lane team,
- * 2: two 16-lane teams) and slots each team claims per queue fetch (>=1).
+ * occupancy maximum), games a warp steps side by side (1, 2, 4 or 8: teams
+ * of 32, 16, 8 or 4 lanes) and slots each team claims per queue fetch (>=1).
  * Results do not depend on the shape. */
 st_status st_env_set_launch(st_env* env, int32_t warps_per_block, int32_t blocks_per_sm, int32_t games_per_warp,
                             int32_t games_per_fetch);

@@ -1,6 +1,6 @@
 // engine.cuh -- team-cooperative Stratego engine for sm_103a.
 //
-// A team of L lanes (L = 32, 16 or 8: one, two or four games per warp) owns
+// A team of L lanes (L = 32, 16, 8 or 4: 1, 2, 4 or 8 games per warp) owns
 // one game at a time.  The game lives in a team-private shared-memory record
 // (SmemGame): the 288-byte per-game state that persists in HBM between
 // launches, the board (piece id per square), 128-bit square sets kept up to
@@ -9,14 +9,15 @@
 // move.
 //
 // Move generation: non-Scout moves of the whole board come from four shifted
-// square sets; lane j of the team records those of its segment of 13, 7 or 4
-// from-squares (L = 8, 16, 32), each from-square's (at most four)
+// square sets; lane j of the team records those of its segment of 25, 13, 7
+// or 4 from-squares (L = 4, 8, 16, 32), each from-square's (at most four)
 // destinations OR-ed into the mask as one window of at most 21 bits (one or
-// two shared atomics).  Each Scout takes one lane; its slides come from the
-// row and column occupancy with find-first-set.  The scalar part of a ply
-// (apply, battle, rule state) runs on the team's first lane; all collectives
-// are team-masked, so the teams of a warp run in lockstep when their games
-// take the same path and serialize harmlessly when they do not.
+// two shared atomics).  Each Scout takes one lane (two on 4-lane teams); its
+// slides come from the row and column occupancy with find-first-set.  The
+// scalar part of a ply (apply, battle, rule state) runs on the team's first
+// lane; all collectives are team-masked, so the teams of a warp run in
+// lockstep when their games take the same path and serialize harmlessly when
+// they do not.
 //
 // Rules follow App. A of arXiv 2511.07312 (Tab. pieces, Tab. chase), the
 // two-square and chasing state machines of App. B.2-B.3, the k-move rule and
@@ -109,7 +110,7 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // ----------------------------------------------------------------- teams
 template <int L>
 struct Team {
-    static_assert(L == 32 || L == 16 || L == 8, "teams of 8, 16 or 32 lanes");
+    static_assert(L == 32 || L == 16 || L == 8 || L == 4, "teams of 4, 8, 16 or 32 lanes");
     int tl;          // lane within the team
     int base;        // first warp lane of the team
     unsigned mask;   // warp lanes of the team
@@ -492,7 +493,7 @@ __device__ __forceinline__ uint32_t bits_at(Set128 x, int off, int w)
 }
 
 // From-square segments: lane j of a team of L lanes owns squares
-// [kSegW*j, kSegW*j + kSegW) (13, 7 or 4 squares for L = 8, 16, 32).
+// [W*j, W*j + W) (W = 25, 13, 7 or 4 squares for L = 4, 8, 16, 32).
 template <int L> struct Seg {
     static constexpr int W = (kSquares + L - 1) / L;
     static constexpr int N = (kSquares + W - 1) / W;
@@ -592,56 +593,58 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
     if (write_mask && cnt && T.tl < NS) atomicAdd(&G->seg_cnt[T.tl], (uint32_t)cnt);
     // Scouts, one per lane: slides along the row and the column, stopping
     // before a lake or an own piece and on the first enemy piece.
-    int cnt_sc = 0;
-    const int spid = T.tl < 8 ? G->scout_pid[P][T.tl] : kNone;
-    if (spid != kNone && (G->c.flags[spid] & 1)) {
-        const int s = G->c.sq[spid], r = s / 10, c = s - 10 * r;
-        const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
-        const uint32_t rowocc = bits_at(Set128{own.lo | enm.lo, own.hi | enm.hi}, 10 * r, 10) | lake;
-        // slide lengths: empty squares east/west/north/south, then whether
-        // the blocker is an enemy (a capture ends the slide)
-        const uint32_t e = rowocc >> (c + 1);
-        const int runE = e ? __ffs(e) - 1 : 9 - c;
-        const int capE = (e && enemy_of(G->board[s + runE + 1], P)) ? 1 : 0;
-        const uint32_t w = rowocc & ((1u << c) - 1u);
-        const int hw = w ? 31 - __clz(w) : -1;
-        const int runW = c - 1 - hw;
-        const int capW = (hw >= 0 && enemy_of(G->board[10 * r + hw], P)) ? 1 : 0;
-        const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
-        const uint32_t n = colocc >> (r + 1);
-        const int runN = n ? __ffs(n) - 1 : 9 - r;
-        const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
-        const uint32_t so = colocc & ((1u << r) - 1u);
-        const int hs = so ? 31 - __clz(so) : -1;
-        const int runS = r - 1 - hs;
-        const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
-        const int ne = runE + capE, nw = runW + capW, nn = runN + capN, ns = runS + capS;
-        cnt_sc = ne + nw + nn + ns;
-        if (cnt_sc && (chase_on || s == ts_from)) {
-            Set128 d = or128(range128(s + 1, ne), range128(s - nw, nw));
-            d = or128(d, column128(c, r + 1, r + nn));
-            d = or128(d, column128(c, r - ns, r - 1));
-            d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
-            cnt_sc = popc128(d);
-            if (write_mask) or_row(G->mask, s, d);
-        } else if (cnt_sc && write_mask) {
-            // along the row: to-squares s-nw .. s+ne except s, one run of mask
-            // bits around bit 101s
-            const int b = 101 * s - nw;
-            const uint64_t v = (((1ull << (nw + ne + 1)) - 1ull) & ~(1ull << nw)) << (b & 31);
-            if (v) {
-                atomicOr(&G->mask[b >> 5], (uint32_t)v);
-                if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+    for (int si = T.tl; si < 8; si += L) {
+        const int spid = G->scout_pid[P][si];
+        if (spid != kNone && (G->c.flags[spid] & 1)) {
+            const int s = G->c.sq[spid], r = s / 10, c = s - 10 * r;
+            const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
+            const uint32_t rowocc = bits_at(Set128{own.lo | enm.lo, own.hi | enm.hi}, 10 * r, 10) | lake;
+            // slide lengths: empty squares east/west/north/south, then whether
+            // the blocker is an enemy (a capture ends the slide)
+            const uint32_t e = rowocc >> (c + 1);
+            const int runE = e ? __ffs(e) - 1 : 9 - c;
+            const int capE = (e && enemy_of(G->board[s + runE + 1], P)) ? 1 : 0;
+            const uint32_t w = rowocc & ((1u << c) - 1u);
+            const int hw = w ? 31 - __clz(w) : -1;
+            const int runW = c - 1 - hw;
+            const int capW = (hw >= 0 && enemy_of(G->board[10 * r + hw], P)) ? 1 : 0;
+            const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
+            const uint32_t n = colocc >> (r + 1);
+            const int runN = n ? __ffs(n) - 1 : 9 - r;
+            const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
+            const uint32_t so = colocc & ((1u << r) - 1u);
+            const int hs = so ? 31 - __clz(so) : -1;
+            const int runS = r - 1 - hs;
+            const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
+            const int ne = runE + capE, nw = runW + capW, nn = runN + capN, ns = runS + capS;
+            int cnt_sc = ne + nw + nn + ns;
+            if (cnt_sc && (chase_on || s == ts_from)) {
+                Set128 d = or128(range128(s + 1, ne), range128(s - nw, nw));
+                d = or128(d, column128(c, r + 1, r + nn));
+                d = or128(d, column128(c, r - ns, r - 1));
+                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+                cnt_sc = popc128(d);
+                if (write_mask) or_row(G->mask, s, d);
+            } else if (cnt_sc && write_mask) {
+                // along the row: to-squares s-nw .. s+ne except s, one run of mask
+                // bits around bit 101s
+                const int b = 101 * s - nw;
+                const uint64_t v = (((1ull << (nw + ne + 1)) - 1ull) & ~(1ull << nw)) << (b & 31);
+                if (v) {
+                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
+                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
+                }
+                // along the column: to-squares s+10k, mask bits 101s+10k
+                for (int k = -ns; k <= nn; ++k) {
+                    const int m = 101 * s + 10 * k;
+                    if (k) atomicOr(&G->mask[m >> 5], 1u << (m & 31));
+                }
             }
-            // along the column: to-squares s+10k, mask bits 101s+10k
-            for (int k = -ns; k <= nn; ++k) {
-                const int m = 101 * s + 10 * k;
-                if (k) atomicOr(&G->mask[m >> 5], 1u << (m & 31));
-            }
+            if (write_mask && cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
+            cnt += cnt_sc;
         }
-        if (write_mask && cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
     }
-    const int total = T.sum(cnt + cnt_sc);
+    const int total = T.sum(cnt);
     T.sync();
     return total;
 }

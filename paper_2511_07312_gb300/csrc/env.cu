@@ -25,7 +25,7 @@ struct st_env {
     int32_t* status = nullptr;      // [0] latched st_status, [1] first slot (min)
     int32_t* queue = nullptr;       // work counter of the persistent launch
     int wpb = 4, bps = 0, gpf = 1;  // launch shape of st_env_run
-    int gpw = 1;                    // games per warp (1 or 2)
+    int gpw = 1;                    // games per warp (1, 2, 4 or 8)
     int sms = 0;
     int max_bps = 0;
     cudaGraphExec_t graph = nullptr;
@@ -230,11 +230,11 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
 // Persistent form: each warp claims (32/L)*gpf slots at a time from a global
 // counter; each team plays n_steps plies in each of its slots, keeping the
 // game in shared memory.
-#ifndef ST_RUN_MIN_BLOCKS
-#define ST_RUN_MIN_BLOCKS 2   // 512 x 2 threads per SM -> at most 64 registers per thread
+#ifndef ST_RUN_MAX_REGS
+#define ST_RUN_MAX_REGS 72    // shared memory, not registers, bounds the resident teams
 #endif
 template <int L>
-__global__ void __launch_bounds__(512, ST_RUN_MIN_BLOCKS) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
+__global__ void __maxnreg__(ST_RUN_MAX_REGS) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
                                                  int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
                                                  int16_t* ply_ring, uint8_t* mask_ring)
 {
@@ -370,36 +370,43 @@ struct DeviceGuard {
 // Dynamic shared memory of one block of the persistent launch.
 size_t run_smem(int wpb, int gpw) { return (size_t)wpb * gpw * sizeof(SmemGame); }
 
+template <int L>
+cudaError_t run_occupancy_t(int wpb, int* occ)
+{
+    const size_t smem = run_smem(wpb, 32 / L);
+    cudaError_t e = cudaFuncSetAttribute(k_env_run<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<L>, 32 * wpb, smem);
+    if (e != cudaSuccess) cudaGetLastError();   // leave no pending error behind for later launches
+    return e;
+}
+
 cudaError_t run_occupancy(int wpb, int gpw, int* occ)
 {
-    const size_t smem = run_smem(wpb, gpw);
-    cudaError_t e;
-    if (gpw == 4) {
-        e = cudaFuncSetAttribute(k_env_run<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<8>, 32 * wpb, smem);
-    } else if (gpw == 2) {
-        e = cudaFuncSetAttribute(k_env_run<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<16>, 32 * wpb, smem);
-    } else {
-        e = cudaFuncSetAttribute(k_env_run<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<32>, 32 * wpb, smem);
+    switch (gpw) {
+    case 8: return run_occupancy_t<4>(wpb, occ);
+    case 4: return run_occupancy_t<8>(wpb, occ);
+    case 2: return run_occupancy_t<16>(wpb, occ);
+    default: return run_occupancy_t<32>(wpb, occ);
     }
-    return e;
+}
+
+template <int L>
+void launch_run_t(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
+                  int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+{
+    k_env_run<L><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
+        a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
 }
 
 void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
                 int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
 {
-    const size_t smem = run_smem(e->wpb, e->gpw);
-    if (e->gpw == 4)
-        k_env_run<8><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
-                                                             reward_ring, done_ring, ply_ring, mask_ring);
-    else if (e->gpw == 2)
-        k_env_run<16><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
-                                                              reward_ring, done_ring, ply_ring, mask_ring);
-    else
-        k_env_run<32><<<blocks, 32 * e->wpb, smem, e->stream>>>(a, e->queue, n_steps, ring_steps, e->gpf, action_ring,
-                                                              reward_ring, done_ring, ply_ring, mask_ring);
+    switch (e->gpw) {
+    case 8: launch_run_t<4>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
+    case 4: launch_run_t<8>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
+    case 2: launch_run_t<16>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
+    default: launch_run_t<32>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    }
 }
 
 }  // namespace
@@ -504,10 +511,15 @@ extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32
     ST_CHECK_ARG(e, "st_env_set_launch: null env");
     ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= 16, "st_env_set_launch: warps_per_block 1..16");
     ST_CHECK_ARG(blocks_per_sm >= 0 && blocks_per_sm <= 64, "st_env_set_launch: blocks_per_sm 0..64");
-    ST_CHECK_ARG(games_per_warp == 1 || games_per_warp == 2 || games_per_warp == 4,
-                 "st_env_set_launch: games_per_warp 1, 2 or 4");
+    ST_CHECK_ARG(games_per_warp == 1 || games_per_warp == 2 || games_per_warp == 4 || games_per_warp == 8,
+                 "st_env_set_launch: games_per_warp 1, 2, 4 or 8");
     ST_CHECK_ARG(games_per_fetch >= 1 && games_per_fetch <= 4096, "st_env_set_launch: games_per_fetch 1..4096");
     DeviceGuard guard(e->device);
+    int smem_max = 0;
+    ST_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->device));
+    ST_CHECK_ARG(run_smem(warps_per_block, games_per_warp) <= (size_t)smem_max,
+                 "st_env_set_launch: %d warps x %d games need %zu bytes of shared memory per block (device: %d)",
+                 warps_per_block, games_per_warp, run_smem(warps_per_block, games_per_warp), smem_max);
     int occ = 0;
     ST_CUDA(run_occupancy(warps_per_block, games_per_warp, &occ));
     ST_CHECK_ARG(occ >= 1, "st_env_set_launch: %d warps per block do not fit on an SM", warps_per_block);

@@ -57,7 +57,7 @@ def test_plain_step_64_games_1000_plies_bit_exact():
     np.testing.assert_array_equal(stats, ref["stats"].astype(np.int32))
 
 
-@pytest.mark.parametrize("gpw", [1, 2, 4])
+@pytest.mark.parametrize("gpw", [1, 2, 4, 8])
 def test_persistent_run_matches_plain_and_oracle(gpw):
     env = st.Env(64, seed=1)
     env.set_launch(4, 0, 1, games_per_warp=gpw)
@@ -69,7 +69,8 @@ def test_persistent_run_matches_plain_and_oracle(gpw):
 
 
 @pytest.mark.parametrize("wpb,gpf,gpw", [(1, 1, 1), (4, 3, 1), (8, 1, 1), (16, 7, 1), (1, 1, 2), (4, 3, 2),
-                                         (8, 1, 2), (16, 5, 2), (1, 1, 4), (4, 3, 4), (8, 1, 4), (16, 2, 4)])
+                                         (8, 1, 2), (16, 5, 2), (1, 1, 4), (4, 3, 4), (8, 1, 4), (16, 2, 4),
+                                         (1, 1, 8), (2, 3, 8), (4, 1, 8), (8, 2, 8)])
 def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
     # 1,000 slots (not a multiple of any block), 300 plies, ring of 7 rows
     N, S, R = 1000, 300, 7
@@ -92,6 +93,17 @@ def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
     for s in slots:
         r = oracle.env_run(5, 1, S, slot0=int(s), want_mask=False)
         np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
+
+
+def test_oversized_launch_shape_is_rejected_and_leaves_no_error_behind():
+    env = st.Env(64, seed=1)
+    with pytest.raises(st.StrategoError):
+        env.set_launch(16, 0, 1, games_per_warp=8)   # 128 games per block: more shared memory than a block may use
+    out = env.run(50)   # the previous shape is kept
+    env.stream.synchronize()
+    ref = oracle.env_run(1, 64, 50)
+    _compare({k: v.cpu().numpy() for k, v in out.items()}, ref)
+    st.Env(64, seed=2).close()
 
 
 def test_full_size_65536_games_2000_plies_sampled_slots():
