@@ -42,7 +42,7 @@ constexpr uint8_t kEmpty = 0xFF;
 constexpr uint8_t kLake = 0xFE;
 constexpr uint8_t kNone = 0xFF;
 constexpr int kMaskBytes = 1264;
-constexpr int kMaskWordsAlloc = 320;   // 316 used by the output layout, the rest kept zero
+constexpr int kMaskWordsAlloc = 316;   // the output layout: 1,264 bytes
 constexpr int kSegMax = 25;            // from-square segments (one per lane; 25 of 4 squares for 32 lanes)
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
 constexpr int kPiWords = 2 * kPiCap;   // each: hash of the chaser's pieces, hash of the chased side's pieces
@@ -98,9 +98,10 @@ struct __align__(16) SmemGame {
     uint8_t scout_pid[2][8];  // the Scouts of each side in piece-id order (kNone after the last)
     uint8_t pad[2];
     uint32_t seg_cnt[kSegMax];// moves per from-square segment in G->mask (written with the mask)
+    uint64_t pi_theirs[4];    // chased-side hash of chase positions n_pi-4 .. n_pi-1 (slot i & 3)
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 4 * kMaskWordsAlloc,
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 32 + 4 * kMaskWordsAlloc,
               "SmemGame layout");
 static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
@@ -227,11 +228,12 @@ __device__ __forceinline__ void bb_set(uint64_t* b, int s) { b[s >> 6] |= 1ull <
 __device__ __forceinline__ void bb_clr(uint64_t* b, int s) { b[s >> 6] &= ~(1ull << (s & 63)); }
 
 // Everything derived from the core and the board: square sets per player,
-// column occupancy, flag ids, Scout lists, the last two moves.  Needs
-// G->board.  Each side has at most 8 Scouts (Tab. pieces; setups, imported
+// column occupancy, flag ids, Scout lists, the last two moves, the cached
+// chased-side hashes of the newest chase positions (from the store pi).
+// Needs G->board.  Each side has at most 8 Scouts (Tab. pieces; setups, imported
 // positions and belief samples keep the piece counts).
 template <int L>
-__device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, Team<L>)
+__device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, const uint64_t* pi, Team<L>)
 {
     // out-of-line engine functions rebuild the team from the lane id rather
     // than reading the caller's copy through memory
@@ -267,6 +269,8 @@ __device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, Tea
             if (G->board[10 * r + c] < kPieces) col |= 1u << r;
         G->colocc[c] = (uint16_t)col;
     }
+    const int npi = G->c.n_pi;
+    for (int i = max(npi - 4, 0) + T.tl; i < npi; i += L) G->pi_theirs[i & 3] = pi[2 * i + 1];
     if (T.leader()) {
         G->h0 = (uint16_t)hist_at(G, ring, 0);
         G->h1 = (uint16_t)hist_at(G, ring, 1);
@@ -363,21 +367,27 @@ __device__ __forceinline__ bool chase_blocks(const SmemGame* G, const PlyCtx& x,
     const uint64_t mine = G->c.hash_side[P] ^ zkey(pid, from) ^ zkey(pid, to);
     const uint64_t theirs = G->c.hash_side[1 - P];
     const int n = G->c.n_pi;
-    for (int i = 0; i < n; ++i)
-        if (pi[2 * i] == mine && pi[2 * i + 1] == theirs) return true;
+    // chased-side hashes of the newest four positions from shared memory; the
+    // store is read for a chaser hash only where the chased side matches
+    for (int i = max(n - 4, 0); i < n; ++i)
+        if (G->pi_theirs[i & 3] == theirs && pi[2 * i] == mine) return true;
+    for (int i = 0; i < n - 4; ++i)
+        if (pi[2 * i + 1] == theirs && pi[2 * i] == mine) return true;
     return false;
 }
 
 // Can any of P's moves be chase-blocked?  A move of P changes only P's
 // pieces, so a stored chase position can be recreated only if the chased
-// side's pieces stand exactly where they stood then.  Team-uniform.
+// side's pieces stand exactly where they stood then.  The newest four
+// positions are checked in shared memory, older ones in the store.
+// Team-uniform.
 template <int L>
 __device__ __forceinline__ bool chase_live(const SmemGame* G, const Team<L>& T, const uint64_t* pi, int P)
 {
     const uint64_t theirs = G->c.hash_side[1 - P];
     const int n = G->c.n_pi;
-    bool hit = false;
-    for (int i = T.tl; i < n; i += L) hit |= pi[2 * i + 1] == theirs;
+    bool hit = T.tl < 4 && T.tl < n && G->pi_theirs[T.tl] == theirs;
+    for (int i = T.tl; i < n - 4; i += L) hit |= pi[2 * i + 1] == theirs;
     return T.any(hit);
 }
 
@@ -834,7 +844,11 @@ __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* r
         // chase state
         if (cls == kClThreat) {
             if (c.chaser != P) { c.chaser = (uint8_t)P; c.n_pi = 0; c.chase_plies = 0; }
-            if (c.n_pi < kPiCap) { pi[2 * c.n_pi] = h; pi[2 * c.n_pi + 1] = hq; c.n_pi += 1; }
+            if (c.n_pi < kPiCap) {
+                pi[2 * c.n_pi] = h; pi[2 * c.n_pi + 1] = hq;
+                G->pi_theirs[c.n_pi & 3] = hq;
+                c.n_pi += 1;
+            }
             c.chase_plies += 1;
         } else if (cls == kClEvade && c.chaser == 1 - P) {
             c.chase_plies += 1;
@@ -889,7 +903,7 @@ __device__ __noinline__ void reset_game(SmemGame* G, Team<L>, uint32_t k0, uint3
     const uint64_t h0 = side_hash(G, T, 0), h1 = side_hash(G, T, 1);
     if (T.leader()) { G->c.hash_side[0] = h0; G->c.hash_side[1] = h1; }
     build_board(G, T);
-    derive_state(G, (const uint16_t*)nullptr, T);
+    derive_state(G, (const uint16_t*)nullptr, (const uint64_t*)nullptr, T);
 }
 
 // ----------------------------------------------------------------- endings

@@ -198,7 +198,7 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     uint64_t* pi = A.pi + (size_t)g * kPiWords;
     load_core(G, A.core + g, T);
     build_board(G, T);
-    derive_state(G, ring, T);
+    derive_state(G, ring, pi, T);
     const int P = G->c.ply & 1;
     int n = 0;
     if (G->c.terminated) zero_mask(G, T);
@@ -256,7 +256,7 @@ __global__ void __maxnreg__(ST_RUN_MAX_REGS) k_env_run(EnvArgs A, int32_t* queue
             uint64_t* pi = A.pi + (size_t)g * kPiWords;
             load_core(G, A.core + g, T);
             build_board(G, T);
-            derive_state(G, ring, T);
+            derive_state(G, ring, pi, T);
             int n = 0;
             if (G->c.terminated) zero_mask(G, T);
             else n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);

@@ -164,7 +164,7 @@ __device__ __forceinline__ int rollout_one(RolloutSmem* S, const Team<L>& T, con
     T.sync();
     for (int i = lane; i < 40; i += L) G->c.type[opp * 40 + i] = S->types[i];
     T.sync();
-    derive_state(G, S->ring, T);   // bitboards and flag ids of the sampled types
+    derive_state(G, S->ring, S->pi, T);   // bitboards and flag ids of the sampled types
     int n = gen_moves(G, T, searcher, Rl.flags, false, true, S->pi);
     int code = 0, winner = -1;
     if (n == 0) start_end(G, T, Rl, S->pi, code, winner);

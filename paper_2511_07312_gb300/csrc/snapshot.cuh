@@ -110,7 +110,7 @@ __device__ __forceinline__ int import_position(SmemGame* G, const st_position* i
     bad = T.shfl(bad, 0);
     T.sync();
     if (bad) return bad;
-    derive_state(G, ring, T);
+    derive_state(G, ring, pi, T);
     return 0;
 }
 
