@@ -186,7 +186,7 @@ st_status st_env_step(st_env* env, const int16_t* actions, int16_t* action_out, 
 st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
                      int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring);
 
-/* Launch shape of st_env_run: warps per block (1..16), blocks per SM (0 =
+/* Launch shape of st_env_run: warps per block (1..8), blocks per SM (0 =
  * occupancy maximum), games a warp steps side by side (1, 2, 4 or 8: teams
  * of 32, 16, 8 or 4 lanes) and slots each team claims per queue fetch (>=1).
  * Results do not depend on the shape. */

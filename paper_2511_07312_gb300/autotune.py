@@ -14,7 +14,7 @@ import torch
 
 from . import Env, version
 
-WARPS_PER_BLOCK = (2, 4, 8, 16)
+WARPS_PER_BLOCK = (1, 2, 4, 8)
 GAMES_PER_WARP = (1, 2, 4, 8)
 GAMES_PER_FETCH = (1, 4)
 

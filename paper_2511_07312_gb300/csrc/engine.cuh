@@ -366,7 +366,7 @@ __device__ __forceinline__ bool chase_blocks(const SmemGame* G, const PlyCtx& x,
     if (from == x.h1_to && to == x.h1_from) return false;
     const uint64_t mine = G->c.hash_side[P] ^ zkey(pid, from) ^ zkey(pid, to);
     const uint64_t theirs = G->c.hash_side[1 - P];
-    const int n = G->c.n_pi;
+    const int n = min((int)G->c.n_pi, kPiCap);
     // chased-side hashes of the newest four positions from shared memory; the
     // store is read for a chaser hash only where the chased side matches
     for (int i = max(n - 4, 0); i < n; ++i)
@@ -385,7 +385,7 @@ template <int L>
 __device__ __forceinline__ bool chase_live(const SmemGame* G, const Team<L>& T, const uint64_t* pi, int P)
 {
     const uint64_t theirs = G->c.hash_side[1 - P];
-    const int n = G->c.n_pi;
+    const int n = min((int)G->c.n_pi, kPiCap);
     bool hit = T.tl < 4 && T.tl < n && G->pi_theirs[T.tl] == theirs;
     for (int i = T.tl; i < n - 4; i += L) hit |= pi[2 * i + 1] == theirs;
     return T.any(hit);

@@ -230,11 +230,11 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
 // Persistent form: each warp claims (32/L)*gpf slots at a time from a global
 // counter; each team plays n_steps plies in each of its slots, keeping the
 // game in shared memory.
-#ifndef ST_RUN_MAX_REGS
-#define ST_RUN_MAX_REGS 72    // shared memory, not registers, bounds the resident teams
-#endif
+// At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
+// thread; shared memory, not registers, bounds the resident teams.
+constexpr int kRunMaxWarps = 8;
 template <int L>
-__global__ void __maxnreg__(ST_RUN_MAX_REGS) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
+__global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
                                                  int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
                                                  int16_t* ply_ring, uint8_t* mask_ring)
 {
@@ -509,7 +509,8 @@ extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32
                                        int32_t games_per_warp, int32_t games_per_fetch)
 {
     ST_CHECK_ARG(e, "st_env_set_launch: null env");
-    ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= 16, "st_env_set_launch: warps_per_block 1..16");
+    ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= kRunMaxWarps, "st_env_set_launch: warps_per_block 1..%d",
+                 kRunMaxWarps);
     ST_CHECK_ARG(blocks_per_sm >= 0 && blocks_per_sm <= 64, "st_env_set_launch: blocks_per_sm 0..64");
     ST_CHECK_ARG(games_per_warp == 1 || games_per_warp == 2 || games_per_warp == 4 || games_per_warp == 8,
                  "st_env_set_launch: games_per_warp 1, 2, 4 or 8");

@@ -68,8 +68,8 @@ def test_persistent_run_matches_plain_and_oracle(gpw):
     _compare(gpu, ref)
 
 
-@pytest.mark.parametrize("wpb,gpf,gpw", [(1, 1, 1), (4, 3, 1), (8, 1, 1), (16, 7, 1), (1, 1, 2), (4, 3, 2),
-                                         (8, 1, 2), (16, 5, 2), (1, 1, 4), (4, 3, 4), (8, 1, 4), (16, 2, 4),
+@pytest.mark.parametrize("wpb,gpf,gpw", [(1, 1, 1), (4, 3, 1), (8, 1, 1), (8, 7, 1), (1, 1, 2), (4, 3, 2),
+                                         (8, 1, 2), (8, 5, 2), (1, 1, 4), (4, 3, 4), (8, 1, 4), (8, 2, 4),
                                          (1, 1, 8), (2, 3, 8), (4, 1, 8), (8, 2, 8)])
 def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
     # 1,000 slots (not a multiple of any block), 300 plies, ring of 7 rows
@@ -98,7 +98,7 @@ def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
 def test_oversized_launch_shape_is_rejected_and_leaves_no_error_behind():
     env = st.Env(64, seed=1)
     with pytest.raises(st.StrategoError):
-        env.set_launch(16, 0, 1, games_per_warp=8)   # 128 games per block: more shared memory than a block may use
+        env.set_launch(16, 0, 1, games_per_warp=8)   # more warps per block than the persistent kernel allows
     out = env.run(50)   # the previous shape is kept
     env.stream.synchronize()
     ref = oracle.env_run(1, 64, 50)
