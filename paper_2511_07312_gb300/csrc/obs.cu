@@ -8,9 +8,9 @@
 // log once per chunk (App. B.1: compact records, states reconstructed on
 // demand).  It writes the replayed state of every item to a scratch record
 // (or an st_position), plus the legal mask.  k_obs_emit: one warp per item
-// turns the record into the 487 planes, four squares of one channel per lane
-// per store (32-bit uint8 stores and 64-bit bf16 stores, coalesced across the
-// warp).
+// turns the record into the 487 planes: lane l owns four squares, all lanes
+// walk the channels together, and each channel row is one coalesced 100-byte
+// uint8 store and one 200-byte bf16 store per warp.
 #include <mutex>
 #include "engine.cuh"
 #include "features.cuh"
@@ -204,68 +204,151 @@ __device__ __forceinline__ uint32_t ratio_code(uint32_t num, uint32_t den)
     return u8 | ((bits >> 16) << 8);
 }
 
-__device__ __forceinline__ uint32_t cell(const EmitSmem* E, int ch, int s, int me)
+// Channel-major emission: lane l < 25 owns squares 4l .. 4l+3 and keeps what
+// its squares need in registers; all lanes walk the 487 channels together
+// (no divergence between lanes), each channel row written with one 4-byte
+// uint8 store and one 8-byte bf16 store per lane, 100 / 200 contiguous bytes
+// per warp.  A cell code is u8 | bf16 << 8.
+struct RowOut {
+    uint8_t* u8;
+    uint16_t* bf;
+    int l;       // owning lane (squares 4l .. 4l+3)
+    bool on;     // l < 25
+    __device__ __forceinline__ void codes(int ch, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const
+    {
+        if (!on) return;
+        if (u8)
+            *reinterpret_cast<uint32_t*>(u8 + 100 * ch + 4 * l) =
+                (c0 & 0xFFu) | ((c1 & 0xFFu) << 8) | ((c2 & 0xFFu) << 16) | ((c3 & 0xFFu) << 24);
+        if (bf)
+            *reinterpret_cast<uint2*>(bf + 100 * ch + 4 * l) =
+                make_uint2((c0 >> 8) | ((c1 >> 8) << 16), (c2 >> 8) | ((c3 >> 8) << 16));
+    }
+    // cells of value 0 or 1 (u8 1, bf16 1.0)
+    __device__ __forceinline__ void bits(int ch, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) const
+    {
+        if (!on) return;
+        if (u8) *reinterpret_cast<uint32_t*>(u8 + 100 * ch + 4 * l) = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+        if (bf)
+            *reinterpret_cast<uint2*>(bf + 100 * ch + 4 * l) =
+                make_uint2((b0 | (b1 << 16)) * 0x3F80u, (b2 | (b3 << 16)) * 0x3F80u);
+    }
+};
+
+// bit k of four 64-bit words as 0/1
+#define ST_BITS4(w, k) (uint32_t)(((w)[0] >> (k)) & 1ull), (uint32_t)(((w)[1] >> (k)) & 1ull), \
+                       (uint32_t)(((w)[2] >> (k)) & 1ull), (uint32_t)(((w)[3] >> (k)) & 1ull)
+
+__device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const RowOut& o)
 {
     const ItemState& st = E->s;
-    const uint8_t occ = E->board[s];
-    const bool piece = occ < kPieces;
-    const int side = piece ? occ / 40 : -1;
-    const bool mine = side == me;
-    const uint8_t f = piece ? st.c.flags[occ] : 0;
-    if (ch < 12) return (piece && mine && st.c.type[occ] == ch) ? kOne : 0u;
-    if (ch < 36) {
-        const int T = ch < 24 ? ch - 12 : ch - 24;
-        const int want = ch < 24 ? 1 - me : me;
-        if (!piece || side != want) return 0u;
-        if (f & 2) return st.c.type[occ] == T ? kRatioOne : 0u;
-        if (f & 8) return T == kScout ? kRatioOne : 0u;
-        return E->ratio[side][(f & 4) ? 1 : 0][T];
+    const int s0 = o.on ? 4 * o.l : 0;
+    int occ[4], side[4], ty[4];
+    uint32_t fl[4];
+    bool pc[4], mn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        occ[i] = E->board[s0 + i];
+        pc[i] = occ[i] < kPieces;
+        side[i] = pc[i] ? occ[i] / 40 : -1;
+        mn[i] = side[i] == me;
+        fl[i] = pc[i] ? st.c.flags[occ[i]] : 0u;
+        ty[i] = pc[i] ? st.c.type[occ[i]] : 0xFF;
     }
-    if (ch < 43) {
-        switch (ch) {
-            case 36: return (piece && mine && !(f & 2)) ? kOne : 0u;
-            case 37: return (piece && !mine && !(f & 2)) ? kOne : 0u;
-            case 38: return occ == kEmpty ? kOne : 0u;
-            case 39: return (piece && mine && (f & 4)) ? kOne : 0u;
-            case 40: return (piece && !mine && (f & 4)) ? kOne : 0u;
-            case 41: return E->frac41;
-            default: return E->frac42;
+    // 0-11: own pieces by type
+    for (int t = 0; t < 12; ++t)
+        o.bits(t, pc[0] && mn[0] && ty[0] == t, pc[1] && mn[1] && ty[1] == t, pc[2] && mn[2] && ty[2] == t,
+               pc[3] && mn[3] && ty[3] == t);
+    // 12-23 (opponent's pieces), 24-35 (own pieces): probability of each type
+    for (int g = 0; g < 2; ++g) {
+        const int want = g == 0 ? 1 - me : me;
+        int kind[4], row[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            kind[i] = (!pc[i] || side[i] != want) ? 0 : ((fl[i] & 2) ? 1 : ((fl[i] & 8) ? 2 : 3));
+            row[i] = 2 * (side[i] < 0 ? 0 : side[i]) + ((fl[i] & 4) ? 1 : 0);
+        }
+        const uint32_t* ratio = &E->ratio[0][0][0];
+        for (int T = 0; T < 12; ++T) {
+            uint32_t c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                c[i] = kind[i] == 1 ? (ty[i] == T ? kRatioOne : 0u)
+                     : kind[i] == 2 ? (T == kScout ? kRatioOne : 0u)
+                     : kind[i] == 3 ? ratio[12 * row[i] + T] : 0u;
+            o.codes(12 + 12 * g + T, c[0], c[1], c[2], c[3]);
         }
     }
-    if (ch < 109) {
-        const bool want_mine = ch < 76;
-        if (!piece || mine != want_mine) return 0u;
-        return ((st.fa[occ] >> (ch - (want_mine ? 43 : 76))) & 1ull) ? kOne : 0u;
+    // 36-42
+    o.bits(36, pc[0] && mn[0] && !(fl[0] & 2), pc[1] && mn[1] && !(fl[1] & 2), pc[2] && mn[2] && !(fl[2] & 2),
+           pc[3] && mn[3] && !(fl[3] & 2));
+    o.bits(37, pc[0] && !mn[0] && !(fl[0] & 2), pc[1] && !mn[1] && !(fl[1] & 2), pc[2] && !mn[2] && !(fl[2] & 2),
+           pc[3] && !mn[3] && !(fl[3] & 2));
+    o.bits(38, occ[0] == kEmpty, occ[1] == kEmpty, occ[2] == kEmpty, occ[3] == kEmpty);
+    o.bits(39, pc[0] && mn[0] && (fl[0] & 4), pc[1] && mn[1] && (fl[1] & 4), pc[2] && mn[2] && (fl[2] & 4),
+           pc[3] && mn[3] && (fl[3] & 4));
+    o.bits(40, pc[0] && !mn[0] && (fl[0] & 4), pc[1] && !mn[1] && (fl[1] & 4), pc[2] && !mn[2] && (fl[2] & 4),
+           pc[3] && !mn[3] && (fl[3] & 4));
+    o.codes(41, E->frac41, E->frac41, E->frac41, E->frac41);
+    o.codes(42, E->frac42, E->frac42, E->frac42, E->frac42);
+    // 43-75 / 76-108: history features of the piece on the square (own / opponent)
+    for (int g = 0; g < 2; ++g) {
+        uint64_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = (pc[i] && mn[i] == (g == 0)) ? st.fa[occ[i]] : 0ull;
+        for (int k = 0; k < 33; ++k) o.bits(43 + 33 * g + k, ST_BITS4(w, k));
     }
-    if (ch < 131) {
-        const bool want_mine = ch < 120;
-        const int ti = ch - (want_mine ? 109 : 120);
-        const int pid = s < 40 ? s : (s >= 60 ? s - 20 : -1);
-        if (pid < 0 || ((pid / 40) == me) != want_mine) return 0u;
-        if (st.c.flags[pid] & 1) return 0u;
-        const int t = st.c.type[pid];
-        const int idx = t <= kMarshal ? t : (t == kBomb ? 10 : -1);
-        return idx == ti ? kOne : 0u;
+    // 109-119 / 120-130: captured piece whose start square this is, by type
+    for (int g = 0; g < 2; ++g) {
+        int idx[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s = s0 + i;
+            const int pid = s < 40 ? s : (s >= 60 ? s - 20 : -1);
+            idx[i] = -2;
+            if (pid >= 0 && ((pid / 40) == me) == (g == 0) && !(st.c.flags[pid] & 1)) {
+                const int t = st.c.type[pid];
+                idx[i] = t <= kMarshal ? t : (t == kBomb ? 10 : -1);
+            }
+        }
+        for (int ti = 0; ti < 11; ++ti)
+            o.bits(109 + 11 * g + ti, idx[0] == ti, idx[1] == ti, idx[2] == ti, idx[3] == ti);
     }
-    if (ch < 251) {
-        const bool want_mine = ch < 191;
-        const int bit = ch - (want_mine ? 131 : 191);
-        const int want_side = want_mine ? me : 1 - me;
-        return ((E->death[want_side][s] >> bit) & 1ull) ? kOne : 0u;
+    // 131-190 / 191-250: deaths on the square by cause and rank (own / opponent)
+    for (int g = 0; g < 2; ++g) {
+        const int want_side = g == 0 ? me : 1 - me;
+        uint64_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = E->death[want_side][s0 + i];
+        for (int k = 0; k < 60; ++k) o.bits(131 + 60 * g + k, ST_BITS4(w, k));
     }
-    if (ch < 355) {
-        const bool want_mine = ch < 303;
-        if (!piece || mine != want_mine) return 0u;
-        return ((st.fb[occ] >> (ch - (want_mine ? 251 : 303))) & 1ull) ? kOne : 0u;
+    // 251-302 / 303-354: further history features (own / opponent)
+    for (int g = 0; g < 2; ++g) {
+        uint64_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = (pc[i] && mn[i] == (g == 0)) ? st.fb[occ[i]] : 0ull;
+        for (int k = 0; k < 52; ++k) o.bits(251 + 52 * g + k, ST_BITS4(w, k));
     }
-    if (ch < 455) return (piece && start_square(occ) == ch - 355) ? kOne : 0u;
-    const int j = ch - 455;
-    const int h = st.hist[j];
-    if (h == 0xFFFF) return 0u;
-    if (s == h % 100) return kOne;
-    if (s == h / 100) return kMinus;
-    return 0u;
+    // 355-454: the piece on the square started on square ch - 355
+    {
+        int ss[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ss[i] = pc[i] ? start_square(occ[i]) : -1;
+        for (int q = 0; q < 100; ++q) o.bits(355 + q, ss[0] == q, ss[1] == q, ss[2] == q, ss[3] == q);
+    }
+    // 455-486: the last 32 moves, +1 on the to-square and -1 on the from-square
+    for (int j = 0; j < 32; ++j) {
+        const int h = st.hist[j];
+        uint32_t c[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s = s0 + i;
+            c[i] = h == 0xFFFF ? 0u : (s == h % 100 ? kOne : (s == h / 100 ? kMinus : 0u));
+        }
+        o.codes(455 + j, c[0], c[1], c[2], c[3]);
+    }
 }
+#undef ST_BITS4
 
 __global__ void k_obs_emit(EmitArgs A)
 {
@@ -338,17 +421,12 @@ __global__ void k_obs_emit(EmitArgs A)
     }
     __syncwarp();
     const int me = (A.player && A.player[b] >= 0) ? (A.player[b] & 1) : (E->s.c.ply & 1);
-    for (int g = lane; g < kGroups; g += 32) {
-        const int ch = g / 25;
-        const int s0 = (g - 25 * ch) * 4;
-        const uint32_t c0 = cell(E, ch, s0, me), c1 = cell(E, ch, s0 + 1, me);
-        const uint32_t c2 = cell(E, ch, s0 + 2, me), c3 = cell(E, ch, s0 + 3, me);
-        if (u8)
-            reinterpret_cast<uint32_t*>(u8)[g] = (c0 & 0xFFu) | ((c1 & 0xFFu) << 8) | ((c2 & 0xFFu) << 16) |
-                                                 ((c3 & 0xFFu) << 24);
-        if (bf)
-            reinterpret_cast<uint2*>(bf)[g] = make_uint2((c0 >> 8) | ((c1 >> 8) << 16), (c2 >> 8) | ((c3 >> 8) << 16));
-    }
+    RowOut o;
+    o.u8 = u8;
+    o.bf = bf;
+    o.l = lane;
+    o.on = lane < 25;
+    emit_planes(E, me, o);
 }
 
 ReplayArgs replay_args(const uint8_t* setups, const int16_t* actions, int32_t log_len, int32_t num_logs,
