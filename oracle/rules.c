@@ -621,8 +621,11 @@ int or_import(or_game* g, const uint8_t in[OR_POS_BYTES], const or_rules* rules,
         g->ts_pid[p] = in[248 + p] == 0xFF ? -1 : in[248 + p];
         g->ts_len[p] = in[250 + p];
         for (int i = 0; i < 4; ++i) g->ts_sq[p][i] = in[252 + 4 * p + i] == 0xFF ? -1 : in[252 + 4 * p + i];
-        if (g->ts_pid[p] >= 0 && (g->ts_len[p] < 2 || g->ts_len[p] > 4)) return -8;
+        if (g->ts_pid[p] >= 0 && (g->ts_pid[p] >= OR_NPIECE || g->ts_len[p] < 2 || g->ts_len[p] > 4)) return -8;
         if (g->ts_pid[p] < 0 && g->ts_len[p] != 0) return -8;
+        /* the squares of the piece's last moves lie on the board */
+        for (int i = 0; i < g->ts_len[p] && i < 4; ++i)
+            if (g->ts_sq[p][i] < 0 || g->ts_sq[p][i] >= OR_NSQ || or_is_lake(g->ts_sq[p][i])) return -8;
     }
     for (int i = 0; i < OR_HIST; ++i) g->hist[i] = (uint16_t)(in[272 + 2 * i] | (in[273 + 2 * i] << 8));
     /* chase positions: undo the chase plies from the current board */
@@ -641,7 +644,7 @@ int or_import(or_game* g, const uint8_t in[OR_POS_BYTES], const or_rules* rules,
                 nt++;
             }
             int f = g->hist[i] / 100, t = g->hist[i] % 100;
-            if (b[t] < 0 || b[f] != -1) return -12;
+            if (f >= OR_NSQ || b[t] < 0 || b[f] != -1) return -12;
             b[f] = b[t];
             b[t] = -1;
         }

@@ -374,3 +374,21 @@ def test_snapshot_roundtrip():
         out, _, _ = oracle.apply(p, g["actions"][i, t:t + n])
         ref = oracle.replay_positions(g["setups"], g["actions"], [i], [t + n])[0]
         np.testing.assert_array_equal(out, ref)
+
+
+def test_import_rejects_corrupt_rule_state():
+    # the snapshot checks the GPU import makes (App. B.2 two-square record;
+    # chase history), one corrupt field at a time on a valid position
+    pcs = [(0, MARSHAL, sq("e4"), F_MOVED), (0, FLAG, sq("a1"), 0), (1, SCOUT, sq("e6"), F_MOVED),
+           (1, FLAG, sq("j10"), 0)]
+    good = make_position(pcs, ply=4, battleless=4, ts={0: (0, [sq("e3"), sq("e4")])})
+    assert oracle.import_check(good) == 0
+    bad = good.copy(); bad[248] = 100                    # two-square piece id beyond the 80 pieces
+    assert oracle.import_check(bad) == -8
+    bad = good.copy(); bad[253] = 100                    # a two-square square off the board
+    assert oracle.import_check(bad) == -8
+    bad = good.copy(); bad[253] = sq("c5")               # a two-square square in a lake
+    assert oracle.import_check(bad) == -8
+    # a chase whose history move starts off the board
+    chase = make_position(pcs, ply=4, battleless=4, chaser=0, chase_plies=1, hist=[65000])
+    assert oracle.import_check(chase) == -12
