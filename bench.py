@@ -118,6 +118,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def job_rate(units_per_rank, ms_local, world, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaling run: the units all ranks
+    processed divided by the slowest rank's time (max over ranks).  Returns
+    (units per second, that time in ms)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return float(units_per_rank) * world / (ms / 1000.0), ms
+
+
 def kernel_sources_sha256():
     import glob
     import hashlib
@@ -250,14 +263,8 @@ def main():
         end.synchronize()
     torch.cuda.synchronize()
     barrier()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = job_rate(float(N) * S * args.steps, start.elapsed_time(end), world, dist, dev)
     env.sync()
-    env_steps = float(N) * S * args.steps * world
-    value = env_steps / (ms / 1000.0)
     per_launch_s = ms / 1000.0 / args.steps
     bytes_per_launch = float(N) * S * BYTES_PER_ENV_STEP
     peak, peak_kind = peaks()
