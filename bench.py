@@ -131,16 +131,18 @@ def job_rate(units_per_rank, ms_local, world, dist=None, device="cpu"):
     return float(units_per_rank) * world / (ms / 1000.0), ms
 
 
+# The sources the step kernel is compiled from (env.cu and what it includes).
+STEP_KERNEL_SOURCES = ("paper_2511_07312_gb300/csrc/env.cu", "paper_2511_07312_gb300/csrc/engine.cuh",
+                       "paper_2511_07312_gb300/csrc/snapshot.cuh", "paper_2511_07312_gb300/csrc/host_common.h",
+                       "include/stratego.h")
+
+
 def kernel_sources_sha256():
-    import glob
     import hashlib
-    root = os.path.join(ROOT, "paper_2511_07312_gb300", "csrc")
     h = hashlib.sha256()
-    files = glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh")) + \
-        glob.glob(os.path.join(root, "*.h"))
-    for f in sorted(files):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for rel in STEP_KERNEL_SOURCES:
+        h.update(os.path.basename(rel).encode())
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()
 
 
@@ -347,7 +349,7 @@ def main():
                              "traffic": (None if measured_traffic_per_env_step() is None
                                          else measured_traffic_per_env_step() * float(N) * S),
                              "traffic_note": "ncu dram__bytes_read.sum+dram__bytes_write.sum per launch, scaled "
-                                             "from a 16,384 x 100 capture (profiles/k_env_run_traffic.md)",
+                                             "from a 16,384 x 400 capture (profiles/k_env_run_traffic.md)",
                              "peak_kind": peak_kind + " hbm_gbs (copy, burst)",
                              "algorithmic_bytes_per_env_step": BYTES_PER_ENV_STEP, "kernel": "k_env_run"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
