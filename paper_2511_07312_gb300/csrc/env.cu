@@ -2,8 +2,8 @@
 // simulator): N independent game slots kept in HBM, stepped one ply per
 // launch (st_env_step, the plain path) or many plies per persistent launch
 // (st_env_run), with auto-reset, snapshots and per-slot counters.  The
-// persistent launch runs one or two games per warp (teams of 32 or 16
-// lanes), the shape chosen by st_env_set_launch.
+// persistent launch runs 1, 2, 4 or 8 games per warp (teams of 32, 16, 8 or
+// 4 lanes), the shape chosen by st_env_set_launch.
 #include <algorithm>
 #include <cstring>
 #include "engine.cuh"
@@ -227,9 +227,9 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     if (!illegal) store_core(G, A.core + g, T);
 }
 
-// Persistent form: each warp claims (32/L)*gpf slots at a time from a global
-// counter; each team plays n_steps plies in each of its slots, keeping the
-// game in shared memory.
+// Persistent form: each team claims gpf slots at a time from a global
+// counter and plays n_steps plies in each of them, keeping the game in
+// shared memory.
 // At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
 // thread; shared memory, not registers, bounds the resident teams.
 constexpr int kRunMaxWarps = 8;
@@ -241,14 +241,12 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<L> T;
     SmemGame* G = team_game<L>(smem);
-    const int lane = threadIdx.x & 31;
-    constexpr int kTeams = 32 / L;
     for (;;) {
-        int start = 0;
-        if (lane == 0) start = atomicAdd(queue, kTeams * gpf);
-        start = __shfl_sync(0xFFFFFFFFu, start, 0);
-        if (start >= A.N) break;
-        const int first = start + (lane / L) * gpf;
+        // each team claims its own slots: no collective spans more than one team
+        int first = 0;
+        if (T.leader()) first = atomicAdd(queue, gpf);
+        first = T.shfl(first, 0);
+        if (first >= A.N) break;
         for (int gi = 0; gi < gpf; ++gi) {
             const int g = first + gi;
             if (g >= A.N) break;
