@@ -37,7 +37,7 @@ def load(num_games, device=0):
         return None
 
 
-def tune(num_games, device=0, plies=200, reps=2, force=False, verbose=False):
+def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False):
     """Return {"warps_per_block", "games_per_warp", "games_per_fetch",
     "env_steps_per_s"} of the fastest shape, timed with CUDA events."""
     if not force:
