@@ -99,9 +99,10 @@ struct __align__(16) SmemGame {
     uint8_t pad[2];
     uint32_t seg_cnt[kSegMax];// moves per from-square segment in G->mask (written with the mask)
     uint64_t pi_theirs[4];    // chased-side hash of chase positions n_pi-4 .. n_pi-1 (slot i & 3)
+    uint32_t stat[8];         // counters of the current launch (kept by the env's step loop)
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 32 + 4 * kMaskWordsAlloc,
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 32 + 32 + 4 * kMaskWordsAlloc,
               "SmemGame layout");
 static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root

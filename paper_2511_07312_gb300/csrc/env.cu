@@ -258,13 +258,15 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             int n = 0;
             if (G->c.terminated) zero_mask(G, T);
             else n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
-            uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            // the launch's counters live in shared memory, not in registers
+            // that every engine call would have to save
+            for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
                 const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal);
                 const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
                 if (T.leader()) {
-                    count_result(st, r);
+                    count_result(G->stat, r);
                     if (action_ring) action_ring[o] = (int16_t)r.action;
                     if (reward_ring) reward_ring[o] = (int8_t)reward_of(r);
                     if (done_ring) done_ring[o] = (uint8_t)r.code;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             if (T.leader()) {
                 uint32_t* gs = A.stats + 8 * (size_t)g;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) gs[k] += st[k];
+                for (int k = 0; k < 8; ++k) gs[k] += G->stat[k];
                 G->c.n_legal = (uint16_t)n;
             }
             store_core(G, A.core + g, T);
