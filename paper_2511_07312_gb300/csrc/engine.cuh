@@ -665,7 +665,7 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
 // [100*W*j, 100*W*(j+1)), so the per-segment counts written with the mask
 // pick the segment first and only its mask words are scanned.
 template <int L>
-__device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
+__device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
 {
     const Team<L> T;
     constexpr int SW = Seg<L>::W, NS = Seg<L>::N;
@@ -721,6 +721,12 @@ __device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t i
     return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
 
+template <int L>
+__device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
+{
+    return select_impl<L>(G, idx);
+}
+
 __device__ __forceinline__ bool mask_has(const SmemGame* G, int a)
 {
     return a >= 0 && a < 10000 && ((G->mask[a >> 5] >> (a & 31)) & 1u);
@@ -736,7 +742,7 @@ __device__ __forceinline__ bool flag_dead(const SmemGame* G, int side)
 // Plays action a for the player to move.  ring/pi: this game's history ring
 // and chase-position store.
 template <int L>
-__device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* ring, uint64_t* pi)
+__device__ __forceinline__ void apply_impl(SmemGame* G, int a, uint16_t* ring, uint64_t* pi)
 {
     const Team<L> T;
     if (T.leader() && a >= 0 && a < 10000) {
@@ -861,6 +867,22 @@ __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* r
         G->h0 = (uint16_t)a;
     }
     T.sync();
+}
+
+template <int L>
+__device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* ring, uint64_t* pi)
+{
+    apply_impl<L>(G, a, ring, pi);
+}
+
+// The idx-th legal action (a < 0) or action a, then played: selection and
+// the move in one call (the rollouts' ply).  Returns the action.
+template <int L>
+__device__ __noinline__ int select_apply(SmemGame* G, Team<L>, int a, uint32_t idx, uint16_t* ring, uint64_t* pi)
+{
+    if (a < 0) a = select_impl<L>(G, idx);
+    apply_impl<L>(G, a, ring, pi);
+    return a;
 }
 
 // ----------------------------------------------------------------- new game

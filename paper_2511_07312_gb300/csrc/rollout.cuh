@@ -170,8 +170,7 @@ __device__ __forceinline__ int rollout_one(RolloutSmem* S, const Team<L>& T, con
     if (n == 0) start_end(G, T, Rl, S->pi, code, winner);
     for (int d = 0; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
-        const int a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
-        apply_move(G, T, a, S->ring, S->pi);
+        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), S->ring, S->pi);
         check_end(G, T, Rl, S->pi, code, winner, n);
     }
     return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
