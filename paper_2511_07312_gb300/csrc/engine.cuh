@@ -99,10 +99,11 @@ struct __align__(16) SmemGame {
     uint8_t pad[2];
     uint32_t seg_cnt[kSegMax];// moves per from-square segment in G->mask (written with the mask)
     uint64_t pi_theirs[4];    // chased-side hash of chase positions n_pi-4 .. n_pi-1 (slot i & 3)
+    uint64_t pi_mine[4];      // the chaser's hash of the same positions
     uint32_t stat[8];         // counters of the current launch (kept by the env's step loop)
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 32 + 32 + 4 * kMaskWordsAlloc,
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 64 + 32 + 4 * kMaskWordsAlloc,
               "SmemGame layout");
 static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
@@ -230,7 +231,7 @@ __device__ __forceinline__ void bb_clr(uint64_t* b, int s) { b[s >> 6] &= ~(1ull
 
 // Everything derived from the core and the board: square sets per player,
 // column occupancy, flag ids, Scout lists, the last two moves, the cached
-// chased-side hashes of the newest chase positions (from the store pi).
+// hashes of the newest four chase positions (from the store pi).
 // Needs G->board.  Each side has at most 8 Scouts (Tab. pieces; setups, imported
 // positions and belief samples keep the piece counts).
 template <int L>
@@ -271,7 +272,10 @@ __device__ __noinline__ void derive_state(SmemGame* G, const uint16_t* ring, con
         G->colocc[c] = (uint16_t)col;
     }
     const int npi = G->c.n_pi;
-    for (int i = max(npi - 4, 0) + T.tl; i < npi; i += L) G->pi_theirs[i & 3] = pi[2 * i + 1];
+    for (int i = max(npi - 4, 0) + T.tl; i < npi; i += L) {
+        G->pi_mine[i & 3] = pi[2 * i];
+        G->pi_theirs[i & 3] = pi[2 * i + 1];
+    }
     if (T.leader()) {
         G->h0 = (uint16_t)hist_at(G, ring, 0);
         G->h1 = (uint16_t)hist_at(G, ring, 1);
@@ -368,10 +372,9 @@ __device__ __forceinline__ bool chase_blocks(const SmemGame* G, const PlyCtx& x,
     const uint64_t mine = G->c.hash_side[P] ^ zkey(pid, from) ^ zkey(pid, to);
     const uint64_t theirs = G->c.hash_side[1 - P];
     const int n = min((int)G->c.n_pi, kPiCap);
-    // chased-side hashes of the newest four positions from shared memory; the
-    // store is read for a chaser hash only where the chased side matches
+    // the newest four positions from shared memory, older ones from the store
     for (int i = max(n - 4, 0); i < n; ++i)
-        if (G->pi_theirs[i & 3] == theirs && pi[2 * i] == mine) return true;
+        if (G->pi_theirs[i & 3] == theirs && G->pi_mine[i & 3] == mine) return true;
     for (int i = 0; i < n - 4; ++i)
         if (pi[2 * i + 1] == theirs && pi[2 * i] == mine) return true;
     return false;
@@ -854,6 +857,7 @@ __device__ __forceinline__ void apply_impl(SmemGame* G, int a, uint16_t* ring, u
             if (c.n_pi < kPiCap) {
                 pi[2 * c.n_pi] = h; pi[2 * c.n_pi + 1] = hq;
                 G->pi_theirs[c.n_pi & 3] = hq;
+                G->pi_mine[c.n_pi & 3] = h;
                 c.n_pi += 1;
             }
             c.chase_plies += 1;

@@ -115,6 +115,13 @@ struct __align__(16) RolloutSmem {
     uint8_t types[48];
 };
 
+// A rollout team's record when no history ring is kept.
+struct __align__(16) FlatSmem {
+    SmemGame g;
+    uint64_t pi[kPiWords];
+    uint8_t types[48];
+};
+
 // Warp: import snapshot `in` and write its root state (bad != 0 if invalid).
 __device__ inline void build_root(RolloutSmem* S, const st_position* in, RootState* out)
 {
@@ -135,43 +142,49 @@ __device__ inline void build_root(RolloutSmem* S, const st_position* in, RootSta
 }
 
 // Team: one rollout of `depth` random plies from root R with sample `k`
-// (types given, or drawn from R->plan).  Returns the tally slot: 0 win,
-// 1 loss, 2 draw for the player to move at the root, 3 unfinished.
+// (types given, or drawn from plan, R's plan) in the game record G; types_s: 40
+// bytes of shared scratch for the sample; pi: the rollout's chase store;
+// ring: a history ring to continue (a copy of the root's is made), or
+// nullptr to keep no history (the last two moves come from the root's).
+// Returns the tally slot: 0 win, 1 loss, 2 draw for the player to move at
+// the root, 3 unfinished.
 template <int L>
-__device__ __forceinline__ int rollout_one(RolloutSmem* S, const Team<L>& T, const RootState* R, const uint8_t* types,
-                                           int depth, uint32_t k0, uint32_t k1, uint32_t stream, uint32_t k,
-                                           const Rules& Rl)
+__device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64_t* pi, uint16_t* ring,
+                                           const Team<L>& T, const RootState* R, const BeliefPlan* plan,
+                                           const uint8_t* types, int depth, uint32_t k0, uint32_t k1, uint32_t stream,
+                                           uint32_t k, const Rules& Rl)
 {
     const int lane = T.tl;
-    SmemGame* G = &S->g;
     {
         const uint4* src = reinterpret_cast<const uint4*>(R);
         uint4* dst = reinterpret_cast<uint4*>(G);
         for (int i = lane; i < (288 + 112) / 16; i += L) dst[i] = src[i];
-        const uint4* rs = reinterpret_cast<const uint4*>(R->ring);
-        uint4* rd = reinterpret_cast<uint4*>(S->ring);
-        for (int i = lane; i < kRing * 2 / 16; i += L) rd[i] = rs[i];
+        if (ring) {
+            const uint4* rs = reinterpret_cast<const uint4*>(R->ring);
+            uint4* rd = reinterpret_cast<uint4*>(ring);
+            for (int i = lane; i < kRing * 2 / 16; i += L) rd[i] = rs[i];
+        }
     }
     T.sync();
     const int npi = G->c.n_pi;
-    for (int i = lane; i < 2 * npi; i += L) S->pi[i] = R->pi[i];
+    for (int i = lane; i < 2 * npi; i += L) pi[i] = R->pi[i];
     const int searcher = G->c.ply & 1, opp = 1 - searcher;
     if (types) {
-        for (int i = lane; i < 40; i += L) S->types[i] = types[i];
+        for (int i = lane; i < 40; i += L) types_s[i] = types[i];
     } else if (lane == 0) {
-        draw_sample(&R->plan, k0, k1, stream, k, S->types);
+        draw_sample(plan, k0, k1, stream, k, types_s);
     }
     T.sync();
-    for (int i = lane; i < 40; i += L) G->c.type[opp * 40 + i] = S->types[i];
+    for (int i = lane; i < 40; i += L) G->c.type[opp * 40 + i] = types_s[i];
     T.sync();
-    derive_state(G, S->ring, S->pi, T);   // bitboards and flag ids of the sampled types
-    int n = gen_moves(G, T, searcher, Rl.flags, false, true, S->pi);
+    derive_state(G, ring ? ring : R->ring, pi, T);   // square sets and flag ids of the sampled types
+    int n = gen_moves(G, T, searcher, Rl.flags, false, true, pi);
     int code = 0, winner = -1;
-    if (n == 0) start_end(G, T, Rl, S->pi, code, winner);
+    if (n == 0) start_end(G, T, Rl, pi, code, winner);
     for (int d = 0; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
-        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), S->ring, S->pi);
-        check_end(G, T, Rl, S->pi, code, winner, n);
+        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi);
+        check_end(G, T, Rl, pi, code, winner, n);
     }
     return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
 }

@@ -8,9 +8,10 @@
 // whole samples (Fisher-Yates over at most 40 pieces) from its own Philox
 // stream.
 // st_rollout: k_roots imports every position once (one warp each) into a
-// root record in HBM; k_rollout_flat runs one warp per (position, sample),
-// copying the root into shared memory, so a single position's samples spread
-// over the whole GPU.
+// root record in HBM; k_rollout_flat runs one 8-lane team per (position,
+// sample), copying the root into shared memory, so a single position's
+// samples spread over the whole GPU.  A rollout keeps no history ring (its
+// last two moves start from the root's).
 #include "rollout.cuh"
 #include "host_common.h"
 
@@ -73,12 +74,15 @@ __global__ void k_roots(const st_position* pos, int P, RootState* roots, uint8_t
     if (lane_id() == 0 && status) status[p] = roots[p].bad ? 1 : 0;
 }
 
+// One (position, sample) unit per 8-lane team; consecutive teams of a block
+// share a position, so its root and plan come mostly from L1.  A rollout
+// keeps no history ring (its last two moves start from the root's).
 __global__ void k_rollout_flat(const RootState* roots, int P, int K, int depth, uint32_t k0, uint32_t k1,
                                const uint32_t* stream_ids, const uint8_t* types_in, Rules Rl, int32_t* tallies)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<kFlatLanes> T;
-    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + threadIdx.x / kFlatLanes;
+    FlatSmem* S = reinterpret_cast<FlatSmem*>(smem) + threadIdx.x / kFlatLanes;
     const long long u = (long long)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes;
     if (u >= (long long)P * K) return;
     const int p = (int)(u / K), k = (int)(u - (long long)p * K);
@@ -86,8 +90,9 @@ __global__ void k_rollout_flat(const RootState* roots, int P, int K, int depth, 
     if (R->bad) return;
     const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
     const uint8_t* t = types_in ? types_in + ((size_t)p * K + k) * 40 : nullptr;
-    const int slot = rollout_one(S, T, R, t, depth, k0, k1, stream, (uint32_t)k, Rl);
-    if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + slot], 1);
+    const int out = rollout_one(&S->g, S->types, S->pi, (uint16_t*)nullptr, T, R, &R->plan, t, depth, k0, k1, stream,
+                                (uint32_t)k, Rl);
+    if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + out], 1);
 }
 
 }  // namespace
@@ -130,7 +135,7 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
     if (err == cudaSuccess && K > 0) {
         const long long units = (long long)P * K;
         const long long fb = (units + kFlatTeams - 1) / kFlatTeams;
-        k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(RolloutSmem), s>>>(
+        k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
             roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, types, r, tallies);
         err = cudaGetLastError();
     }

@@ -110,7 +110,8 @@ __global__ void k_serve_rollouts(const BatchEntry* entries, int n, long long uni
     const bool bad = R->bad != 0;
     const int lane = T.tl;
     if (!bad) {
-        const int outcome = rollout_one(S, T, R, nullptr, d->depth, d->k0, d->k1, d->stream, (uint32_t)k, Rl);
+        const int outcome = rollout_one(&S->g, S->types, S->pi, (uint16_t*)nullptr, T, R, &R->plan, nullptr, d->depth,
+                                        d->k0, d->k1, d->stream, (uint32_t)k, Rl);
         SampleRec* rec = samples + d->sample_base + k;
         for (int i = lane; i < 10; i += kServeLanes)
             reinterpret_cast<uint32_t*>(rec->types)[i] = reinterpret_cast<const uint32_t*>(S->types)[i];
