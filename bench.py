@@ -118,6 +118,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def workload_config(games, plies, ring):
+    """The config object both arms print for the env-step workload."""
+    return {"workload": "%s random-policy Stratego games, auto-reset, %s plies per slot per step" % (
+                "{:,}".format(games), "{:,}".format(plies)),
+            "games_per_gpu": games, "plies_per_step": plies, "ring_rows": ring,
+            "l2": "output ring %.2f GB > L2 (inputs larger than L2, no flush)" % (ring * games * MASK_BYTES / 1e9)}
+
+
 def job_rate(units_per_rank, ms_local, world, dist=None, device="cpu"):
     """Whole-job throughput of a weak-scaling run: the units all ranks
     processed divided by the slowest rank's time (max over ranks).  Returns
@@ -205,8 +213,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "65,536 random-policy Stratego games, auto-reset, 2,000 plies per slot",
-                       "games": args.games, "plies_per_step": plies},
+            "config": workload_config(args.games, plies, args.ring),
             "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -337,13 +344,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
                 "data": "synthetic",
-                "config": {"workload": "65,536 random-policy Stratego games, auto-reset, 2,000 plies per slot "
-                                       "per step",
-                           "games_per_gpu": N, "plies_per_step": S, "ring_rows": R,
-                           "l2": "output ring %.2f GB > L2 (inputs larger than L2, no flush)" %
-                                 (R * N * MASK_BYTES / 1e9),
-                           "launch": {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
-                                      "chosen_by": "autotuner" if tuned else "command line"}},
+                "config": dict(workload_config(N, S, R),
+                               launch={"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
+                                       "chosen_by": "autotuner" if tuned else "command line"}),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,
                              "traffic": (None if measured_traffic_per_env_step() is None
