@@ -87,24 +87,36 @@ __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, 
     const int X = G->board[from];
     const bool battle = G->board[to] != kEmpty;
     const bool ts_on = (rule_flags & kTwoSquare) && G->c.ts_pid[P] != kNone && G->c.ts_len[P] == 4;
-    // active adjacency: one lane per own piece
-    for (int j = lane; j < 40; j += 32) {
-        const int pid = P * 40 + j;
-        if (!(G->c.flags[pid] & 1) || G->c.type[pid] >= kFlag) continue;
-        const int s = G->c.sq[pid];
-        const int r = s / 10, c = s - 10 * r;
-        uint64_t bits = 0;
-        for (int dir = 0; dir < 4; ++dir) {
-            const int rr = r + (dir == 0) - (dir == 1), cc = c + (dir == 2) - (dir == 3);
-            if ((unsigned)rr > 9u || (unsigned)cc > 9u) continue;
-            const int n = rr * 10 + cc;
-            const uint8_t Z = G->board[n];
-            if (!enemy_of(Z, P)) continue;
-            if (s * 100 + n == a) continue;
-            if (ts_on && pid == G->c.ts_pid[P] && two_square_blocks(G, P, n)) continue;
-            bits |= fbit(feat_rank_or_hidden(G, Z)) << 22;
+    // active adjacency: own movable pieces next to enemy pieces, from the
+    // square sets (south, north, west, east neighbour is an enemy); lane j
+    // handles from-squares 4j .. 4j+3, each square's pairs in one pass
+    {
+        const Set128 mv{G->bmov[P][0] | G->bsco[P][0], G->bmov[P][1] | G->bsco[P][1]};
+        const Set128 en = ld128(G->bocc[1 - P]);
+        const Set128 nS = and128(mv, up10(en)), nN = and128(mv, dn10(en));
+        const Set128 nW = and128(and128(mv, up1(en)), Set128{~kCol0Lo, ~kCol0Hi});
+        const Set128 nE = and128(and128(mv, dn1(en)), Set128{~kCol9Lo, ~kCol9Hi});
+        const int off = 4 * lane;
+        const uint32_t bs = bits_at(nS, off, 4), bn = bits_at(nN, off, 4);
+        const uint32_t bw = bits_at(nW, off, 4), be = bits_at(nE, off, 4);
+        uint32_t any = bs | bn | bw | be;
+        while (any) {
+            const int c = __ffs(any) - 1;
+            any &= any - 1;
+            const int sq = off + c;
+            const int pid = G->board[sq];
+            uint64_t bits = 0;
+#pragma unroll
+            for (int dir = 0; dir < 4; ++dir) {
+                const uint32_t m = dir == 0 ? bs : dir == 1 ? bn : dir == 2 ? bw : be;
+                if (!((m >> c) & 1u)) continue;
+                const int n = sq + (dir == 0 ? -10 : dir == 1 ? 10 : dir == 2 ? -1 : 1);
+                if (sq * 100 + n == a) continue;
+                if (ts_on && pid == G->c.ts_pid[P] && two_square_blocks(G, P, n)) continue;
+                bits |= fbit(feat_rank_or_hidden(G, G->board[n])) << 22;
+            }
+            F->a[pid] |= bits;
         }
-        F->a[pid] |= bits;
     }
     __syncwarp(0xFFFFFFFFu);
     if (lane == 0 && !battle) {
