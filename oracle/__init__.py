@@ -63,6 +63,8 @@ def _declare(L):
     L.orx_u8_ratio.argtypes = [u32, u32]
     L.orx_u8_ratio.restype = ctypes.c_uint8
     L.orx_ratio_batch.argtypes = [vp, vp, i32, vp, vp]
+    L.orx_search.argtypes = [vp, i32, i32, i32, u64, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
+                             vp, vp, vp, vp, vp, vp, vp]
 
 
 def _c(a, dtype):
@@ -265,3 +267,29 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
     if r != 0:
         raise ValueError("invalid position %d" % (-r - 1))
     return (tallies, outc) if want_outcomes else tallies
+
+
+SEARCH_MAX_MOVES = 256
+SEARCH_ALPHA, SEARCH_BETA = 0.002, 0.02   # App. E, Tab. search-hyper
+
+
+def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALPHA, beta=SEARCH_BETA, k=100,
+           cap=1000, flags=ALL_RULES):
+    """App. E search: per-candidate-move rollouts (S configurations, depth
+    plies with the forced first move) and the tabular MMD update.  Returns a
+    dict of n_moves [P], actions [P, 256], tallies [P, 256, 4], q and pi
+    [P, 256] (float64), chosen [P], status [P]."""
+    pos = _c(np.atleast_2d(pos), np.uint8)
+    P = pos.shape[0]
+    M = SEARCH_MAX_MOVES
+    sid = None if stream_ids is None else _c(stream_ids, np.uint32)
+    pt = None if pi_theta is None else _c(pi_theta, np.float32)
+    out = dict(n_moves=np.zeros(P, np.int32), actions=np.zeros((P, M), np.int16),
+               tallies=np.zeros((P, M, 4), np.int32), q=np.zeros((P, M)), pi=np.zeros((P, M)),
+               chosen=np.zeros(P, np.int16), status=np.zeros(P, np.uint8))
+    r = lib().orx_search(_p(pos), P, S, depth, seed, _p(sid), _p(pt), float(alpha), float(beta), k, cap, flags,
+                         _p(out["n_moves"]), _p(out["actions"]), _p(out["tallies"]), _p(out["q"]), _p(out["pi"]),
+                         _p(out["chosen"]), _p(out["status"]))
+    if r != 0:
+        raise ValueError("position %d has more than %d legal moves" % (-r - 1, M))
+    return out

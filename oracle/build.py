@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.c", "rules.c", "obs.c", "belief.c", "drivers.c"]
+SOURCES = ["philox.c", "rules.c", "obs.c", "belief.c", "drivers.c", "search.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -16,7 +16,8 @@
  *                                        non-initial states
  *   App. C.1-C.2                        information-state channels
  *   App. D.1 (Tab. game-hyper)          k-move rule and game-length cap
- *   App. E "Search"                     belief samples and rollouts
+ *   App. E "Search"                     belief samples, rollouts, the search
+ *                                        update (search.c)
  *   Salmon et al., SC'11                Philox4x32-10
  *
  * Readings where the paper is silent are listed at the top of each source
@@ -35,6 +36,7 @@
 #define OR_HIST        256     /* moves of history kept in a position snapshot */
 #define OR_MAX_PI      160     /* stored chase positions (<= ceil(k/2) for k <= 255) */
 #define OR_POS_BYTES   784     /* size of the position snapshot layout */
+#define OR_SEARCH_MAX_MOVES 256 /* legal moves of one side never exceed 244 */
 
 /* Type codes follow the order of channels 0-11 (App. C.1). */
 enum { T_SPY = 0, T_SCOUT = 1, T_MINER = 2, T_SERGEANT = 3, T_LIEUTENANT = 4,
@@ -122,5 +124,12 @@ void or_side_marginals(const or_game* g, int side, uint32_t* num /*[40][12]*/, u
 /* ---- belief.c ---- */
 void or_belief_sample_one(const or_game* g, uint64_t seed, uint32_t stream, uint32_t sample,
                           uint8_t out_types[40]);
+
+/* App. E search (search.c): per-candidate-move rollouts and the tabular
+ * magnetic-mirror-descent update; outputs [P][OR_SEARCH_MAX_MOVES](x4). */
+int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const uint32_t* stream_ids,
+               const float* pi_theta, double alpha, double beta, int k, int cap, int flags,
+               int32_t* n_moves, int16_t* actions, int32_t* tallies, double* q, double* pi, int16_t* chosen,
+               uint8_t* status);
 
 #endif
