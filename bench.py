@@ -365,7 +365,8 @@ def main():
 
 def secondary(st, torch, dev, args):
     """Observation planes of 16,384 replayed positions, belief-sample
-    rollouts of 4,096 positions, and the serving workload."""
+    rollouts of 4,096 positions, the per-move search of 256 positions, and
+    the serving workload."""
     import numpy as np
     out = {}
     # 64 random-policy games (seed 1) played on the GPU to their end or the 1,000-ply cap
@@ -415,6 +416,23 @@ def secondary(st, torch, dev, args):
     out["belief_rollout"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K, "depth": D,
                              "ply_steps_per_s_upper": P * K * D / (ms / 1000),
                              "tallies_win_loss_draw_unfinished": tl}
+    # per-move search (App. E steps 1-4): 256 positions x every legal move x
+    # 16 configurations x depth 40, then the tabular update and the sampled move
+    Ps, Ss, Ds = 256, 16, 40
+    spos = pos[::P // Ps][:Ps].contiguous()
+    res = st.search(spos, Ss, Ds, seed=11)
+    torch.cuda.synchronize()
+    reps = 5
+    t0.record()
+    for _ in range(reps):
+        st.search(spos, Ss, Ds, seed=11)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    n_roll = int(res["n_moves"].sum().item()) * Ss
+    out["search"] = {"positions_per_s": Ps / (ms / 1000), "rollouts_per_s": n_roll / (ms / 1000), "ms": ms,
+                     "positions": Ps, "S": Ss, "depth": Ds, "rollouts": n_roll,
+                     "mean_legal_moves": n_roll / Ss / Ps}
     out["serving"] = serving(st, torch, dev, pos.cpu().numpy(), args)
     env.close()
     return out

@@ -299,6 +299,49 @@ st_status st_rollout(const st_position* pos, int32_t P, int32_t K, int32_t depth
                      const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
                      int32_t* tallies, uint8_t* item_status, void* stream);
 
+#define ST_SEARCH_MAX_MOVES 256   /* one side never has more than 244 legal moves */
+
+/*
+ * st_search: per-candidate-move search with the tabular magnetic-mirror-
+ * descent update (App. E "Search", steps 1-4; Sec. "Test-Time Search via
+ * Update Equivalence"), with the uniform belief sampler in place of the
+ * belief network and the uniform random policy in place of the move network.
+ * For each position p, the player to move being the searcher:
+ *   1. S configurations of the opponent's hidden pieces; configuration s is
+ *      st_belief_sample's sample s of stream stream_ids[p] (p if NULL);
+ *   2. one rollout per (legal move j in ascending action order,
+ *      configuration s): move j, then up to depth-1 random-policy plies, ply
+ *      d taking word 0 of Philox at counter (stream, j*S + s, d, 5<<24);
+ *   3. q[j] = mean over the S rollouts of +1 win, -1 loss, 0 draw or
+ *      unfinished (for the searcher), 0 when S = 0;
+ *   4. rho[j] = 1 / (pieces with a legal move * legal moves of move j's
+ *      piece) (the magnet policy, Tab. notation); pi[j] proportional to
+ *      exp((q[j] + alpha ln rho[j] + beta ln pi_theta[j]) / (alpha + beta)),
+ *      in double; chosen = the first move whose ascending running sum of the
+ *      unnormalized weights exceeds u * (their sum), u = (w0 >> 5) * 2^-27 +
+ *      (w1 >> 6) * 2^-53 from Philox at counter (stream, 0, 0, 6<<24).
+ * Arguments (device pointers, caller-owned; P <= 65535, S >= 0, depth >= 1,
+ * alpha, beta >= 0 with alpha + beta > 0; App. E uses 0.002 and 0.02):
+ *   pos[P]                     positions;
+ *   pi_theta[P][10000] float   move-network probabilities by action (NULL:
+ *                              uniform over the legal moves); only legal
+ *                              entries are read, a zero excludes the move;
+ *   n_moves[P] int32           the searcher's legal moves (0: none searched);
+ *   actions[P][256] int16      those moves ascending, -1 after the last;
+ *   tallies[P][256][4] int32   wins, losses, draws, unfinished per move;
+ *   q, pi[P][256] double       values and the updated policy (0 after the last);
+ *   chosen[P] int16            the move played, -1 when there is none;
+ *   item_status[P] uint8       0 ok, 1 invalid position, 2 pi_theta zero on
+ *                              every legal move (may be NULL).
+ * Errors: ST_ERR_INVALID for bad sizes or coefficients or a NULL output,
+ * before anything is enqueued.  Stream-ordered; scratch is stream-ordered
+ * device memory.
+ */
+st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth, uint64_t seed,
+                    const uint32_t* stream_ids, const float* pi_theta, double alpha, double beta,
+                    const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies, double* q,
+                    double* pi, int16_t* chosen, uint8_t* item_status, void* stream);
+
 /*
  * Serving: test-time search requests with continuous batching (App. E: one
  * search per move; here the search is st_rollout's belief samples and

@@ -2,7 +2,8 @@
 
 Compiles the plain C sources of this directory with gcc into
 ``liboracle.so`` next to them.  No fast-math, no target-specific flags: the
-same source gives the same results on x86-64 and AArch64.
+same source gives the same results on x86-64 and AArch64 (no FMA
+contraction: every product and sum is rounded on its own).
 """
 import os
 import subprocess
@@ -22,7 +23,7 @@ def build(force: bool = False) -> str:
             return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
-           "-fno-fast-math", "-o", tmp] + srcs
+           "-fno-fast-math", "-ffp-contract=off", "-o", tmp] + srcs
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -102,6 +102,8 @@ def _declare(L):
         "st_obs_encode_static": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
         "st_belief_sample": [vp, i32, i32, u64, vp, vp, vp, vp],
         "st_rollout": [vp, i32, i32, i32, u64, vp, vp, ctypes.POINTER(st_rules), vp, vp, vp],
+        "st_search": [vp, i32, i32, i32, u64, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(st_rules),
+                      vp, vp, vp, vp, vp, vp, vp, vp],
         "st_serve_create": [ctypes.POINTER(st_serve_config), ctypes.POINTER(vp)],
         "st_serve_submit": [vp, ctypes.POINTER(st_request), ctypes.POINTER(ctypes.c_uint64)],
         "st_serve_poll": [vp, ctypes.c_uint64, vp, ctypes.POINTER(st_timing)],
@@ -297,6 +299,38 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
                             _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
                             _ptr(tallies), _ptr(status), _stream(stream)))
     return tallies, status
+
+
+SEARCH_MAX_MOVES = 256
+SEARCH_ALPHA, SEARCH_BETA = 0.002, 0.02   # App. E
+
+
+def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALPHA, beta=SEARCH_BETA, k=100,
+           cap=1000, flags=RULES_ALL, stream=None):
+    """Per-candidate-move search with the tabular MMD update (st_search).
+
+    pos: [P, 784] uint8 CUDA tensor; pi_theta: optional [P, 10000] float32
+    CUDA tensor of move probabilities by action.  Returns a dict of CUDA
+    tensors: n_moves [P] int32, actions [P, 256] int16, tallies [P, 256, 4]
+    int32, q and pi [P, 256] float64, chosen [P] int16, status [P] uint8."""
+    P = pos.shape[0]
+    dev = pos.device
+    out = {
+        "n_moves": torch.empty(P, dtype=torch.int32, device=dev),
+        "actions": torch.empty((P, SEARCH_MAX_MOVES), dtype=torch.int16, device=dev),
+        "tallies": torch.empty((P, SEARCH_MAX_MOVES, 4), dtype=torch.int32, device=dev),
+        "q": torch.empty((P, SEARCH_MAX_MOVES), dtype=torch.float64, device=dev),
+        "pi": torch.empty((P, SEARCH_MAX_MOVES), dtype=torch.float64, device=dev),
+        "chosen": torch.empty(P, dtype=torch.int16, device=dev),
+        "status": torch.empty(P, dtype=torch.uint8, device=dev),
+    }
+    r = make_rules(k, cap, flags)
+    _check(lib().st_search(_ptr(pos, torch.uint8), P, int(S), int(depth), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                           _ptr(stream_ids, torch.int32), _ptr(pi_theta, torch.float32), float(alpha), float(beta),
+                           ctypes.byref(r), _ptr(out["n_moves"]), _ptr(out["actions"]), _ptr(out["tallies"]),
+                           _ptr(out["q"]), _ptr(out["pi"]), _ptr(out["chosen"]), _ptr(out["status"]),
+                           _stream(stream)))
+    return out
 
 
 class Server:

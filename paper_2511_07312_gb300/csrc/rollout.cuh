@@ -122,8 +122,9 @@ struct __align__(16) FlatSmem {
     uint8_t types[48];
 };
 
-// Warp: import snapshot `in` and write its root state (bad != 0 if invalid).
-__device__ inline void build_root(RolloutSmem* S, const st_position* in, RootState* out)
+// Warp: import snapshot `in` and write its root state; returns (to every
+// lane) and records bad != 0 if the snapshot is invalid.
+__device__ inline int build_root(RolloutSmem* S, const st_position* in, RootState* out)
 {
     const int lane = lane_id();
     const int bad = import_position(&S->g, in, S->ring, S->pi);
@@ -131,7 +132,7 @@ __device__ inline void build_root(RolloutSmem* S, const st_position* in, RootSta
         out->bad = bad;
         if (!bad) make_plan(&S->g, &out->plan);
     }
-    if (bad) return;
+    if (bad) return bad;
     {
         const uint4* src = reinterpret_cast<const uint4*>(&S->g);   // core + board
         uint4* dst = reinterpret_cast<uint4*>(out);
@@ -139,20 +140,18 @@ __device__ inline void build_root(RolloutSmem* S, const st_position* in, RootSta
     }
     for (int i = lane; i < kRing; i += 32) out->ring[i] = S->ring[i];
     for (int i = lane; i < 2 * S->g.c.n_pi; i += 32) out->pi[i] = S->pi[i];
+    return 0;
 }
 
-// Team: one rollout of `depth` random plies from root R with sample `k`
-// (types given, or drawn from plan, R's plan) in the game record G; types_s: 40
-// bytes of shared scratch for the sample; pi: the rollout's chase store;
-// ring: a history ring to continue (a copy of the root's is made), or
-// nullptr to keep no history (the last two moves come from the root's).
-// Returns the tally slot: 0 win, 1 loss, 2 draw for the player to move at
-// the root, 3 unfinished.
+// Team: the rollout record of one belief sample.  Copies root R into G
+// (core, board, chase store; the history ring too when `ring` is given),
+// puts sample `k` (types given, or drawn from plan) on the opponent's hidden
+// pieces and rebuilds the square sets.  types_s: 40 bytes of shared scratch.
 template <int L>
-__device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64_t* pi, uint16_t* ring,
-                                           const Team<L>& T, const RootState* R, const BeliefPlan* plan,
-                                           const uint8_t* types, int depth, uint32_t k0, uint32_t k1, uint32_t stream,
-                                           uint32_t k, const Rules& Rl)
+__device__ __forceinline__ void begin_rollout(SmemGame* G, uint8_t* types_s, uint64_t* pi, uint16_t* ring,
+                                              const Team<L>& T, const RootState* R, const BeliefPlan* plan,
+                                              const uint8_t* types, uint32_t k0, uint32_t k1, uint32_t stream,
+                                              uint32_t k)
 {
     const int lane = T.tl;
     {
@@ -168,7 +167,7 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
     T.sync();
     const int npi = G->c.n_pi;
     for (int i = lane; i < 2 * npi; i += L) pi[i] = R->pi[i];
-    const int searcher = G->c.ply & 1, opp = 1 - searcher;
+    const int opp = 1 - (G->c.ply & 1);
     if (types) {
         for (int i = lane; i < 40; i += L) types_s[i] = types[i];
     } else if (lane == 0) {
@@ -178,6 +177,28 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
     for (int i = lane; i < 40; i += L) G->c.type[opp * 40 + i] = types_s[i];
     T.sync();
     derive_state(G, ring ? ring : R->ring, pi, T);   // square sets and flag ids of the sampled types
+}
+
+__device__ __forceinline__ int tally_slot(int code, int winner, int searcher)
+{
+    return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
+}
+
+// Team: one rollout of `depth` random plies from root R with sample `k`
+// (types given, or drawn from plan, R's plan) in the game record G; types_s: 40
+// bytes of shared scratch for the sample; pi: the rollout's chase store;
+// ring: a history ring to continue (a copy of the root's is made), or
+// nullptr to keep no history (the last two moves come from the root's).
+// Returns the tally slot: 0 win, 1 loss, 2 draw for the player to move at
+// the root, 3 unfinished.
+template <int L>
+__device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64_t* pi, uint16_t* ring,
+                                           const Team<L>& T, const RootState* R, const BeliefPlan* plan,
+                                           const uint8_t* types, int depth, uint32_t k0, uint32_t k1, uint32_t stream,
+                                           uint32_t k, const Rules& Rl)
+{
+    begin_rollout(G, types_s, pi, ring, T, R, plan, types, k0, k1, stream, k);
+    const int searcher = G->c.ply & 1;
     int n = gen_moves(G, T, searcher, Rl.flags, false, true, pi);
     int code = 0, winner = -1;
     if (n == 0) start_end(G, T, Rl, pi, code, winner);
@@ -186,7 +207,30 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
         select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi);
         check_end(G, T, Rl, pi, code, winner, n);
     }
-    return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
+    return tally_slot(code, winner, searcher);
+}
+
+// Team: one rollout of the per-move search (App. E "Search", step 2) from
+// root R: belief sample `s` of R's plan, the searcher's move `first` (legal
+// at the root, whatever the sample), then up to depth-1 random plies, ply d
+// taking word 0 of Philox at counter (stream, c1, d, 5<<24) with c1 = j*S+s.
+// No history ring is kept.  Returns the tally slot as rollout_one does.
+template <int L>
+__device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uint64_t* pi, const Team<L>& T,
+                                              const RootState* R, int first, int depth, uint32_t k0, uint32_t k1,
+                                              uint32_t stream, uint32_t c1, uint32_t s, const Rules& Rl)
+{
+    begin_rollout(G, types_s, pi, (uint16_t*)nullptr, T, R, &R->plan, (const uint8_t*)nullptr, k0, k1, stream, s);
+    const int searcher = G->c.ply & 1;
+    int code = 0, winner = -1, n = 0;
+    select_apply(G, T, first, 0u, (uint16_t*)nullptr, pi);
+    check_end(G, T, Rl, pi, code, winner, n);
+    for (int d = 1; !code && d < depth; ++d) {
+        const uint4 w = philox(make_uint4(stream, c1, (uint32_t)d, 5u << 24), k0, k1);
+        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), (uint16_t*)nullptr, pi);
+        check_end(G, T, Rl, pi, code, winner, n);
+    }
+    return tally_slot(code, winner, searcher);
 }
 
 }  // namespace stg

@@ -12,6 +12,14 @@
 // sample), copying the root into shared memory, so a single position's
 // samples spread over the whole GPU.  A rollout keeps no history ring (its
 // last two moves start from the root's).
+// st_search (steps 1-4): k_search_prep imports every position, lists the
+// searcher's legal moves in ascending order and clears the outputs;
+// k_search_offsets turns the move counts into unit offsets; k_search_rollouts
+// runs one 8-lane team per (position, move, sample) unit; k_search_policy
+// forms the values, the magnet policy, the update and the sampled move, one
+// warp per position.
+#include <algorithm>
+#include <math_constants.h>
 #include "rollout.cuh"
 #include "host_common.h"
 
@@ -95,6 +103,200 @@ __global__ void k_rollout_flat(const RootState* roots, int P, int K, int depth, 
     if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + out], 1);
 }
 
+// ----------------------------------------------------------------- st_search
+constexpr int kSearchMoves = ST_SEARCH_MAX_MOVES;
+constexpr int kMaskWordsUsed = (10000 + 31) / 32;                  // 313
+constexpr int kCompactWords = (kMaskWordsUsed + 31) / 32;          // mask words per lane
+
+// Warp per position: root record, the searcher's legal moves ascending, and
+// every output of the position cleared.
+__global__ void k_search_prep(const st_position* pos, int P, Rules Rl, RootState* roots, int32_t* n_moves,
+                              int16_t* actions, int32_t* tallies, double* q, double* pi, int16_t* chosen,
+                              uint8_t* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= P) return;
+    const Team<32> T;
+    const int lane = T.tl;
+    int16_t* act = actions + (size_t)p * kSearchMoves;
+    {
+        int4* tl = reinterpret_cast<int4*>(tallies + (size_t)p * kSearchMoves * 4);
+        for (int i = lane; i < kSearchMoves; i += 32) {
+            tl[i] = make_int4(0, 0, 0, 0);
+            q[(size_t)p * kSearchMoves + i] = 0.0;
+            pi[(size_t)p * kSearchMoves + i] = 0.0;
+        }
+    }
+    int bad_w = build_root(S, pos + p, roots + p);
+    int n = 0;
+    uint32_t words[kCompactWords];
+    int mine = 0;
+    if (!bad_w) {
+        n = gen_moves(&S->g, T, S->g.c.ply & 1, Rl.flags, false, true, S->pi);
+        if (n > kSearchMoves) { bad_w = 14; n = 0; }   // more moves than a position can have
+        for (int i = 0; i < kCompactWords; ++i) {
+            const int w = lane * kCompactWords + i;
+            words[i] = w < kMaskWordsUsed ? S->g.mask[w] : 0u;
+            mine += __popc(words[i]);
+        }
+    }
+    uint32_t before = mine;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = T.shfl_up(before, d);
+        if (lane >= d) before += v;
+    }
+    before -= mine;   // moves listed by lower lanes
+    for (int i = lane; i < kSearchMoves; i += 32)
+        if (i >= n) act[i] = -1;
+    if (!bad_w) {
+        int o = (int)before;
+        for (int i = 0; i < kCompactWords; ++i) {
+            uint32_t m = words[i];
+            const int base = 32 * (lane * kCompactWords + i);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                act[o++] = (int16_t)(base + b);
+            }
+        }
+    }
+    if (lane == 0) {
+        n_moves[p] = bad_w ? 0 : n;
+        chosen[p] = -1;
+        if (status) status[p] = bad_w ? 1 : 0;
+    }
+}
+
+// Single block: offs[p] = S * (moves of positions before p), offs[P] = total.
+constexpr int kOffsetThreads = 1024;
+
+__global__ void __launch_bounds__(kOffsetThreads) k_search_offsets(const int32_t* n_moves, int P, int S,
+                                                                   long long* offs)
+{
+    __shared__ long long part[kOffsetThreads];
+    const int per = (P + kOffsetThreads - 1) / kOffsetThreads;
+    const int a = threadIdx.x * per, b = min(P, a + per);
+    long long sum = 0;
+    for (int i = a; i < b; ++i) sum += (long long)n_moves[i] * S;
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < kOffsetThreads; d <<= 1) {
+        const long long v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = part[threadIdx.x] - sum;
+    for (int i = a; i < b; ++i) {
+        offs[i] = run;
+        run += (long long)n_moves[i] * S;
+    }
+    if (threadIdx.x == kOffsetThreads - 1) offs[P] = part[threadIdx.x];
+}
+
+// One (position, move j, sample s) unit per 8-lane team, unit u of position
+// p being offs[p] + j*S + s; consecutive teams share a position and mostly a
+// move.  Grid-stride over the units.
+__global__ void k_search_rollouts(const RootState* roots, const long long* offs, int P, int S, int depth, uint32_t k0,
+                                  uint32_t k1, const uint32_t* stream_ids, const int16_t* actions, Rules Rl,
+                                  int32_t* tallies)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Team<kFlatLanes> T;
+    FlatSmem* F = reinterpret_cast<FlatSmem*>(smem) + threadIdx.x / kFlatLanes;
+    const long long total = offs[P];
+    const long long stride = (long long)gridDim.x * kFlatTeams;
+    for (long long u = (long long)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes; u < total; u += stride) {
+        int lo = 0, hi = P;   // the last p with offs[p] <= u
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offs[mid] <= u) lo = mid;
+            else hi = mid;
+        }
+        const int p = lo;
+        const int r = (int)(u - offs[p]);
+        const int j = r / S, s = r - j * S;
+        const RootState* R = roots + p;
+        const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
+        const int first = actions[(size_t)p * kSearchMoves + j];
+        const int out = search_rollout(&F->g, F->types, F->pi, T, R, first, depth, k0, k1, stream, (uint32_t)r,
+                                       (uint32_t)s, Rl);
+        if (T.leader()) atomicAdd(&tallies[((size_t)p * kSearchMoves + j) * 4 + out], 1);
+        T.sync();
+    }
+}
+
+constexpr int kPolicyWarps = 4;
+
+// Warp per position: q, rho, the update in double and the sampled move.
+// Products, sums and quotients are rounded one at a time in the order the
+// update is written (no contraction), so only log and exp differ from a
+// correctly rounded evaluation, by at most an ulp or two.
+__global__ void k_search_policy(int P, int S, uint32_t k0, uint32_t k1, const uint32_t* stream_ids,
+                                const float* pi_theta, double alpha, double beta, const int32_t* n_moves,
+                                const int16_t* actions, const int32_t* tallies, double* q, double* pi, int16_t* chosen,
+                                uint8_t* status)
+{
+    __shared__ double wsh[kPolicyWarps][kSearchMoves];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kPolicyWarps + wi;
+    if (p >= P) return;
+    const int n = n_moves[p];
+    if (n == 0) return;
+    const int16_t* act = actions + (size_t)p * kSearchMoves;
+    double* qp = q + (size_t)p * kSearchMoves;
+    double* pp = pi + (size_t)p * kSearchMoves;
+    double* w = wsh[wi];
+    // pieces with a legal move: runs of equal from-squares in the ascending list
+    int starts = 0;
+    for (int j = lane; j < n; j += 32) starts += (j == 0 || act[j] / 100 != act[j - 1] / 100);
+    const int pieces = __reduce_add_sync(0xffffffffu, (unsigned)starts);
+    const double ab = __dadd_rn(alpha, beta);
+    double zmax = -CUDART_INF;
+    for (int j = lane; j < n; j += 32) {
+        const int4 t = reinterpret_cast<const int4*>(tallies + (size_t)p * kSearchMoves * 4)[j];
+        const double qj = S > 0 ? __ddiv_rn((double)(t.x - t.y), (double)S) : 0.0;
+        qp[j] = qj;
+        const int a = act[j], f = a / 100;
+        int lo = j, hi = j;
+        while (lo > 0 && act[lo - 1] / 100 == f) --lo;
+        while (hi + 1 < n && act[hi + 1] / 100 == f) ++hi;
+        const double rho = __ddiv_rn(1.0, __dmul_rn((double)pieces, (double)(hi - lo + 1)));
+        const double pt = pi_theta ? (double)pi_theta[(size_t)p * 10000 + a] : __ddiv_rn(1.0, (double)n);
+        double z = -CUDART_INF;
+        if (pt > 0.0)
+            z = __ddiv_rn(__dadd_rn(__dadd_rn(qj, __dmul_rn(alpha, log(rho))), __dmul_rn(beta, log(pt))), ab);
+        w[j] = z;
+        zmax = fmax(zmax, z);
+    }
+    for (int d = 16; d >= 1; d >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, d));
+    if (zmax == -CUDART_INF) {
+        if (lane == 0 && status) status[p] = 2;
+        return;
+    }
+    for (int j = lane; j < n; j += 32) w[j] = w[j] == -CUDART_INF ? 0.0 : exp(__dadd_rn(w[j], -zmax));
+    __syncwarp();
+    double W = 0.0;
+    if (lane == 0) {
+        for (int j = 0; j < n; ++j) W = __dadd_rn(W, w[j]);
+        const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
+        const uint4 r = philox(make_uint4(stream, 0u, 0u, 6u << 24), k0, k1);
+        const double u = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6)) / 9007199254740992.0;   // exact
+        const double t = __dmul_rn(u, W);
+        double c = 0.0;
+        int pick = n - 1;
+        for (int j = 0; j < n; ++j) {
+            c = __dadd_rn(c, w[j]);
+            if (t < c) { pick = j; break; }
+        }
+        chosen[p] = act[pick];
+    }
+    W = __shfl_sync(0xffffffffu, W, 0);
+    for (int j = lane; j < n; j += 32) pp[j] = __ddiv_rn(w[j], W);
+}
+
 }  // namespace
 
 extern "C" st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_t seed,
@@ -142,6 +344,62 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
     cudaFreeAsync(roots, s);
     if (err != cudaSuccess) {
         stg::set_error("st_rollout: launch failed: %s", cudaGetErrorString(err));
+        return ST_ERR_CUDA;
+    }
+    return ST_OK;
+}
+
+extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth, uint64_t seed,
+                               const uint32_t* stream_ids, const float* pi_theta, double alpha, double beta,
+                               const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies,
+                               double* q, double* pi, int16_t* chosen, uint8_t* item_status, void* stream)
+{
+    ST_CHECK_ARG(rules_ok(rules), "st_search: invalid rules");
+    ST_CHECK_ARG(P >= 0 && P <= 65535, "st_search: P must be in [0, 65535]");
+    ST_CHECK_ARG(S >= 0 && S <= (1 << 24), "st_search: S must be in [0, 2^24]");
+    ST_CHECK_ARG(depth >= 1, "st_search: depth must be >= 1");
+    ST_CHECK_ARG(alpha >= 0.0 && beta >= 0.0 && alpha + beta > 0.0 && alpha + beta < 1e300,
+                 "st_search: alpha, beta must be finite, >= 0, with a positive sum");
+    if (P == 0) return ST_OK;
+    ST_CHECK_ARG(pos && n_moves && actions && tallies && q && pi && chosen, "st_search: null argument");
+    ST_CHECK_ARG(aligned16(tallies), "st_search: tallies must be 16-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Rules r;
+    r.k = rules->battleless_limit;
+    r.cap = rules->max_plies;
+    r.flags = rules->flags;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    RootState* roots = nullptr;
+    long long* offs = nullptr;
+    ST_CUDA(cudaMallocAsync(&roots, (size_t)P * sizeof(RootState), s));
+    cudaError_t err = cudaMallocAsync(&offs, (size_t)(P + 1) * sizeof(long long), s);
+    if (err == cudaSuccess) {
+        const int rb = (P + kRootWarps - 1) / kRootWarps;
+        k_search_prep<<<rb, 32 * kRootWarps, kRootWarps * sizeof(RolloutSmem), s>>>(
+            pos, P, r, roots, n_moves, actions, tallies, q, pi, chosen, item_status);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess && S > 0) {
+        k_search_offsets<<<1, kOffsetThreads, 0, s>>>(n_moves, P, S, offs);
+        err = cudaGetLastError();
+        if (err == cudaSuccess) {
+            // at most 244 moves per position; grid-stride beyond 2^24 blocks
+            const long long units = (long long)P * 244 * S;
+            const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams, 1LL << 24);
+            k_search_rollouts<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
+                roots, offs, P, S, depth, k0, k1, stream_ids, actions, r, tallies);
+            err = cudaGetLastError();
+        }
+    }
+    if (err == cudaSuccess) {
+        k_search_policy<<<(P + kPolicyWarps - 1) / kPolicyWarps, 32 * kPolicyWarps, 0, s>>>(
+            P, S, k0, k1, stream_ids, pi_theta, alpha, beta, n_moves, actions, tallies, q, pi, chosen, item_status);
+        err = cudaGetLastError();
+    }
+    if (offs) cudaFreeAsync(offs, s);
+    cudaFreeAsync(roots, s);
+    if (err != cudaSuccess) {
+        stg::set_error("st_search: launch failed: %s", cudaGetErrorString(err));
         return ST_ERR_CUDA;
     }
     return ST_OK;
