@@ -20,6 +20,7 @@ NCHAN = 487
 RULE_TWO_SQUARE = 1
 RULE_CHASE = 2
 ALL_RULES = RULE_TWO_SQUARE | RULE_CHASE
+ROLLOUT_MAGNET = 0x100   # rollouts and search: the magnet policy instead of uniform
 
 _lib = None
 
@@ -47,6 +48,7 @@ def _declare(L):
     L.orx_rollout.argtypes = [vp, i32, i32, i32, u64, vp, vp, i32, i32, i32, vp, vp]
     L.orx_legal_moves.argtypes = [vp, i32, i32, i32, i32, vp]
     L.orx_brute_moves.argtypes = [vp, vp]
+    L.orx_policy_pick.argtypes = [vp, i32, i32, i32, u32, u32]
     L.orx_apply.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp]
     L.orx_start_check.argtypes = [vp, i32, i32, i32, vp]
     L.orx_two_square_applies.argtypes = [vp, i32, i32, i32]
@@ -130,6 +132,16 @@ def legal_moves(pos, k=100, cap=1000, flags=ALL_RULES, physical=False):
     if n < 0:
         raise ValueError("invalid position")
     return buf[:n].copy()
+
+
+def policy_pick(pos, w0, w1, magnet=True, k=100, cap=1000, flags=ALL_RULES):
+    """The rollout policy's move in `pos` for Philox words (w0, w1)."""
+    pos = _c(pos, np.uint8)
+    f = (flags | ROLLOUT_MAGNET) if magnet else (flags & ~ROLLOUT_MAGNET)
+    a = lib().orx_policy_pick(_p(pos), k, cap, f, int(w0) & 0xFFFFFFFF, int(w1) & 0xFFFFFFFF)
+    if a == -2:
+        raise ValueError("invalid position")
+    return a
 
 
 def brute_moves(pos):

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.c", "rules.c", "obs.c", "belief.c", "drivers.c", "search.c"]
+SOURCES = ["philox.c", "rules.c", "obs.c", "belief.c", "drivers.c", "search.c", "policy.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

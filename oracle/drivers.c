@@ -44,7 +44,8 @@ static or_rules make_rules(int k, int cap, int flags)
     return r;
 }
 
-/* Select the idx-th legal move (ascending action order) for the random policy. */
+/* The random policy's move (the rules' OR_ROLLOUT_MAGNET bit selects the
+ * magnet policy) from the legal moves in ascending action order. */
 static int pick_random(const or_game* g, const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t c2,
                        uint32_t tag, int* n_out)
 {
@@ -56,7 +57,7 @@ static int pick_random(const or_game* g, const uint32_t key[2], uint32_t c0, uin
     uint32_t ctr[4] = { c0, c1, c2, tag << 24 };
     uint32_t w[4];
     or_philox4x32_10(ctr, key, w);
-    return mv[or_uniform(w[0], (uint32_t)n)];
+    return or_policy_pick(mv, n, w, g->rules.flags & OR_ROLLOUT_MAGNET);
 }
 
 /*
@@ -291,6 +292,22 @@ int orx_legal_moves(const uint8_t* pos, int k, int cap, int flags, int physical,
     qsort(moves, (size_t)n, sizeof(int), sort_int);
     free(g);
     return n;
+}
+
+/* The rollout policy's move in a position for the words (w0, w1, 0, 0);
+ * -1 without a legal move, -2 for an invalid snapshot. */
+int orx_policy_pick(const uint8_t* pos, int k, int cap, int flags, uint32_t w0, uint32_t w1)
+{
+    or_rules rules = make_rules(k, cap, flags);
+    or_game* g = (or_game*)malloc(sizeof(or_game));
+    int mv[400];
+    if (or_import(g, pos, &rules, 0)) { free(g); return -2; }
+    const int n = or_legal_moves(g, g->ply & 1, mv);
+    qsort(mv, (size_t)n, sizeof(int), sort_int);
+    const uint32_t w[4] = { w0, w1, 0u, 0u };
+    const int a = or_policy_pick(mv, n, w, flags & OR_ROLLOUT_MAGNET);
+    free(g);
+    return a;
 }
 
 int orx_brute_moves(const uint8_t* pos, int* moves)

@@ -50,6 +50,9 @@ enum { END_NONE = 0, END_FLAG = 1, END_NO_MOVES = 2, END_NEITHER_CAN_MOVE = 3,
 /* Rule toggles. */
 #define OR_RULE_TWO_SQUARE 1
 #define OR_RULE_CHASE      2
+/* Rollout policy: the magnet policy instead of uniform over the legal moves
+ * (rollouts and search only; the game rules ignore it). */
+#define OR_ROLLOUT_MAGNET  0x100
 
 typedef struct {
     int battleless_limit;   /* k of the k-move rule (App. D.1: 100 in training) */
@@ -120,6 +123,11 @@ void or_encode_planes(const or_game* g, int player, uint8_t* planes_u8, uint16_t
 uint16_t or_bf16_ratio(uint32_t num, uint32_t den);
 uint8_t  or_u8_ratio(uint32_t num, uint32_t den);
 void or_side_marginals(const or_game* g, int side, uint32_t* num /*[40][12]*/, uint32_t* den /*[40][12]*/);
+
+/* ---- policy.c ---- */
+/* The rollout policy's move from the legal moves in ascending order and the
+ * ply's four Philox words (magnet != 0: the magnet policy). */
+int or_policy_pick(const int* moves, int n, const uint32_t w[4], int magnet);
 
 /* ---- belief.c ---- */
 void or_belief_sample_one(const or_game* g, uint64_t seed, uint32_t stream, uint32_t sample,

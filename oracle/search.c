@@ -12,8 +12,9 @@
  *      position's stream (R11).
  *  R16 Step 2: one rollout per (legal move j of the searcher in ascending
  *      action order, configuration s).  Its first ply plays move j; plies
- *      d = 1 .. depth-1 take the random policy with word 0 of Philox at
- *      counter (stream, j*S + s, d, 5<<24).  depth counts the forced move.
+ *      d = 1 .. depth-1 take the rollout policy (R19: uniform, or the magnet
+ *      policy under OR_ROLLOUT_MAGNET) with Philox at counter
+ *      (stream, j*S + s, d, 5<<24).  depth counts the forced move.
  *  R17 Step 3: a rollout's value is +1, -1, 0 for a win, loss or draw of the
  *      searcher and 0 when it is unfinished after depth plies (there is no
  *      value network); q(j) is the mean over the S rollouts of move j (0
@@ -43,7 +44,7 @@ static int cmp_int(const void* a, const void* b)
     return (x > y) - (x < y);
 }
 
-/* ply d >= 1 of the rollout with counter word c1: the idx-th legal move */
+/* ply d >= 1 of the rollout with counter word c1: the rollout policy's move (R19) */
 static int random_move(const or_game* g, const uint32_t key[2], uint32_t stream, uint32_t c1, uint32_t d)
 {
     int mv[400];
@@ -53,7 +54,7 @@ static int random_move(const or_game* g, const uint32_t key[2], uint32_t stream,
     uint32_t ctr[4] = { stream, c1, d, 5u << 24 };
     uint32_t w[4];
     or_philox4x32_10(ctr, key, w);
-    return mv[or_uniform(w[0], (uint32_t)n)];
+    return or_policy_pick(mv, n, w, g->rules.flags & OR_ROLLOUT_MAGNET);
 }
 
 int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const uint32_t* stream_ids,
