@@ -72,6 +72,12 @@ typedef enum st_status {
 #define ST_RULE_CHASE      2u    /* continuous-chasing rule, Tab. chase, App. B.3 */
 #define ST_AUTORESET       4u    /* env only: ended games restart at once (App. B.1) */
 #define ST_RULES_ALL       (ST_RULE_TWO_SQUARE | ST_RULE_CHASE)
+/* Rollout policy (st_rollout, st_search, the server; refused by the env and
+ * the observation calls): the magnet policy rho of Tab. notation -- a piece
+ * with a legal move uniformly (ascending squares, word 0 of the ply's Philox
+ * counter), then one of its legal moves uniformly (ascending actions, word
+ * 1) -- instead of uniform over the legal moves (word 0). */
+#define ST_ROLLOUT_MAGNET  0x100u
 
 #define ST_MASK_BYTES   1264
 #define ST_NCHAN        487      /* observation channels, App. C */
@@ -289,9 +295,11 @@ st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_
 /*
  * st_rollout: for each position and each of K samples, replace the hidden
  * opponent types by the sample (types, or the st_belief_sample draw when
- * types is NULL) and play up to `depth` random-policy plies, ply d taking
- * word 0 of Philox at counter (stream_ids[p] or p, k, d, 4<<24) (App. E step
- * 2 with a random policy in place of the move network).  tallies[P][4]
+ * types is NULL) and play up to `depth` plies of the rollout policy (uniform
+ * over the legal moves, or the magnet policy when rules->flags has
+ * ST_ROLLOUT_MAGNET), ply d drawing from Philox at counter (stream_ids[p] or
+ * p, k, d, 4<<24) (App. E step 2 with a random policy in place of the move
+ * network).  tallies[P][4]
  * int32: wins, losses, draws of the player to move at the root, and
  * rollouts unfinished after `depth` plies.
  */
@@ -305,13 +313,14 @@ st_status st_rollout(const st_position* pos, int32_t P, int32_t K, int32_t depth
  * st_search: per-candidate-move search with the tabular magnetic-mirror-
  * descent update (App. E "Search", steps 1-4; Sec. "Test-Time Search via
  * Update Equivalence"), with the uniform belief sampler in place of the
- * belief network and the uniform random policy in place of the move network.
+ * belief network and the uniform (or, with ST_ROLLOUT_MAGNET, the magnet)
+ * rollout policy in place of the move network.
  * For each position p, the player to move being the searcher:
  *   1. S configurations of the opponent's hidden pieces; configuration s is
  *      st_belief_sample's sample s of stream stream_ids[p] (p if NULL);
  *   2. one rollout per (legal move j in ascending action order,
- *      configuration s): move j, then up to depth-1 random-policy plies, ply
- *      d taking word 0 of Philox at counter (stream, j*S + s, d, 5<<24);
+ *      configuration s): move j, then up to depth-1 rollout-policy plies,
+ *      ply d drawing from Philox at counter (stream, j*S + s, d, 5<<24);
  *   3. q[j] = mean over the S rollouts of +1 win, -1 loss, 0 draw or
  *      unfinished (for the searcher), 0 when S = 0;
  *   4. rho[j] = 1 / (pieces with a legal move * legal moves of move j's

@@ -18,6 +18,7 @@ POS_BYTES = 784
 RULE_TWO_SQUARE = 1
 RULE_CHASE = 2
 RULES_ALL = RULE_TWO_SQUARE | RULE_CHASE
+ROLLOUT_MAGNET = 0x100   # rollouts, search, server: the magnet policy as the rollout policy
 AUTORESET = 4
 
 ST_OK = 0

@@ -53,7 +53,7 @@ constexpr uint32_t kLakeCol = 0x30u;   // rows 4,5 of columns 2,3,6,7
 enum : int { kSpy = 0, kScout = 1, kMiner = 2, kMarshal = 9, kFlag = 10, kBomb = 11 };
 enum : int { kClBattle = 0, kClQuiet = 1, kClThreat = 2, kClEvade = 3 };
 
-constexpr uint32_t kTwoSquare = 1u, kChase = 2u, kAutoreset = 4u;
+constexpr uint32_t kTwoSquare = 1u, kChase = 2u, kAutoreset = 4u, kMagnet = 0x100u;
 
 struct Rules {
     int k;          // battleless limit
@@ -724,6 +724,65 @@ __device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
     return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
 
+// The four mask words holding from-square s's row (actions 100s .. 100s+99),
+// bits of the neighbouring rows cleared; returns the row's first word index.
+__device__ __forceinline__ int row_words(const SmemGame* G, int s, uint32_t r[4])
+{
+    const int b = 100 * s, w = b >> 5, off = b & 31;   // off = 4s mod 32: 0 .. 28
+    const int hb = off + 4;                             // row bits in the fourth word
+    r[0] = G->mask[w] & (~0u << off);
+    r[1] = G->mask[w + 1];
+    r[2] = G->mask[w + 2];
+    r[3] = G->mask[w + 3] & (hb >= 32 ? ~0u : ((1u << hb) - 1u));
+    return w;
+}
+
+// The magnet policy's move (Tab. notation rho) from the mask of the player
+// to move: piece number uniform_below(w0, pieces with a legal move) in
+// ascending square order, then move number uniform_below(w1, its moves) in
+// ascending action order.  Lane j looks at the own movable pieces of its
+// segment of squares only.  Team-uniform result.
+template <int L>
+__device__ __forceinline__ int magnet_impl(const SmemGame* G, uint32_t w0, uint32_t w1)
+{
+    const Team<L> T;
+    constexpr int SW = Seg<L>::W;
+    const int t = T.tl, P = G->c.ply & 1;
+    const int lo = SW * t;
+    const Set128 own = or128(ld128(G->bmov[P]), ld128(G->bsco[P]));
+    uint32_t cand = lo < kSquares ? bits_at(own, lo, min(SW, kSquares - lo)) : 0u;
+    uint32_t live = 0;   // bit i: square lo + i has a legal move
+    while (cand) {
+        const int i = __ffs(cand) - 1;
+        cand &= cand - 1;
+        uint32_t r[4];
+        row_words(G, lo + i, r);
+        if (r[0] | r[1] | r[2] | r[3]) live |= 1u << i;
+    }
+    const int np = __popc(live);
+    int incl = np;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const int v = __shfl_up_sync(T.mask, incl, o, L);
+        if (t >= o) incl += v;
+    }
+    const int pieces = T.shfl(incl, L - 1);
+    const int want = (int)uniform_below(w0, (uint32_t)pieces);
+    const uint32_t own_lane = T.ballot(want >= incl - np && want < incl);
+    int a = -1;
+    if (own_lane & (1u << t)) {
+        const int s = lo + nth_set_bit(live, want - (incl - np));
+        uint32_t r[4];
+        const int w = row_words(G, s, r);
+        const int m = __popc(r[0]) + __popc(r[1]) + __popc(r[2]) + __popc(r[3]);
+        int k = (int)uniform_below(w1, (uint32_t)m);
+        int i = 0;
+        while (i < 3 && k >= __popc(r[i])) { k -= __popc(r[i]); ++i; }
+        a = 32 * (w + i) + nth_set_bit(r[i], k);
+    }
+    return T.shfl(a, own_lane ? __ffs(own_lane) - 1 : 0);
+}
+
 template <int L>
 __device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
 {
@@ -885,6 +944,15 @@ template <int L>
 __device__ __noinline__ int select_apply(SmemGame* G, Team<L>, int a, uint32_t idx, uint16_t* ring, uint64_t* pi)
 {
     if (a < 0) a = select_impl<L>(G, idx);
+    apply_impl<L>(G, a, ring, pi);
+    return a;
+}
+
+// The magnet policy's move for Philox words (w0, w1), then played.
+template <int L>
+__device__ __noinline__ int magnet_apply(SmemGame* G, Team<L>, uint32_t w0, uint32_t w1, uint16_t* ring, uint64_t* pi)
+{
+    const int a = magnet_impl<L>(G, w0, w1);
     apply_impl<L>(G, a, ring, pi);
     return a;
 }

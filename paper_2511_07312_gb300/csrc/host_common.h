@@ -28,10 +28,12 @@ void set_error(const char* fmt, ...);
         }                                                                          \
     } while (0)
 
-inline bool rules_ok(const st_rules* r)
+// rollout: the call runs rollouts, so the rollout-policy bit is allowed.
+inline bool rules_ok(const st_rules* r, bool rollout = false)
 {
+    const uint32_t allowed = ST_RULE_TWO_SQUARE | ST_RULE_CHASE | (rollout ? ST_ROLLOUT_MAGNET : 0u);
     return r && r->battleless_limit >= 1 && r->battleless_limit <= ST_MAX_BATTLELESS && r->max_plies >= 1 &&
-           (r->flags & ~(ST_RULE_TWO_SQUARE | ST_RULE_CHASE)) == 0;
+           (r->flags & ~allowed) == 0;
 }
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -184,7 +184,8 @@ __device__ __forceinline__ int tally_slot(int code, int winner, int searcher)
     return !code ? 3 : (winner < 0 ? 2 : (winner == searcher ? 0 : 1));
 }
 
-// Team: one rollout of `depth` random plies from root R with sample `k`
+// Team: one rollout of `depth` plies of the rollout policy (uniform, or the
+// magnet policy under kMagnet) from root R with sample `k`
 // (types given, or drawn from plan, R's plan) in the game record G; types_s: 40
 // bytes of shared scratch for the sample; pi: the rollout's chase store;
 // ring: a history ring to continue (a copy of the root's is made), or
@@ -204,7 +205,8 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
     if (n == 0) start_end(G, T, Rl, pi, code, winner);
     for (int d = 0; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
-        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi);
+        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, ring, pi);
+        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi);
         check_end(G, T, Rl, pi, code, winner, n);
     }
     return tally_slot(code, winner, searcher);
@@ -212,8 +214,9 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
 
 // Team: one rollout of the per-move search (App. E "Search", step 2) from
 // root R: belief sample `s` of R's plan, the searcher's move `first` (legal
-// at the root, whatever the sample), then up to depth-1 random plies, ply d
-// taking word 0 of Philox at counter (stream, c1, d, 5<<24) with c1 = j*S+s.
+// at the root, whatever the sample), then up to depth-1 plies of the rollout
+// policy, ply d drawing from Philox at counter (stream, c1, d, 5<<24) with
+// c1 = j*S+s.
 // No history ring is kept.  Returns the tally slot as rollout_one does.
 template <int L>
 __device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uint64_t* pi, const Team<L>& T,
@@ -227,7 +230,8 @@ __device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uin
     check_end(G, T, Rl, pi, code, winner, n);
     for (int d = 1; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, c1, (uint32_t)d, 5u << 24), k0, k1);
-        select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), (uint16_t*)nullptr, pi);
+        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, (uint16_t*)nullptr, pi);
+        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), (uint16_t*)nullptr, pi);
         check_end(G, T, Rl, pi, code, winner, n);
     }
     return tally_slot(code, winner, searcher);

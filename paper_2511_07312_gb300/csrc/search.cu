@@ -316,7 +316,7 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
                                 const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
                                 int32_t* tallies, uint8_t* item_status, void* stream)
 {
-    ST_CHECK_ARG(rules_ok(rules), "st_rollout: invalid rules");
+    ST_CHECK_ARG(rules_ok(rules, true), "st_rollout: invalid rules");
     ST_CHECK_ARG(P >= 0 && K >= 0 && depth >= 0, "st_rollout: negative size");
     if (P == 0) return ST_OK;
     ST_CHECK_ARG(pos && tallies, "st_rollout: null argument");
@@ -354,7 +354,7 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
                                const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies,
                                double* q, double* pi, int16_t* chosen, uint8_t* item_status, void* stream)
 {
-    ST_CHECK_ARG(rules_ok(rules), "st_search: invalid rules");
+    ST_CHECK_ARG(rules_ok(rules, true), "st_search: invalid rules");
     ST_CHECK_ARG(P >= 0 && P <= 65535, "st_search: P must be in [0, 65535]");
     ST_CHECK_ARG(S >= 0 && S <= (1 << 24), "st_search: S must be in [0, 2^24]");
     ST_CHECK_ARG(depth >= 1, "st_search: depth must be >= 1");

@@ -373,7 +373,7 @@ extern "C" st_status st_serve_create(const st_serve_config* cfg, st_server** out
     ST_CHECK_ARG(cfg->max_requests >= 1 && cfg->max_requests <= 65536, "st_serve_create: max_requests 1..65536");
     ST_CHECK_ARG(cfg->sample_slots >= 1 && cfg->sample_slots <= (1 << 26), "st_serve_create: sample_slots 1..2^26");
     ST_CHECK_ARG(cfg->max_batches >= 1 && cfg->max_batches <= 64, "st_serve_create: max_batches 1..64");
-    ST_CHECK_ARG(rules_ok(&cfg->rules), "st_serve_create: invalid rules");
+    ST_CHECK_ARG(rules_ok(&cfg->rules, true), "st_serve_create: invalid rules");
     int ndev = 0;
     ST_CUDA(cudaGetDeviceCount(&ndev));
     ST_CHECK_ARG(cfg->device >= 0 && cfg->device < ndev, "st_serve_create: device %d not present", cfg->device);

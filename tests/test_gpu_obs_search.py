@@ -100,19 +100,21 @@ def test_belief_samples_bit_exact():
     np.testing.assert_array_equal(types2.cpu().numpy(), oracle.belief_sample(pos, 5, 7, stream_ids=sid.cpu().numpy()))
 
 
-@pytest.mark.parametrize("depth", [0, 1, 32, 200])
-def test_rollout_tallies_bit_exact(depth):
+@pytest.mark.parametrize("depth,magnet", [(0, False), (1, False), (32, False), (200, False), (1, True), (32, True),
+                                          (200, True)])
+def test_rollout_tallies_bit_exact(depth, magnet):
     g, S, A = _games(37, 8)
     games, plies = _items(g, 3, seed=3)
     pos = oracle.replay_positions(g["setups"], g["actions"], games, plies)
     tp = torch.from_numpy(pos).cuda()
-    tallies, status = st.rollout(tp, 19, depth, seed=99)
+    flags = st.RULES_ALL | (st.ROLLOUT_MAGNET if magnet else 0)
+    tallies, status = st.rollout(tp, 19, depth, seed=99, flags=flags)
     torch.cuda.synchronize()
-    ref = oracle.rollout(pos, 19, depth, 99)
+    ref = oracle.rollout(pos, 19, depth, 99, flags=flags)
     np.testing.assert_array_equal(tallies.cpu().numpy(), ref)
     assert (tallies.cpu().numpy().sum(1) == 19).all()
     # with supplied samples
     types = oracle.belief_sample(pos, 19, 5)
-    t2, _ = st.rollout(tp, 19, depth, seed=99, types=torch.from_numpy(types).cuda())
+    t2, _ = st.rollout(tp, 19, depth, seed=99, types=torch.from_numpy(types).cuda(), flags=flags)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(t2.cpu().numpy(), oracle.rollout(pos, 19, depth, 99, types=types))
+    np.testing.assert_array_equal(t2.cpu().numpy(), oracle.rollout(pos, 19, depth, 99, types=types, flags=flags))

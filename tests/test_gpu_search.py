@@ -59,13 +59,15 @@ def _compare(got, ref, seed, stream_ids=None):
             p, g["chosen"][p], ref["chosen"][p], u, edge)
 
 
-@pytest.mark.parametrize("S,depth", [(5, 1), (7, 9), (3, 80)])
-def test_search_matches_oracle(S, depth):
+@pytest.mark.parametrize("S,depth,magnet", [(5, 1, False), (7, 9, False), (3, 80, False), (4, 9, True),
+                                            (3, 80, True)])
+def test_search_matches_oracle(S, depth, magnet):
     pos = _positions(41, 6, 2)   # 12 positions: not a multiple of the warps per block
     seed = 1000 + depth
-    got = st.search(torch.from_numpy(pos).cuda(), S, depth, seed)
+    flags = st.RULES_ALL | (st.ROLLOUT_MAGNET if magnet else 0)
+    got = st.search(torch.from_numpy(pos).cuda(), S, depth, seed, flags=flags)
     torch.cuda.synchronize()
-    ref = oracle.search(pos, S, depth, seed)
+    ref = oracle.search(pos, S, depth, seed, flags=flags)
     assert (ref["status"] == 0).all() and (ref["n_moves"] > 0).all()
     _compare(got, ref, seed)
     t = got["tallies"].cpu().numpy()

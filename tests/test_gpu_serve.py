@@ -135,3 +135,16 @@ def test_edge_requests():
         assert tallies.sum() == 64
     finally:
         srv.close()
+
+
+def test_server_with_the_magnet_rollout_policy():
+    pos = _positions(57, 4)
+    flags = st.RULES_ALL | st.ROLLOUT_MAGNET
+    srv = st.Server(max_requests=4, sample_slots=2048, max_batches=2, flags=flags)
+    try:
+        for p, K, D, seed, sid in _requests(pos, 4):
+            tallies, _ = srv.wait(srv.submit(p, K, D, seed, sid), 60000)
+            np.testing.assert_array_equal(tallies, oracle.rollout(p[None], K, D, seed, stream_ids=[sid],
+                                                                  flags=flags)[0])
+    finally:
+        srv.close()
