@@ -392,3 +392,26 @@ def test_import_rejects_corrupt_rule_state():
     # a chase whose history move starts off the board
     chase = make_position(pcs, ply=4, battleless=4, chaser=0, chase_plies=1, hist=[65000])
     assert oracle.import_check(chase) == -12
+
+
+def test_online_200_move_rule_and_the_rule_fractions():
+    # App. A "Additional rule for online play" and App. D.1: the online game
+    # draws after 200 battleless moves, and channels 41-42 (App. C.1) give
+    # ply / max plies and battleless / k.  Values below are worked by hand:
+    # 151/200 -> uint8 floor(255*151/200 + 1/2) = 193, bf16 193/256 = 0x3F41;
+    # 161/4000 -> uint8 floor(10.26 + 1/2) = 10, bf16 165/4096 = 0x3D25.
+    pcs = [(0, MARSHAL, sq("e4"), 0), (0, FLAG, sq("a1"), 0), (1, SCOUT, sq("j9"), 0), (1, FLAG, sq("j10"), 0)]
+    mv = [action("e4", "e5")]
+    out, ending, _, u8, bf = oracle.apply(make_position(pcs, ply=160, battleless=150), mv, k=200, cap=4000,
+                                          planes=True)
+    assert ending == 0 and field(out, "battleless") == 151
+    assert (u8[42] == 193).all() and (bf[42] == 0x3F41).all()
+    assert (u8[41] == 10).all() and (bf[41] == 0x3D25).all()
+    # the same move ends the game under the 100-move rule, and under the
+    # 200-move rule once 200 battleless plies are reached
+    _, ending, _ = oracle.apply(make_position(pcs, ply=160, battleless=150), mv, k=100)
+    assert ending == 4
+    _, ending, _ = oracle.apply(make_position(pcs, ply=300, battleless=199), mv, k=200, cap=4000)
+    assert ending == 4
+    _, ending, _ = oracle.apply(make_position(pcs, ply=300, battleless=198), mv, k=200, cap=4000)
+    assert ending == 0
