@@ -40,7 +40,8 @@ def _p(a):
 
 def _declare(L):
     vp, i32, u64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32
-    L.orx_env_run.argtypes = [u64, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.orx_env_run.argtypes = [u64, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, i32,
+                              i32, vp, vp]
     L.orx_play_games.argtypes = [u64, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     L.orx_replay_positions.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, vp]
     L.orx_obs_encode.argtypes = [vp, vp, i32, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp]
@@ -196,8 +197,13 @@ def perft(pos, depth, brute=False, k=100, cap=1000, flags=ALL_RULES):
 # --------------------------------------------------------------- drivers
 
 def env_run(seed, n_slots, n_steps, slot0=0, k=100, cap=1000, flags=ALL_RULES, autoreset=True,
-            actions=None, want_mask=True, want_final=False):
-    """Oracle environment loop; outputs are [n_steps, n_slots] (mask [..., 1264])."""
+            actions=None, want_mask=True, want_final=False, episode0=0, pool=None, mirror=False, pins=None):
+    """Oracle environment loop; outputs are [n_steps, n_slots] (mask [..., 1264]).
+
+    pool: [2, M, 40] uint8 setups per side (types on the side's setup
+    squares in ascending order); mirror: left-right orientation
+    randomisation of pool setups; pins: {slot index i: 784-byte snapshot}
+    for slots that start and restart from a fixed position."""
     shape = (n_steps, n_slots)
     act = np.zeros(shape, np.int16)
     rew = np.zeros(shape, np.int8)
@@ -207,9 +213,20 @@ def env_run(seed, n_slots, n_steps, slot0=0, k=100, cap=1000, flags=ALL_RULES, a
     stats = np.zeros((n_slots, 8), np.uint32)
     final = np.zeros((n_slots, POS_BYTES), np.uint8) if want_final else None
     ain = None if actions is None else _c(actions, np.int16)
+    pl = None if pool is None else _c(pool, np.uint8)
+    pin_pos = pinned = None
+    if pins:
+        pin_pos = np.zeros((n_slots, POS_BYTES), np.uint8)
+        pinned = np.zeros(n_slots, np.uint8)
+        for i, p in pins.items():
+            pin_pos[i] = p
+            pinned[i] = 1
     r = lib().orx_env_run(seed, slot0, n_slots, n_steps, k, cap, flags, int(autoreset), _p(ain),
-                          _p(act), _p(rew), _p(done), _p(ply), _p(mask), _p(stats), _p(final))
+                          _p(act), _p(rew), _p(done), _p(ply), _p(mask), _p(stats), _p(final), int(episode0),
+                          _p(pl), 0 if pl is None else pl.shape[1], int(bool(mirror)), _p(pin_pos), _p(pinned))
     if r != 0:
+        if -r - 1 >= n_steps * n_slots:
+            raise ValueError("corrupt pinned snapshot for slot %d" % (-r - 1 - n_steps * n_slots))
         raise ValueError("illegal supplied action (flat index %d)" % (-r - 1))
     return dict(action=act, reward=rew, done=done, ply=ply, mask=mask, stats=stats, final=final)
 

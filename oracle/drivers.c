@@ -61,16 +61,64 @@ static int pick_random(const or_game* g, const uint32_t key[2], uint32_t c0, uin
 }
 
 /*
- * Run slots [slot0, slot0+n_slots) for n_steps steps each.  Outputs are
- * [n_steps][n_slots] (mask [n_steps][n_slots][1264]); any may be NULL.
- * stats[n_slots][8]: games ended by code 1..5, plies played, red wins, blue wins.
- * Returns 0, or -(1 + step*n_slots + slot) for an illegal supplied action.
+ * Reading R20 (setup pool, Sec. "Data Collection"; left-right orientation
+ * randomisation, App. "Learned Setups"): side s of a new game at (slot,
+ * episode) takes pool entry number uniform(word 0) of Philox at counter
+ * (slot, episode, 0, 7<<24 | s), an entry listing the types on the side's
+ * 40 setup squares in ascending square order; with mirroring on, the entry
+ * is mirrored left-right (file a <-> j) when word 1 is odd.
+ */
+static void pool_setup(uint64_t seed, uint32_t slot, uint32_t episode, const uint8_t* pool, int M, int mirror,
+                       uint8_t types[OR_NPIECE])
+{
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    for (int side = 0; side < 2; ++side) {
+        const uint32_t ctr[4] = { slot, episode, 0u, (7u << 24) | (uint32_t)side };
+        uint32_t w[4];
+        or_philox4x32_10(ctr, key, w);
+        const uint8_t* e = pool + ((size_t)side * (size_t)M + or_uniform(w[0], (uint32_t)M)) * 40;
+        const int flip = mirror && (w[1] & 1u);
+        for (int i = 0; i < 40; ++i) {
+            const int row = i / 10, col = i % 10;
+            types[40 * side + i] = e[10 * row + (flip ? 9 - col : col)];
+        }
+    }
+}
+
+/*
+ * A new game of a slot (App. B.1 reset, App. B.4 reset to a non-initial
+ * state): the pinned snapshot if the slot has one (reading R21: its
+ * history, two-square and chase state come with it), else the pool's
+ * setups, else the Philox setup.  Returns nonzero for a corrupt snapshot.
+ */
+static int new_game(or_game* g, uint64_t seed, uint32_t slot, uint32_t episode, const or_rules* rules,
+                    const uint8_t* pool, int M, int mirror, const uint8_t* pin)
+{
+    uint8_t types[OR_NPIECE];
+    if (pin) return or_import(g, pin, rules, 0);
+    if (pool) pool_setup(seed, slot, episode, pool, M, mirror, types);
+    else or_setup_types(seed, slot, episode, types);
+    or_game_init(g, types, rules, 0);
+    return 0;
+}
+
+/*
+ * Run slots [slot0, slot0+n_slots) for n_steps steps each, starting with
+ * episode episode0.  Outputs are [n_steps][n_slots] (mask
+ * [n_steps][n_slots][1264]); any may be NULL.  stats[n_slots][8]: games
+ * ended by code 1..5, plies played, red wins, blue wins.  pool[2][M][40]
+ * (or NULL) gives new games their setups; pins[n_slots][784] with pinned[i]
+ * != 0 makes slot i start and restart from its snapshot.
+ * Returns 0, -(1 + step*n_slots + slot) for an illegal supplied action, or
+ * -(1 + n_steps*n_slots + slot) for a corrupt pinned snapshot.
  */
 int orx_env_run(uint64_t seed, int slot0, int n_slots, int n_steps,
                 int k, int cap, int flags, int autoreset,
                 const int16_t* actions_in,
                 int16_t* action_out, int8_t* reward_out, uint8_t* done_out, int16_t* ply_out,
-                uint8_t* mask_out, uint32_t* stats, uint8_t* final_pos)
+                uint8_t* mask_out, uint32_t* stats, uint8_t* final_pos,
+                int episode0, const uint8_t* pool, int pool_m, int mirror, const uint8_t* pins,
+                const uint8_t* pinned)
 {
     or_rules rules = make_rules(k, cap, flags);
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
@@ -78,10 +126,12 @@ int orx_env_run(uint64_t seed, int slot0, int n_slots, int n_steps,
     int mv[400];
     for (int i = 0; i < n_slots; ++i) {
         uint32_t slot = (uint32_t)(slot0 + i);
-        uint32_t episode = 0;
-        uint8_t types[OR_NPIECE];
-        or_setup_types(seed, slot, episode, types);
-        or_game_init(g, types, &rules, 0);
+        uint32_t episode = (uint32_t)episode0;
+        const uint8_t* pin = (pins && pinned && pinned[i]) ? pins + (size_t)i * OR_POS_BYTES : NULL;
+        if (new_game(g, seed, slot, episode, &rules, pool, pool_m, mirror, pin)) {
+            free(g);
+            return -(int)(1 + (size_t)n_steps * (size_t)n_slots + (size_t)i);
+        }
         int terminated = 0;
         uint32_t st[8] = { 0 };
         for (int t = 0; t < n_steps; ++t) {
@@ -117,8 +167,7 @@ int orx_env_run(uint64_t seed, int slot0, int n_slots, int n_steps,
             if (code) {
                 if (autoreset) {
                     episode++;
-                    or_setup_types(seed, slot, episode, types);
-                    or_game_init(g, types, &rules, 0);
+                    new_game(g, seed, slot, episode, &rules, pool, pool_m, mirror, pin);
                 } else {
                     terminated = 1;
                 }
