@@ -141,8 +141,8 @@ def job_rate(units_per_rank, ms_local, world, dist=None, device="cpu"):
 
 # The sources the step kernel is compiled from (env.cu and what it includes).
 STEP_KERNEL_SOURCES = ("paper_2511_07312_gb300/csrc/env.cu", "paper_2511_07312_gb300/csrc/engine.cuh",
-                       "paper_2511_07312_gb300/csrc/snapshot.cuh", "paper_2511_07312_gb300/csrc/host_common.h",
-                       "include/stratego.h")
+                       "paper_2511_07312_gb300/csrc/snapshot.cuh", "paper_2511_07312_gb300/csrc/rollout.cuh",
+                       "paper_2511_07312_gb300/csrc/host_common.h", "include/stratego.h")
 
 
 def kernel_sources_sha256():

@@ -212,6 +212,43 @@ st_status st_env_stats(st_env* env, uint32_t* stats_out);
 st_status st_env_export(st_env* env, const int32_t* idx, int32_t n, st_position* out);
 st_status st_env_import(st_env* env, const int32_t* idx, int32_t n, const st_position* in);
 
+#define ST_POOL_MIRROR   1u          /* st_env_set_setup_pool: left-right orientation randomisation */
+#define ST_MAX_POOL      (1 << 20)   /* setups per side in a pool */
+
+/*
+ * st_env_set_setup_pool: new games (auto-reset, and st_env_reset without
+ * setups) take each side's setup from a pool of pre-generated setups (Sec.
+ * "Data Collection": a pool per player; App. "Learned Setups": left-right
+ * orientation randomisation).  Side s of the game of slot g at episode e
+ * takes entry uniform_below(w0, M) of pool[s], (w0, w1, w2, w3) being Philox
+ * at counter (g, e, 0, 7<<24 | s); with ST_POOL_MIRROR the entry is mirrored
+ * left-right (file a <-> j) when w1 is odd.
+ *   pool: device, [2][M][40] uint8: per side and entry, the types on the
+ *         side's 40 setup squares in ascending square order (red 0-39, blue
+ *         60-99); copied into the env (the caller keeps ownership).  M = 0
+ *         turns the pool off.
+ * Errors (nothing changes): ST_ERR_INVALID for M outside [0, ST_MAX_POOL],
+ * unknown flags, a NULL pool with M > 0, or an entry that is not one side's
+ * 40 pieces.  Synchronous: the pool is checked on the host.
+ */
+st_status st_env_set_setup_pool(st_env* env, const uint8_t* pool, int32_t M, uint32_t flags);
+
+/*
+ * st_env_pin: restarts from a fixed non-initial position (App. B.4, for
+ * search; the snapshot's history, two-square and chase state come with it,
+ * App. B.3).  From now on slot idx[i] restarts from states[i] whenever its
+ * game ends (auto-reset) and at st_env_reset without setups, its episode
+ * counter incremented as for any new game; games in progress continue.  Each
+ * call replaces the whole pin set (n = 0 clears it); with a slot listed
+ * twice the later entry wins.  Slots not pinned restart from the pool or
+ * the Philox setup.
+ *   idx[n] int32, states[n]: device, caller-owned, read in stream order.
+ * Errors: ST_ERR_INVALID for n outside [0, N] or NULL arrays with n > 0
+ * (nothing changes); a slot index outside [0, N) or an invalid snapshot
+ * leaves that entry unpinned and latches ST_ERR_BAD_POSITION.
+ */
+st_status st_env_pin(st_env* env, const int32_t* idx, int32_t n, const st_position* states);
+
 /*
  * Replay of action logs (App. B.1: states are reconstructed on demand from
  * compact records).  Game g < num_logs starts from setups[g] (type per piece

@@ -18,6 +18,7 @@ POS_BYTES = 784
 RULE_TWO_SQUARE = 1
 RULE_CHASE = 2
 RULES_ALL = RULE_TWO_SQUARE | RULE_CHASE
+POOL_MIRROR = 1          # st_env_set_setup_pool: left-right orientation randomisation
 ROLLOUT_MAGNET = 0x100   # rollouts, search, server: the magnet policy as the rollout policy
 AUTORESET = 4
 
@@ -97,6 +98,8 @@ def _declare(L):
         "st_env_stats": [vp, vp],
         "st_env_export": [vp, vp, i32, vp],
         "st_env_import": [vp, vp, i32, vp],
+        "st_env_set_setup_pool": [vp, vp, i32, ctypes.c_uint32],
+        "st_env_pin": [vp, vp, i32, vp],
         "st_replay_positions": [vp, vp, i32, i32, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp],
         "st_replay_set_chunk": [i32],
         "st_obs_encode": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
@@ -246,6 +249,25 @@ class Env:
     def import_(self, idx, pos):
         idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
         self._launch(lib().st_env_import, self._h, _ptr(idx), idx.numel(), _ptr(pos, torch.uint8, "positions"))
+
+    def set_setup_pool(self, pool, mirror=False):
+        """New games take their setups from pool [2, M, 40] uint8 (None: off)."""
+        if pool is None:
+            self._launch(lib().st_env_set_setup_pool, self._h, None, 0, 0)
+            return
+        pool = pool.to(device=self.device, dtype=torch.uint8).contiguous()
+        if pool.dim() != 3 or pool.shape[0] != 2 or pool.shape[2] != 40:
+            raise ValueError("pool must be [2, M, 40]")
+        self._launch(lib().st_env_set_setup_pool, self._h, _ptr(pool), pool.shape[1], POOL_MIRROR if mirror else 0)
+
+    def pin(self, idx=None, states=None):
+        """Slots idx restart from states [n, 784] whenever their games end
+        (replaces the previous pin set; no arguments: clear it)."""
+        if idx is None:
+            self._launch(lib().st_env_pin, self._h, None, 0, None)
+            return
+        idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
+        self._launch(lib().st_env_pin, self._h, _ptr(idx), idx.numel(), _ptr(states, torch.uint8, "states"))
 
 
 def _dev(t, dtype, device):

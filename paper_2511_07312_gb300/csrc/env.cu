@@ -6,8 +6,8 @@
 // 4 lanes), the shape chosen by st_env_set_launch.
 #include <algorithm>
 #include <cstring>
-#include "engine.cuh"
-#include "snapshot.cuh"
+#include <vector>
+#include "rollout.cuh"
 #include "host_common.h"
 
 using namespace stg;
@@ -30,6 +30,12 @@ struct st_env {
     int max_bps = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_key[11] = {0};
+    uint8_t* pool = nullptr;        // [2][pool_m][40] setups per side, or null
+    int pool_m = 0;
+    uint32_t pool_flags = 0;
+    int32_t* pin_of = nullptr;      // [N] pinned record of each slot, -1 none
+    RootState* pins = nullptr;      // [n_pins] pinned restart positions
+    int n_pins = 0;
 };
 
 namespace stg {
@@ -70,6 +76,11 @@ struct EnvArgs {
     int N;
     uint32_t k0, k1;
     Rules R;
+    const uint8_t* pool;      // setup pool, or null
+    int pool_m;
+    uint32_t pool_flags;
+    const int32_t* pin_of;    // null while no slot is pinned
+    const RootState* pins;
 };
 
 __device__ __forceinline__ void latch(int32_t* status, int code, int slot)
@@ -102,6 +113,65 @@ __device__ __forceinline__ bool setup_counts_ok(const uint8_t* s)
     return true;
 }
 
+// Setup pool (Sec. "Data Collection", App. "Learned Setups"): each side's
+// types from entry uniform_below(w0, M) of its pool, mirrored left-right
+// when mirroring is on and w1 is odd, (w0, w1) from Philox at counter
+// (slot, episode, 0, 7<<24 | side).  Writes G->c.type.
+template <int L>
+__device__ __noinline__ void pool_types(SmemGame* G, Team<L>, const uint8_t* pool, int M, uint32_t pool_flags,
+                                        uint32_t k0, uint32_t k1, uint32_t slot, uint32_t episode)
+{
+    const Team<L> T;
+    for (int p = T.tl; p < kPieces; p += L) {
+        const int side = p / 40, i = p - 40 * side;
+        const uint4 w = philox(make_uint4(slot, episode, 0u, (7u << 24) | (uint32_t)side), k0, k1);
+        const uint32_t e = uniform_below(w.x, (uint32_t)M);
+        const bool flip = (pool_flags & ST_POOL_MIRROR) && (w.y & 1u);
+        const int row = i / 10, col = i - 10 * row;
+        G->c.type[p] = pool[((size_t)side * (size_t)M + e) * 40 + 10 * row + (flip ? 9 - col : col)];
+    }
+    T.sync();
+}
+
+// Restart from a pinned position (App. B.4): its core, board, history ring
+// and chase positions, with the slot's new episode number.
+template <int L>
+__device__ __noinline__ void restart_pinned(SmemGame* G, Team<L>, const RootState* R, uint32_t episode, uint16_t* ring,
+                                            uint64_t* pi)
+{
+    const Team<L> T;
+    const uint4* src = reinterpret_cast<const uint4*>(R);
+    uint4* dst = reinterpret_cast<uint4*>(G);
+    for (int i = T.tl; i < (288 + 112) / 16; i += L) dst[i] = src[i];
+    const uint4* rs = reinterpret_cast<const uint4*>(R->ring);
+    uint4* rd = reinterpret_cast<uint4*>(ring);
+    for (int i = T.tl; i < kRing * 2 / 16; i += L) rd[i] = rs[i];
+    const int npi = R->c.n_pi;
+    for (int i = T.tl; i < 2 * npi; i += L) pi[i] = R->pi[i];
+    T.sync();
+    if (T.leader()) {
+        G->c.episode = episode;
+        G->c.terminated = 0;
+    }
+    T.sync();
+    derive_state(G, ring, pi, T);
+}
+
+// A new game of slot `slot` at `episode`: its pinned position, else the
+// setup pool, else the Philox setup.
+template <int L>
+__device__ __forceinline__ void new_game(SmemGame* G, const Team<L>& T, const EnvArgs& A, uint32_t slot,
+                                         uint32_t episode, uint16_t* ring, uint64_t* pi)
+{
+    const int pin = A.pin_of ? A.pin_of[slot] : -1;
+    if (pin >= 0) {
+        restart_pinned(G, T, A.pins + pin, episode, ring, pi);
+        return;
+    }
+    if (A.pool) pool_types(G, T, A.pool, A.pool_m, A.pool_flags, A.k0, A.k1, slot, episode);
+    reset_game(G, T, A.k0, A.k1, slot, episode, A.pool ? G->c.type : (const uint8_t*)nullptr);
+}
+
 // One ply of slot `slot` (App. B.1): the mask of the player to move is in
 // G->mask with count n.  given: the supplied action or -1 for the random
 // policy.
@@ -129,8 +199,8 @@ __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int&
     }
     if (res.code) {
         if (A.R.flags & kAutoreset) {
-            reset_game(G, T, A.k0, A.k1, slot, G->c.episode + 1, nullptr);
-            n = gen_moves(G, T, 0, A.R.flags, false, true, pi);
+            new_game(G, T, A, slot, G->c.episode + 1, ring, pi);
+            n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
         } else {
             if (T.leader()) G->c.terminated = (uint8_t)res.code;
             zero_mask(G, T);
@@ -179,8 +249,11 @@ __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* whi
         episode = G->c.episode + 1;
     }
     if (first && T.tl < 8) A.stats[8 * (size_t)g + T.tl] = 0;
-    reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
-    const int n = gen_moves(G, T, 0, A.R.flags, false, false, A.pi + (size_t)g * kPiWords);
+    uint16_t* ring = A.ring + (size_t)g * kRing;
+    uint64_t* pi = A.pi + (size_t)g * kPiWords;
+    if (setup) reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
+    else new_game(G, T, A, (uint32_t)g, episode, ring, pi);
+    const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
     if (T.leader()) G->c.n_legal = (uint16_t)n;
     store_core(G, A.core + g, T);
 }
@@ -351,11 +424,36 @@ __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_posi
     store_core(G, A.core + g, T);
 }
 
+// Warp per entry: the pinned record of states[i] for slot idx[i] (the later
+// entry wins for a slot listed twice).
+__global__ void k_env_pin(EnvArgs A, const int32_t* idx, int n, const st_position* states, RootState* recs,
+                          int32_t* pin_of)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int g = idx[i];
+    if (g < 0 || g >= A.N) {
+        if (lane == 0) latch(A.status, ST_ERR_BAD_POSITION, i);
+        return;
+    }
+    const int bad = build_root(S, states + i, recs + i);
+    if (lane == 0) {
+        if (bad) latch(A.status, ST_ERR_BAD_POSITION, i);
+        else atomicMax(&pin_of[g], i);
+    }
+}
+
 EnvArgs env_args(st_env* e)
 {
     EnvArgs a;
     a.core = e->core; a.ring = e->ring; a.pi = e->pi; a.stats = e->stats; a.status = e->status;
     a.N = e->N; a.k0 = (uint32_t)e->seed; a.k1 = (uint32_t)(e->seed >> 32); a.R = e->rules;
+    a.pool = e->pool; a.pool_m = e->pool_m; a.pool_flags = e->pool_flags;
+    a.pin_of = e->n_pins > 0 ? e->pin_of : nullptr;
+    a.pins = e->pins;
     return a;
 }
 
@@ -476,6 +574,7 @@ extern "C" st_status st_env_destroy(st_env* e)
     if (e->graph) cudaGraphExecDestroy(e->graph);
     cudaFree(e->core); cudaFree(e->ring); cudaFree(e->pi); cudaFree(e->stats);
     cudaFree(e->status); cudaFree(e->queue);
+    cudaFree(e->pool); cudaFree(e->pin_of); cudaFree(e->pins);
     delete e;
     return ST_OK;
 }
@@ -634,5 +733,92 @@ extern "C" st_status st_env_import(st_env* e, const int32_t* idx, int32_t n, con
     const int blocks = (n + kPlainWarps - 1) / kPlainWarps;
     k_env_import<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, idx, n, in);
     ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_set_setup_pool(st_env* e, const uint8_t* pool, int32_t M, uint32_t flags)
+{
+    ST_CHECK_ARG(e, "st_env_set_setup_pool: null env");
+    ST_CHECK_ARG(M >= 0 && M <= ST_MAX_POOL, "st_env_set_setup_pool: M must be in [0, %d]", ST_MAX_POOL);
+    ST_CHECK_ARG((flags & ~ST_POOL_MIRROR) == 0, "st_env_set_setup_pool: unknown flags");
+    ST_CHECK_ARG(M == 0 || pool, "st_env_set_setup_pool: null pool");
+    DeviceGuard guard(e->device);
+    uint8_t* dev = nullptr;
+    if (M > 0) {
+        const size_t bytes = (size_t)2 * (size_t)M * 40;
+        std::vector<uint8_t> h(bytes);
+        ST_CUDA(cudaMemcpyAsync(h.data(), pool, bytes, cudaMemcpyDeviceToHost, e->stream));
+        ST_CUDA(cudaStreamSynchronize(e->stream));
+        static const int want[12] = {1, 8, 5, 4, 4, 4, 3, 2, 1, 1, 1, 6};
+        for (size_t k = 0; k < (size_t)2 * (size_t)M; ++k) {
+            int cnt[12] = {0};
+            bool ok = true;
+            for (int i = 0; i < 40 && ok; ++i) {
+                const uint8_t t = h[k * 40 + i];
+                if (t >= 12) ok = false;
+                else cnt[t]++;
+            }
+            for (int t = 0; t < 12 && ok; ++t) ok = cnt[t] == want[t];
+            ST_CHECK_ARG(ok, "st_env_set_setup_pool: side %d entry %d is not one side's 40 pieces", (int)(k / M),
+                         (int)(k % M));
+        }
+        cudaError_t err = cudaMalloc(&dev, bytes);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(dev, h.data(), bytes, cudaMemcpyHostToDevice, e->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+        if (err != cudaSuccess) {
+            cudaFree(dev);
+            stg::set_error("st_env_set_setup_pool: %s", cudaGetErrorString(err));
+            return err == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA;
+        }
+    }
+    ST_CUDA(cudaStreamSynchronize(e->stream));   // no launch still reads the old pool
+    cudaFree(e->pool);
+    e->pool = dev;
+    e->pool_m = M;
+    e->pool_flags = flags;
+    if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+    return ST_OK;
+}
+
+extern "C" st_status st_env_pin(st_env* e, const int32_t* idx, int32_t n, const st_position* states)
+{
+    ST_CHECK_ARG(e, "st_env_pin: null env");
+    ST_CHECK_ARG(n >= 0 && n <= e->N, "st_env_pin: n must be in [0, N]");
+    ST_CHECK_ARG(n == 0 || (idx && states), "st_env_pin: null argument");
+    DeviceGuard guard(e->device);
+    ST_CUDA(cudaStreamSynchronize(e->stream));   // no launch still reads the old pin set
+    if (!e->pin_of) {
+        cudaError_t err = cudaMalloc(&e->pin_of, (size_t)e->N * sizeof(int32_t));
+        if (err != cudaSuccess) {
+            e->pin_of = nullptr;
+            stg::set_error("st_env_pin: %s", cudaGetErrorString(err));
+            return ST_ERR_OOM;
+        }
+    }
+    cudaFree(e->pins);
+    e->pins = nullptr;
+    e->n_pins = 0;
+    if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+    ST_CUDA(cudaMemsetAsync(e->pin_of, 0xFF, (size_t)e->N * sizeof(int32_t), e->stream));
+    if (n == 0) return ST_OK;
+    RootState* recs = nullptr;
+    cudaError_t err = cudaMalloc(&recs, (size_t)n * sizeof(RootState));
+    if (err != cudaSuccess) {
+        stg::set_error("st_env_pin: %s", cudaGetErrorString(err));
+        return ST_ERR_OOM;
+    }
+    EnvArgs a = env_args(e);
+    const int blocks = (n + kPlainWarps - 1) / kPlainWarps;
+    k_env_pin<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(RolloutSmem), e->stream>>>(a, idx, n, states, recs,
+                                                                                          e->pin_of);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        cudaStreamSynchronize(e->stream);
+        cudaFree(recs);
+        stg::set_error("st_env_pin: launch failed: %s", cudaGetErrorString(err));
+        return ST_ERR_CUDA;
+    }
+    e->pins = recs;
+    e->n_pins = n;
     return ST_OK;
 }

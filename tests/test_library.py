@@ -58,3 +58,6 @@ def test_argument_errors_are_reported_without_a_gpu():
     # the rollout-policy bit is for rollouts only: the env refuses it
     magnet = st.st_env_config(8, 1, st.make_rules(flags=st.RULES_ALL | st.ROLLOUT_MAGNET), 0, 0, None)
     assert L.st_env_create(ctypes.byref(magnet), ctypes.byref(h)) == 1
+    # env configuration calls check their arguments before touching the env
+    assert L.st_env_set_setup_pool(None, None, 0, 0) == 1
+    assert L.st_env_pin(None, None, 0, None) == 1
