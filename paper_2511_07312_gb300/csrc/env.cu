@@ -67,6 +67,15 @@ extern "C" const char* st_version(void) { return "stratego-gb300 0.2 (sm_103a)";
 
 namespace {
 
+// Where new games come from besides the Philox setup.
+struct ResetSrc {
+    const uint8_t* pool;      // setup pool [2][pool_m][40], or null
+    const int32_t* pin_of;    // [N] pinned record per slot (-1 none), null while nothing is pinned
+    const RootState* pins;
+    int pool_m;
+    uint32_t pool_flags;
+};
+
 struct EnvArgs {
     GameCore* core;
     uint16_t* ring;
@@ -76,11 +85,7 @@ struct EnvArgs {
     int N;
     uint32_t k0, k1;
     Rules R;
-    const uint8_t* pool;      // setup pool, or null
-    int pool_m;
-    uint32_t pool_flags;
-    const int32_t* pin_of;    // null while no slot is pinned
-    const RootState* pins;
+    ResetSrc reset;
 };
 
 __device__ __forceinline__ void latch(int32_t* status, int code, int slot)
@@ -160,16 +165,28 @@ __device__ __noinline__ void restart_pinned(SmemGame* G, Team<L>, const RootStat
 // A new game of slot `slot` at `episode`: its pinned position, else the
 // setup pool, else the Philox setup.
 template <int L>
-__device__ __forceinline__ void new_game(SmemGame* G, const Team<L>& T, const EnvArgs& A, uint32_t slot,
-                                         uint32_t episode, uint16_t* ring, uint64_t* pi)
+__device__ __forceinline__ void new_game(SmemGame* G, const Team<L>& T, const ResetSrc& src, uint32_t k0, uint32_t k1,
+                                         uint32_t slot, uint32_t episode, uint16_t* ring, uint64_t* pi)
 {
-    const int pin = A.pin_of ? A.pin_of[slot] : -1;
+    const int pin = src.pin_of ? src.pin_of[slot] : -1;
     if (pin >= 0) {
-        restart_pinned(G, T, A.pins + pin, episode, ring, pi);
+        restart_pinned(G, T, src.pins + pin, episode, ring, pi);
         return;
     }
-    if (A.pool) pool_types(G, T, A.pool, A.pool_m, A.pool_flags, A.k0, A.k1, slot, episode);
-    reset_game(G, T, A.k0, A.k1, slot, episode, A.pool ? G->c.type : (const uint8_t*)nullptr);
+    if (src.pool) pool_types(G, T, src.pool, src.pool_m, src.pool_flags, k0, k1, slot, episode);
+    reset_game(G, T, k0, k1, slot, episode, src.pool ? G->c.type : (const uint8_t*)nullptr);
+}
+
+// Auto-reset inside a launch: the new game, then the mask of its player to
+// move (its move count returned).  One out-of-line call on the rare path.
+template <int L>
+__device__ __noinline__ int restart_slot(SmemGame* G, Team<L>, ResetSrc src, uint32_t k0, uint32_t k1,
+                                         uint32_t rule_flags, uint32_t slot, uint32_t episode, uint16_t* ring,
+                                         uint64_t* pi)
+{
+    const Team<L> T;
+    new_game(G, T, src, k0, k1, slot, episode, ring, pi);
+    return gen_moves(G, T, G->c.ply & 1, rule_flags, false, true, pi);
 }
 
 // One ply of slot `slot` (App. B.1): the mask of the player to move is in
@@ -199,8 +216,7 @@ __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int&
     }
     if (res.code) {
         if (A.R.flags & kAutoreset) {
-            new_game(G, T, A, slot, G->c.episode + 1, ring, pi);
-            n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
+            n = restart_slot(G, T, A.reset, A.k0, A.k1, A.R.flags, slot, G->c.episode + 1, ring, pi);
         } else {
             if (T.leader()) G->c.terminated = (uint8_t)res.code;
             zero_mask(G, T);
@@ -252,7 +268,7 @@ __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* whi
     uint16_t* ring = A.ring + (size_t)g * kRing;
     uint64_t* pi = A.pi + (size_t)g * kPiWords;
     if (setup) reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
-    else new_game(G, T, A, (uint32_t)g, episode, ring, pi);
+    else new_game(G, T, A.reset, A.k0, A.k1, (uint32_t)g, episode, ring, pi);
     const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
     if (T.leader()) G->c.n_legal = (uint16_t)n;
     store_core(G, A.core + g, T);
@@ -451,9 +467,9 @@ EnvArgs env_args(st_env* e)
     EnvArgs a;
     a.core = e->core; a.ring = e->ring; a.pi = e->pi; a.stats = e->stats; a.status = e->status;
     a.N = e->N; a.k0 = (uint32_t)e->seed; a.k1 = (uint32_t)(e->seed >> 32); a.R = e->rules;
-    a.pool = e->pool; a.pool_m = e->pool_m; a.pool_flags = e->pool_flags;
-    a.pin_of = e->n_pins > 0 ? e->pin_of : nullptr;
-    a.pins = e->pins;
+    a.reset.pool = e->pool; a.reset.pool_m = e->pool_m; a.reset.pool_flags = e->pool_flags;
+    a.reset.pin_of = e->n_pins > 0 ? e->pin_of : nullptr;
+    a.reset.pins = e->pins;
     return a;
 }
 
