@@ -249,6 +249,61 @@ st_status st_env_set_setup_pool(st_env* env, const uint8_t* pool, int32_t M, uin
  */
 st_status st_env_pin(st_env* env, const int32_t* idx, int32_t n, const st_position* states);
 
+#define ST_MAX_HISTORY 32767          /* steps kept by the history ring */
+
+/*
+ * History (App. B.1: the simulator doubles as the rollout buffer and
+ * answers queries about past time steps from a circular buffer).  A time
+ * step t counts env steps: st_env_step adds 1, st_env_run n_steps; the
+ * state at step t is every slot's state after t steps, before step t's ply.
+ * st_env_enable_history(H) keeps, per slot, one 4-byte record of each of
+ * the last H steps (action, ending code, red's reward, whether the step's
+ * state began a game): H x N x 4 bytes of device memory; H = 0 turns it off.
+ * Steps taken while it is off are not recorded; games in progress when it
+ * is turned on after steps were taken count as begun before the window.
+ * Past positions are rebuilt by replaying a game's recorded actions from
+ * its start (recompute rather than store, App. B.1), so a query about step
+ * t is answered for t in the window [max(first recorded step, now - H),
+ * now], and a slot's position only if its game began inside the window,
+ * as a new game (Philox setup, pool or pin) under the reset sources still
+ * in force.  Errors: ST_ERR_INVALID for t outside the window or a NULL
+ * output (nothing is enqueued); ST_ERR_OOM if the ring does not fit.
+ */
+st_status st_env_enable_history(st_env* env, int32_t H);
+
+/* Steps taken since create (App. B.1 CurrentStep). */
+st_status st_env_current_step(st_env* env, int64_t* now);
+
+/*
+ * Positions at step t (the state every historical query of App. B.1 is
+ * about: acting player = ply & 1, moves played = ply, moves since the last
+ * attack = battleless, unknown pieces and piece types from the flags and
+ * types; legal masks via st_positions_mask).  out[N]: snapshots (device).
+ * status[N] (may be NULL): 0 rebuilt, 2 the game began before the window
+ * or before the last change of the setup pool or pins, 3 it began from
+ * given setups or an import (out is then left unwritten; step t = now is
+ * always answered).  ended[N]: ending code of the slot's game if it was
+ * over at step t, else 0; since[N]: steps since the step that ended it
+ * (GetTerminatedSince; 0 while running, -1 if that step left the window).
+ */
+st_status st_env_history_positions(st_env* env, int64_t t, st_position* out, uint8_t* status, uint8_t* ended,
+                                   int32_t* since);
+
+/* The record of step t < now per slot (any output may be NULL): action
+ * played (-1 none; GetPlayedActions), ending code reported (1 flag captured,
+ * ...), red's reward (ComputeRewardPl0), and 0 or how the step's state began
+ * a game (1 new game, 2 given setups, 3 import). */
+st_status st_env_history_steps(st_env* env, int64_t t, int16_t* action, uint8_t* done, int8_t* reward,
+                               uint8_t* start);
+
+/* The setup and action log of each slot's game at step t, the input of
+ * st_obs_encode (game g, ply plies[g]) for its planes and mask at step t
+ * (ComputeInfostateTensor): setups[N][80], logs[N][L] (-1 after the last
+ * action), plies[N]; status[N] as for positions, plus 4 a pinned start (no
+ * setup to replay from) and 5 more than L actions. */
+st_status st_env_history_logs(st_env* env, int64_t t, int32_t L, uint8_t* setups, int16_t* logs, int16_t* plies,
+                              uint8_t* status);
+
 /*
  * Replay of action logs (App. B.1: states are reconstructed on demand from
  * compact records).  Game g < num_logs starts from setups[g] (type per piece
@@ -343,6 +398,18 @@ st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_
 st_status st_rollout(const st_position* pos, int32_t P, int32_t K, int32_t depth, uint64_t seed,
                      const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
                      int32_t* tallies, uint8_t* item_status, void* stream);
+
+/*
+ * st_positions_mask: for each snapshot, the legal mask of the player to move
+ * (App. B.1 ComputeLegalActionMask; the 1,264-byte layout of st_env_step),
+ * its number of legal moves (GetHasLegalMovement: > 0), and whether the
+ * two-square rule removes one of that player's moves (App. B.2,
+ * ComputeTwoSquareRuleApplies; 0 when the rules leave it off).  Arrays are
+ * device, caller-owned, [P] (mask [P][1264], 16-byte aligned); any output
+ * may be NULL.  item_status[P]: 0 ok, 1 invalid snapshot (outputs zero).
+ */
+st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* rules, uint8_t* mask,
+                            int32_t* n_legal, uint8_t* two_square, uint8_t* item_status, void* stream);
 
 #define ST_SEARCH_MAX_MOVES 256   /* one side never has more than 244 legal moves */
 

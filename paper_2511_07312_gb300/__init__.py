@@ -100,6 +100,12 @@ def _declare(L):
         "st_env_import": [vp, vp, i32, vp],
         "st_env_set_setup_pool": [vp, vp, i32, ctypes.c_uint32],
         "st_env_pin": [vp, vp, i32, vp],
+        "st_env_enable_history": [vp, i32],
+        "st_env_current_step": [vp, ctypes.POINTER(ctypes.c_int64)],
+        "st_env_history_positions": [vp, ctypes.c_int64, vp, vp, vp, vp],
+        "st_env_history_steps": [vp, ctypes.c_int64, vp, vp, vp, vp],
+        "st_env_history_logs": [vp, ctypes.c_int64, i32, vp, vp, vp, vp],
+        "st_positions_mask": [vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
         "st_replay_positions": [vp, vp, i32, i32, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp],
         "st_replay_set_chunk": [i32],
         "st_obs_encode": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
@@ -260,6 +266,39 @@ class Env:
             raise ValueError("pool must be [2, M, 40]")
         self._launch(lib().st_env_set_setup_pool, self._h, _ptr(pool), pool.shape[1], POOL_MIRROR if mirror else 0)
 
+    def enable_history(self, H):
+        """Keep a record of each of the last H steps (0: off)."""
+        self._launch(lib().st_env_enable_history, self._h, int(H))
+
+    def current_step(self):
+        v = ctypes.c_int64()
+        _check(lib().st_env_current_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def history_positions(self, t):
+        """Positions at step t: dict(pos [N, 784], status, ended, since)."""
+        out = dict(pos=self._empty((self.N, POS_BYTES), torch.uint8), status=self._empty(self.N, torch.uint8),
+                   ended=self._empty(self.N, torch.uint8), since=self._empty(self.N, torch.int32))
+        self._launch(lib().st_env_history_positions, self._h, int(t), _ptr(out["pos"]), _ptr(out["status"]),
+                     _ptr(out["ended"]), _ptr(out["since"]))
+        return out
+
+    def history_steps(self, t):
+        """The record of step t: dict(action, done, reward, start)."""
+        out = dict(action=self._empty(self.N, torch.int16), done=self._empty(self.N, torch.uint8),
+                   reward=self._empty(self.N, torch.int8), start=self._empty(self.N, torch.uint8))
+        self._launch(lib().st_env_history_steps, self._h, int(t), _ptr(out["action"]), _ptr(out["done"]),
+                     _ptr(out["reward"]), _ptr(out["start"]))
+        return out
+
+    def history_logs(self, t, L):
+        """Setups [N, 80], logs [N, L], plies [N], status [N] of the games at step t."""
+        out = dict(setups=self._empty((self.N, 80), torch.uint8), logs=self._empty((self.N, int(L)), torch.int16),
+                   plies=self._empty(self.N, torch.int16), status=self._empty(self.N, torch.uint8))
+        self._launch(lib().st_env_history_logs, self._h, int(t), int(L), _ptr(out["setups"]), _ptr(out["logs"]),
+                     _ptr(out["plies"]), _ptr(out["status"]))
+        return out
+
     def pin(self, idx=None, states=None):
         """Slots idx restart from states [n, 784] whenever their games end
         (replaces the previous pin set; no arguments: clear it)."""
@@ -322,6 +361,21 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
                             _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
                             _ptr(tallies), _ptr(status), _stream(stream)))
     return tallies, status
+
+
+def positions_mask(pos, k=100, cap=1000, flags=RULES_ALL, stream=None):
+    """Legal masks [P, 1264], move counts, two-square flags and status of snapshots."""
+    P = pos.shape[0]
+    dev = pos.device
+    out = dict(mask=torch.empty((P, MASK_BYTES), dtype=torch.uint8, device=dev),
+               n_legal=torch.empty(P, dtype=torch.int32, device=dev),
+               two_square=torch.empty(P, dtype=torch.uint8, device=dev),
+               status=torch.empty(P, dtype=torch.uint8, device=dev))
+    r = make_rules(k, cap, flags)
+    _check(lib().st_positions_mask(_ptr(pos, torch.uint8), P, ctypes.byref(r), _ptr(out["mask"]),
+                                   _ptr(out["n_legal"]), _ptr(out["two_square"]), _ptr(out["status"]),
+                                   _stream(stream)))
+    return out
 
 
 SEARCH_MAX_MOVES = 256

@@ -54,6 +54,9 @@ enum : int { kSpy = 0, kScout = 1, kMiner = 2, kMarshal = 9, kFlag = 10, kBomb =
 enum : int { kClBattle = 0, kClQuiet = 1, kClThreat = 2, kClEvade = 3 };
 
 constexpr uint32_t kTwoSquare = 1u, kChase = 2u, kAutoreset = 4u, kMagnet = 0x100u;
+// How a game began (env history): a new game (Philox setup, pool or pin), a
+// reset to given setups, an imported snapshot.
+enum : uint8_t { kFreshNew = 1, kFreshSetup = 2, kFreshImport = 3 };
 
 struct Rules {
     int k;          // battleless limit
@@ -76,10 +79,11 @@ struct __align__(16) GameCore {
     uint8_t ts_len[2];
     uint8_t ts_sq[2][4];
     uint8_t terminated;     // ending code of a finished game kept without auto-reset
-    uint8_t pad0;
+    uint8_t fresh;          // env history: this state began a game (kFresh*), 0 once a step is recorded
     uint16_t n_legal;
     uint32_t episode;
-    uint32_t pad1;
+    uint16_t hrow;          // env history: ring row of the next step
+    uint16_t hcur;          // env history: the fresh mark of the ply being played
     uint64_t hash_side[2];  // per side: XOR of zkey(pid, square) over its alive pieces
 };
 static_assert(sizeof(GameCore) == 288, "GameCore layout");

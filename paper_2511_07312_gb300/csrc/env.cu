@@ -36,6 +36,12 @@ struct st_env {
     int32_t* pin_of = nullptr;      // [N] pinned record of each slot, -1 none
     RootState* pins = nullptr;      // [n_pins] pinned restart positions
     int n_pins = 0;
+    long long now = 0;              // env steps taken (every slot advances one ply per step)
+    uint32_t* hist = nullptr;       // [H][N] history ring (see hist_after)
+    int H = 0;
+    long long* d_now = nullptr;     // device copy of `now` while the history is on
+    long long hist_start = 0;       // first step recorded
+    long long cfg_floor = 0;        // last change of the reset sources
 };
 
 namespace stg {
@@ -86,6 +92,9 @@ struct EnvArgs {
     uint32_t k0, k1;
     Rules R;
     ResetSrc reset;
+    uint32_t* hist;           // history ring [H][N], or null
+    const long long* now;     // steps taken before this launch
+    int H;
 };
 
 __device__ __forceinline__ void latch(int32_t* status, int code, int slot)
@@ -145,6 +154,8 @@ __device__ __noinline__ void restart_pinned(SmemGame* G, Team<L>, const RootStat
                                             uint64_t* pi)
 {
     const Team<L> T;
+    const uint16_t hrow = G->c.hrow, hcur = G->c.hcur;
+    T.sync();
     const uint4* src = reinterpret_cast<const uint4*>(R);
     uint4* dst = reinterpret_cast<uint4*>(G);
     for (int i = T.tl; i < (288 + 112) / 16; i += L) dst[i] = src[i];
@@ -157,6 +168,8 @@ __device__ __noinline__ void restart_pinned(SmemGame* G, Team<L>, const RootStat
     if (T.leader()) {
         G->c.episode = episode;
         G->c.terminated = 0;
+        G->c.hrow = hrow;
+        G->c.hcur = hcur;
     }
     T.sync();
     derive_state(G, ring, pi, T);
@@ -171,10 +184,12 @@ __device__ __forceinline__ void new_game(SmemGame* G, const Team<L>& T, const Re
     const int pin = src.pin_of ? src.pin_of[slot] : -1;
     if (pin >= 0) {
         restart_pinned(G, T, src.pins + pin, episode, ring, pi);
-        return;
+    } else {
+        if (src.pool) pool_types(G, T, src.pool, src.pool_m, src.pool_flags, k0, k1, slot, episode);
+        reset_game(G, T, k0, k1, slot, episode, src.pool ? G->c.type : (const uint8_t*)nullptr);
     }
-    if (src.pool) pool_types(G, T, src.pool, src.pool_m, src.pool_flags, k0, k1, slot, episode);
-    reset_game(G, T, k0, k1, slot, episode, src.pool ? G->c.type : (const uint8_t*)nullptr);
+    if (T.leader()) G->c.fresh = kFreshNew;
+    T.sync();
 }
 
 // Auto-reset inside a launch: the new game, then the mask of its player to
@@ -267,11 +282,39 @@ __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* whi
     if (first && T.tl < 8) A.stats[8 * (size_t)g + T.tl] = 0;
     uint16_t* ring = A.ring + (size_t)g * kRing;
     uint64_t* pi = A.pi + (size_t)g * kPiWords;
-    if (setup) reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
-    else new_game(G, T, A.reset, A.k0, A.k1, (uint32_t)g, episode, ring, pi);
+    if (setup) {
+        reset_game(G, T, A.k0, A.k1, (uint32_t)g, episode, setup);
+        if (T.leader()) G->c.fresh = kFreshSetup;
+    } else {
+        new_game(G, T, A.reset, A.k0, A.k1, (uint32_t)g, episode, ring, pi);
+    }
     const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
     if (T.leader()) G->c.n_legal = (uint16_t)n;
     store_core(G, A.core + g, T);
+}
+
+// History ring (App. B.1: a circular buffer of past steps): the row of a
+// step holds, per slot, the action played (bits 0-13, 0x3FFF for none), how
+// the game began if the step's state was its first (bits 14-15, kFresh*),
+// the ending code reported by the step (bits 16-18) and red's reward + 1
+// (bits 19-20).  The leader notes the mark before the ply (the ply may start
+// the next game) ...
+template <int L>
+__device__ __forceinline__ void hist_before(SmemGame* G, const Team<L>& T)
+{
+    if (T.leader()) {
+        G->c.hcur = G->c.fresh;
+        G->c.fresh = 0;
+    }
+}
+
+// ... and writes the row after it.
+__device__ __forceinline__ void hist_after(SmemGame* G, const EnvArgs& A, int g, const PlyResult& r)
+{
+    const uint32_t v = (r.action >= 0 ? (uint32_t)r.action : 0x3FFFu) | ((uint32_t)G->c.hcur << 14) |
+                       ((uint32_t)r.code << 16) | ((uint32_t)(reward_of(r) + 1) << 19);
+    A.hist[(size_t)G->c.hrow * (size_t)A.N + (size_t)g] = v;
+    G->c.hrow = (uint16_t)(G->c.hrow + 1 == A.H ? 0 : G->c.hrow + 1);
 }
 
 template <int L>
@@ -294,8 +337,13 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     else n = gen_moves(G, T, P, A.R.flags, false, true, pi);
     bool illegal = false;
     const int given = actions ? (int)actions[g] : -1;
+    if (A.hist) {
+        if (T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
+        hist_before(G, T);
+    }
     const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, given, ring, pi, illegal);
     if (T.leader()) {
+        if (A.hist) hist_after(G, A, g, r);
         if (illegal) latch(A.status, ST_ERR_ILLEGAL_ACTION, g);
         if (action_out) action_out[g] = (int16_t)r.action;
         if (reward_out) reward_out[g] = (int8_t)reward_of(r);
@@ -313,7 +361,7 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
         G->c.n_legal = (uint16_t)n;
     }
     if (mask_out) write_mask(G, T, mask_out + (size_t)g * kMaskBytes);
-    if (!illegal) store_core(G, A.core + g, T);
+    store_core(G, A.core + g, T);   // an illegal action changed nothing but the history marks
 }
 
 // Persistent form: each team claims gpf slots at a time from a global
@@ -350,11 +398,14 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             // the launch's counters live in shared memory, not in registers
             // that every engine call would have to save
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
+            if (A.hist && T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
+                if (A.hist) hist_before(G, T);
                 const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal);
                 const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
                 if (T.leader()) {
+                    if (A.hist) hist_after(G, A, g, r);
                     count_result(G->stat, r);
                     if (action_ring) action_ring[o] = (int16_t)r.action;
                     if (reward_ring) reward_ring[o] = (int8_t)reward_of(r);
@@ -376,23 +427,11 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
 
 // ----------------------------------------------------------------- snapshots
 
-__global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* out)
+// Warp: the snapshot of game G (history ring `ring`) into o.
+__device__ void export_position(const SmemGame* G, const uint16_t* ring, st_position* o)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const Team<32> T;
-    SmemGame* G = team_game<32>(smem);
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const int g = idx[i];
-    if (g < 0 || g >= A.N) {
-        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, i);
-        return;
-    }
-    load_core(G, A.core + g, T);
-    const uint16_t* ring = A.ring + (size_t)g * kRing;
-    st_position* o = out + i;
     uint8_t* ob = reinterpret_cast<uint8_t*>(o);
-    const int lane = T.tl;
+    const int lane = lane_id();
     for (int b = lane; b < 240; b += 32) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
     for (int h = lane; h < 256; h += 32) o->hist[h] = (uint16_t)hist_at(G, ring, h);
     if (lane == 0) {
@@ -409,6 +448,23 @@ __global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* 
         }
         for (int k = 0; k < 12; ++k) o->reserved1[k] = 0;
     }
+    __syncwarp();
+}
+
+__global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Team<32> T;
+    SmemGame* G = team_game<32>(smem);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int g = idx[i];
+    if (g < 0 || g >= A.N) {
+        if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, i);
+        return;
+    }
+    load_core(G, A.core + g, T);
+    export_position(G, A.ring + (size_t)g * kRing, out + i);
 }
 
 __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_position* in)
@@ -436,6 +492,7 @@ __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_posi
     if (T.leader()) {
         G->c.episode = episode;
         G->c.n_legal = (uint16_t)nl;
+        G->c.fresh = kFreshImport;
     }
     store_core(G, A.core + g, T);
 }
@@ -462,6 +519,203 @@ __global__ void k_env_pin(EnvArgs A, const int32_t* idx, int n, const st_positio
     }
 }
 
+// ----------------------------------------------------------------- history queries
+// Queries about the state at step t (App. B.1 historical queries): the game
+// holding a slot at step t is rebuilt from its start (the latest row in the
+// window with a start mark) by replaying the recorded actions.
+struct HistQuery {
+    const uint32_t* hist;
+    int H;
+    long long now;    // steps taken
+    long long lo;     // first step whose row is in the window
+    long long floor;  // games begun before this step used other reset sources
+    long long t;
+};
+
+__device__ __forceinline__ uint32_t hist_row(const HistQuery& Q, int N, int g, long long s)
+{
+    return Q.hist[(size_t)(s % Q.H) * (size_t)N + (size_t)g];
+}
+
+__device__ __forceinline__ uint32_t row_mark(uint32_t v) { return (v >> 14) & 3u; }
+__device__ __forceinline__ uint32_t row_done(uint32_t v) { return (v >> 16) & 7u; }
+
+// Warp: the latest step s in [lo, hi] whose row has a nonzero field
+// (field(v) != 0), -1 if none; val: that field.
+template <typename F>
+__device__ long long latest_row(const HistQuery& Q, int N, int g, long long hi, F field, uint32_t& val)
+{
+    const int lane = lane_id();
+    for (long long base = hi; base >= Q.lo; base -= 32) {
+        const long long s = base - lane;
+        const uint32_t f = s >= Q.lo ? field(hist_row(Q, N, g, s)) : 0u;
+        const uint32_t m = __ballot_sync(~0u, f != 0);
+        if (m) {
+            const int l = __ffs(m) - 1;
+            val = __shfl_sync(~0u, f, l);
+            return base - l;
+        }
+    }
+    val = 0;
+    return -1;
+}
+
+// Warp: where the game holding slot g at step Q.t began (-1: before the
+// window) and how (kFresh*).  At t = now a pending mark of the slot counts.
+__device__ long long game_start(const HistQuery& Q, const GameCore* cur, int N, int g, int& kind)
+{
+    if (Q.t == Q.now && cur->fresh) {
+        kind = cur->fresh;
+        return Q.now;
+    }
+    uint32_t k = 0;
+    const long long s0 = latest_row(Q, N, g, Q.t == Q.now ? Q.now - 1 : Q.t,
+                                    [](uint32_t v) { return row_mark(v); }, k);
+    kind = (int)k;
+    return s0;
+}
+
+// Warp: the episode number of the game that began at step s0 (counted back
+// from the slot's current episode over the later new games and resets).
+__device__ uint32_t episode_at(const HistQuery& Q, const GameCore* cur, int N, int g, long long s0)
+{
+    int cnt = 0;
+    for (long long s = s0 + 1 + lane_id(); s < Q.now; s += 32) {
+        const uint32_t m = row_mark(hist_row(Q, N, g, s));
+        cnt += (m == kFreshNew || m == kFreshSetup);
+    }
+    cnt = (int)__reduce_add_sync(~0u, (unsigned)cnt);
+    const int pending = (s0 < Q.now && (cur->fresh == kFreshNew || cur->fresh == kFreshSetup)) ? 1 : 0;
+    return cur->episode - (uint32_t)cnt - (uint32_t)pending;
+}
+
+// Warp per slot: the position at step t, how the game stood (ended: its
+// ending code if it was over, since: steps since the step that ended it),
+// and a status (0 ok; 2 the game began before the window or before the last
+// change of reset sources; 3 it began from given setups or an import; the
+// current step always has its position).
+__global__ void k_env_hist_positions(EnvArgs A, HistQuery Q, st_position* out, uint8_t* status, uint8_t* ended,
+                                     int32_t* since)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= A.N) return;
+    const Team<32> T;
+    const int lane = T.tl;
+    const GameCore* cur = A.core + g;
+    int kind = 0;
+    const long long s0 = game_start(Q, cur, A.N, g, kind);
+    // the step that ended the game, if it is over
+    uint32_t code = 0;
+    long long e = -1;
+    if (Q.t > Q.lo) {
+        const long long from = s0 >= 0 ? s0 : Q.lo;
+        HistQuery Qe = Q;
+        Qe.lo = from;
+        if (Q.t - 1 >= from) e = latest_row(Qe, A.N, g, Q.t - 1, [](uint32_t v) { return row_done(v); }, code);
+    }
+    if (Q.t == Q.now && cur->terminated && e < 0) code = cur->terminated;
+    if (lane == 0) {
+        if (ended) ended[g] = (uint8_t)code;
+        if (since) since[g] = e >= 0 ? (int32_t)(Q.t - e) : (code ? -1 : 0);
+    }
+    uint8_t st = 0;
+    if (Q.t == Q.now) {
+        load_core(&S->g, cur, T);
+        export_position(&S->g, A.ring + (size_t)g * kRing, out + g);
+    } else if (s0 < 0 || s0 < Q.floor) {
+        st = 2;
+    } else if (kind != kFreshNew) {
+        st = 3;
+    } else {
+        const uint32_t ep = episode_at(Q, cur, A.N, g, s0);
+        new_game(&S->g, T, A.reset, A.k0, A.k1, (uint32_t)g, ep, S->ring, S->pi);
+        for (long long base = s0; base < Q.t; base += 32) {
+            const long long s = base + lane;
+            const uint32_t v = s < Q.t ? hist_row(Q, A.N, g, s) : 0x3FFFu;
+            const int cnt = (int)min(32LL, Q.t - base);
+            for (int j = 0; j < cnt; ++j) {
+                const int a = (int)(__shfl_sync(~0u, v, j) & 0x3FFFu);
+                if (a != 0x3FFF) apply_move(&S->g, T, a, S->ring, S->pi);
+            }
+        }
+        export_position(&S->g, S->ring, out + g);
+    }
+    if (lane == 0 && status) status[g] = st;
+}
+
+// Thread per slot: the row of step t (t < now): action (-1 none), ending
+// code, red's reward, start mark.
+__global__ void k_env_hist_steps(int N, HistQuery Q, int16_t* action, uint8_t* done, int8_t* reward, uint8_t* start)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const uint32_t v = hist_row(Q, N, g, Q.t);
+    const uint32_t a = v & 0x3FFFu;
+    if (action) action[g] = a == 0x3FFFu ? (int16_t)-1 : (int16_t)a;
+    if (done) done[g] = (uint8_t)row_done(v);
+    if (reward) reward[g] = (int8_t)((int)((v >> 19) & 3u) - 1);
+    if (start) start[g] = (uint8_t)row_mark(v);
+}
+
+// Warp per slot: the setup and the action log of the game at step t, for
+// st_obs_encode (status 0 ok, 2 and 3 as for positions, 4 a pinned start,
+// 5 more than L actions).
+__global__ void k_env_hist_logs(EnvArgs A, HistQuery Q, int L, uint8_t* setups, int16_t* logs, int16_t* plies,
+                                uint8_t* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemGame* G = team_game<32>(smem);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= A.N) return;
+    const Team<32> T;
+    const int lane = T.tl;
+    const GameCore* cur = A.core + g;
+    int kind = 0;
+    const long long s0 = game_start(Q, cur, A.N, g, kind);
+    int16_t* log = logs + (size_t)g * (size_t)L;
+    uint8_t st = 0;
+    if (s0 < 0 || s0 < Q.floor) st = 2;
+    else if (kind != kFreshNew) st = 3;
+    else if (A.reset.pin_of && A.reset.pin_of[g] >= 0) st = 4;
+    int n = 0;
+    if (!st) {
+        const uint32_t ep = episode_at(Q, cur, A.N, g, s0);
+        if (A.reset.pool) pool_types(G, T, A.reset.pool, A.reset.pool_m, A.reset.pool_flags, A.k0, A.k1, (uint32_t)g, ep);
+        reset_game(G, T, A.k0, A.k1, (uint32_t)g, ep, A.reset.pool ? G->c.type : (const uint8_t*)nullptr);
+        for (int i = lane; i < kPieces; i += 32) setups[(size_t)g * kPieces + i] = G->c.type[i];
+        for (long long base = s0; base < Q.t; base += 32) {
+            const long long s = base + lane;
+            const uint32_t a = s < Q.t ? (hist_row(Q, A.N, g, s) & 0x3FFFu) : 0x3FFFu;
+            const bool has = a != 0x3FFFu;
+            const uint32_t m = __ballot_sync(~0u, has);
+            const int o = n + __popc(m & ((1u << lane) - 1u));
+            if (has && o < L) log[o] = (int16_t)a;
+            n += __popc(m);
+        }
+        if (n > L) st = 5;
+    } else {
+        for (int i = lane; i < kPieces; i += 32) setups[(size_t)g * kPieces + i] = 0;
+    }
+    for (int i = n + lane; i < L; i += 32) log[i] = -1;
+    if (lane == 0) {
+        plies[g] = (int16_t)(st ? 0 : n);
+        if (status) status[g] = st;
+    }
+}
+
+__global__ void k_env_advance(long long* now, int n)
+{
+    *now += n;
+}
+
+__global__ void k_env_clear_marks(GameCore* core, int N)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < N) core[g].fresh = 0;
+}
+
 EnvArgs env_args(st_env* e)
 {
     EnvArgs a;
@@ -470,7 +724,22 @@ EnvArgs env_args(st_env* e)
     a.reset.pool = e->pool; a.reset.pool_m = e->pool_m; a.reset.pool_flags = e->pool_flags;
     a.reset.pin_of = e->n_pins > 0 ? e->pin_of : nullptr;
     a.reset.pins = e->pins;
+    a.hist = e->hist;
+    a.H = e->H;
+    a.now = e->d_now;
     return a;
+}
+
+HistQuery hist_query(st_env* e, long long t)
+{
+    HistQuery q;
+    q.hist = e->hist;
+    q.H = e->H;
+    q.now = e->now;
+    q.lo = std::max(e->hist_start, e->now - (long long)e->H);
+    q.floor = e->cfg_floor;
+    q.t = t;
+    return q;
 }
 
 constexpr int kPlainWarps = 4;
@@ -591,6 +860,7 @@ extern "C" st_status st_env_destroy(st_env* e)
     cudaFree(e->core); cudaFree(e->ring); cudaFree(e->pi); cudaFree(e->stats);
     cudaFree(e->status); cudaFree(e->queue);
     cudaFree(e->pool); cudaFree(e->pin_of); cudaFree(e->pins);
+    cudaFree(e->hist); cudaFree(e->d_now);
     delete e;
     return ST_OK;
 }
@@ -617,6 +887,11 @@ extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* act
     k_env_step<32><<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
         a, actions, action_out, reward_out, done_out, ply_out, mask_out);
     ST_CUDA(cudaGetLastError());
+    if (e->hist) {
+        k_env_advance<<<1, 1, 0, e->stream>>>(e->d_now, 1);
+        ST_CUDA(cudaGetLastError());
+    }
+    e->now += 1;
     return ST_OK;
 }
 
@@ -668,6 +943,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
     if (e->stream != nullptr) {
         if (e->graph && std::memcmp(key, e->graph_key, sizeof(key)) == 0) {
             ST_CUDA(cudaGraphLaunch(e->graph, e->stream));
+            e->now += n_steps;
             return ST_OK;
         }
         if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
@@ -675,6 +951,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         ST_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream);
         launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+        if (e->hist) k_env_advance<<<1, 1, 0, e->stream>>>(e->d_now, n_steps);
         const cudaError_t launch_err = cudaGetLastError();
         const cudaError_t cap_err = cudaStreamEndCapture(e->stream, &graph);
         if (launch_err != cudaSuccess || cap_err != cudaSuccess) {
@@ -692,11 +969,17 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         }
         std::memcpy(e->graph_key, key, sizeof(key));
         ST_CUDA(cudaGraphLaunch(e->graph, e->stream));
+        e->now += n_steps;
         return ST_OK;
     }
     ST_CUDA(cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream));
     launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
     ST_CUDA(cudaGetLastError());
+    if (e->hist) {
+        k_env_advance<<<1, 1, 0, e->stream>>>(e->d_now, n_steps);
+        ST_CUDA(cudaGetLastError());
+    }
+    e->now += n_steps;
     return ST_OK;
 }
 
@@ -792,6 +1075,7 @@ extern "C" st_status st_env_set_setup_pool(st_env* e, const uint8_t* pool, int32
     e->pool = dev;
     e->pool_m = M;
     e->pool_flags = flags;
+    e->cfg_floor = e->now;
     if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
     return ST_OK;
 }
@@ -814,6 +1098,7 @@ extern "C" st_status st_env_pin(st_env* e, const int32_t* idx, int32_t n, const 
     cudaFree(e->pins);
     e->pins = nullptr;
     e->n_pins = 0;
+    e->cfg_floor = e->now;
     if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
     ST_CUDA(cudaMemsetAsync(e->pin_of, 0xFF, (size_t)e->N * sizeof(int32_t), e->stream));
     if (n == 0) return ST_OK;
@@ -836,5 +1121,96 @@ extern "C" st_status st_env_pin(st_env* e, const int32_t* idx, int32_t n, const 
     }
     e->pins = recs;
     e->n_pins = n;
+    return ST_OK;
+}
+
+extern "C" st_status st_env_enable_history(st_env* e, int32_t H)
+{
+    ST_CHECK_ARG(e, "st_env_enable_history: null env");
+    ST_CHECK_ARG(H >= 0 && H <= ST_MAX_HISTORY, "st_env_enable_history: H must be in [0, %d]", ST_MAX_HISTORY);
+    DeviceGuard guard(e->device);
+    ST_CUDA(cudaStreamSynchronize(e->stream));   // no launch still writes the old ring
+    if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+    cudaFree(e->hist);
+    e->hist = nullptr;
+    e->H = 0;
+    if (H == 0) return ST_OK;
+    cudaError_t err = cudaSuccess;
+    if (!e->d_now) err = cudaMalloc(&e->d_now, sizeof(long long));
+    if (err == cudaSuccess) err = cudaMalloc(&e->hist, (size_t)H * (size_t)e->N * sizeof(uint32_t));
+    if (err != cudaSuccess) {
+        e->hist = nullptr;
+        cudaGetLastError();
+        stg::set_error("st_env_enable_history: %zu bytes: %s", (size_t)H * (size_t)e->N * sizeof(uint32_t),
+                       cudaGetErrorString(err));
+        return ST_ERR_OOM;
+    }
+    const long long now = e->now;
+    ST_CUDA(cudaMemcpyAsync(e->d_now, &now, sizeof(now), cudaMemcpyHostToDevice, e->stream));
+    // start marks left from before are stale once steps were taken unrecorded
+    if (now > 0) k_env_clear_marks<<<(e->N + 255) / 256, 256, 0, e->stream>>>(e->core, e->N);
+    ST_CUDA(cudaGetLastError());
+    ST_CUDA(cudaStreamSynchronize(e->stream));
+    e->H = H;
+    e->hist_start = now;
+    return ST_OK;
+}
+
+extern "C" st_status st_env_current_step(st_env* e, int64_t* now)
+{
+    ST_CHECK_ARG(e && now, "st_env_current_step: null argument");
+    *now = e->now;
+    return ST_OK;
+}
+
+static st_status hist_window(st_env* e, int64_t t, bool need_row, const char* fn)
+{
+    ST_CHECK_ARG(e, "%s: null env", fn);
+    ST_CHECK_ARG(e->hist, "%s: the history is off (st_env_enable_history)", fn);
+    const long long lo = std::max(e->hist_start, e->now - (long long)e->H);
+    const long long hi = need_row ? e->now - 1 : e->now;
+    ST_CHECK_ARG(t >= lo && t <= hi, "%s: step %lld outside the window [%lld, %lld]", fn, (long long)t, lo, hi);
+    return ST_OK;
+}
+
+extern "C" st_status st_env_history_positions(st_env* e, int64_t t, st_position* out, uint8_t* status,
+                                              uint8_t* ended, int32_t* since)
+{
+    const st_status w = hist_window(e, t, false, "st_env_history_positions");
+    if (w != ST_OK) return w;
+    ST_CHECK_ARG(out, "st_env_history_positions: null out");
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_hist_positions<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(RolloutSmem), e->stream>>>(
+        a, hist_query(e, t), out, status, ended, since);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_history_steps(st_env* e, int64_t t, int16_t* action, uint8_t* done, int8_t* reward,
+                                          uint8_t* start)
+{
+    const st_status w = hist_window(e, t, true, "st_env_history_steps");
+    if (w != ST_OK) return w;
+    DeviceGuard guard(e->device);
+    k_env_hist_steps<<<(e->N + 255) / 256, 256, 0, e->stream>>>(e->N, hist_query(e, t), action, done, reward, start);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_history_logs(st_env* e, int64_t t, int32_t L, uint8_t* setups, int16_t* logs,
+                                         int16_t* plies, uint8_t* status)
+{
+    const st_status w = hist_window(e, t, false, "st_env_history_logs");
+    if (w != ST_OK) return w;
+    ST_CHECK_ARG(L >= 1 && L <= 32767, "st_env_history_logs: L must be in [1, 32767]");
+    ST_CHECK_ARG(setups && logs && plies, "st_env_history_logs: null argument");
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_hist_logs<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
+        a, hist_query(e, t), L, setups, logs, plies, status);
+    ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

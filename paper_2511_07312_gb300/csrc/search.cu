@@ -297,6 +297,40 @@ __global__ void k_search_policy(int P, int S, uint32_t k0, uint32_t k1, const ui
     for (int j = lane; j < n; j += 32) pp[j] = __ddiv_rn(w[j], W);
 }
 
+// Warp per snapshot: the legal mask of the player to move, its move count,
+// and whether the two-square rule removes one of its moves.
+__global__ void k_positions_mask(const st_position* pos, int P, Rules Rl, uint8_t* mask, int32_t* n_legal,
+                                 uint8_t* two_square, uint8_t* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= P) return;
+    const Team<32> T;
+    const int lane = T.tl;
+    const int bad = import_position(&S->g, pos + p, S->ring, S->pi);
+    int n = 0, ts = 0;
+    if (!bad) {
+        const int Pl = S->g.c.ply & 1;
+        n = gen_moves(&S->g, T, Pl, Rl.flags, false, true, S->pi);
+        if (Rl.flags & kTwoSquare) {
+            const int n_ts = gen_moves(&S->g, T, Pl, kTwoSquare, false, false, S->pi);
+            const int n_ph = gen_moves(&S->g, T, Pl, 0u, true, false, S->pi);
+            ts = n_ts < n_ph;
+        }
+    }
+    if (mask) {
+        uint4* d = reinterpret_cast<uint4*>(mask + (size_t)p * kMaskBytes);
+        const uint4* m = reinterpret_cast<const uint4*>(S->g.mask);
+        for (int i = lane; i < kMaskBytes / 16; i += 32) d[i] = bad ? make_uint4(0, 0, 0, 0) : m[i];
+    }
+    if (lane == 0) {
+        if (n_legal) n_legal[p] = n;
+        if (two_square) two_square[p] = (uint8_t)ts;
+        if (status) status[p] = bad ? 1 : 0;
+    }
+}
+
 }  // namespace
 
 extern "C" st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_t seed,
@@ -402,5 +436,25 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
         stg::set_error("st_search: launch failed: %s", cudaGetErrorString(err));
         return ST_ERR_CUDA;
     }
+    return ST_OK;
+}
+
+extern "C" st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* rules, uint8_t* mask,
+                                       int32_t* n_legal, uint8_t* two_square, uint8_t* item_status, void* stream)
+{
+    ST_CHECK_ARG(rules_ok(rules), "st_positions_mask: invalid rules");
+    ST_CHECK_ARG(P >= 0, "st_positions_mask: P < 0");
+    if (P == 0) return ST_OK;
+    ST_CHECK_ARG(pos, "st_positions_mask: null positions");
+    ST_CHECK_ARG(!mask || aligned16(mask), "st_positions_mask: mask must be 16-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Rules r;
+    r.k = rules->battleless_limit;
+    r.cap = rules->max_plies;
+    r.flags = rules->flags;
+    const int blocks = (P + kRootWarps - 1) / kRootWarps;
+    k_positions_mask<<<blocks, 32 * kRootWarps, kRootWarps * sizeof(RolloutSmem), s>>>(pos, P, r, mask, n_legal,
+                                                                                      two_square, item_status);
+    ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

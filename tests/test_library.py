@@ -61,3 +61,6 @@ def test_argument_errors_are_reported_without_a_gpu():
     # env configuration calls check their arguments before touching the env
     assert L.st_env_set_setup_pool(None, None, 0, 0) == 1
     assert L.st_env_pin(None, None, 0, None) == 1
+    assert L.st_env_enable_history(None, 10) == 1
+    assert L.st_env_history_positions(None, 0, None, None, None, None) == 1
+    assert L.st_positions_mask(None, 1, ctypes.byref(st.make_rules(k=0)), None, None, None, None, None) == 1
