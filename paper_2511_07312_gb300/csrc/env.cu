@@ -370,7 +370,7 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
 // At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
 // thread; shared memory, not registers, bounds the resident teams.
 constexpr int kRunMaxWarps = 8;
-template <int L>
+template <int L, bool kHist>
 __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
                                                  int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
                                                  int16_t* ply_ring, uint8_t* mask_ring)
@@ -398,14 +398,14 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             // the launch's counters live in shared memory, not in registers
             // that every engine call would have to save
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
-            if (A.hist && T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
+            if (kHist && T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
-                if (A.hist) hist_before(G, T);
+                if (kHist) hist_before(G, T);
                 const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal);
                 const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
                 if (T.leader()) {
-                    if (A.hist) hist_after(G, A, g, r);
+                    if (kHist) hist_after(G, A, g, r);
                     count_result(G->stat, r);
                     if (action_ring) action_ring[o] = (int16_t)r.action;
                     if (reward_ring) reward_ring[o] = (int8_t)reward_of(r);
@@ -757,8 +757,12 @@ template <int L>
 cudaError_t run_occupancy_t(int wpb, int* occ)
 {
     const size_t smem = run_smem(wpb, 32 / L);
-    cudaError_t e = cudaFuncSetAttribute(k_env_run<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<L>, 32 * wpb, smem);
+    // both forms of the kernel (with and without the history ring) get the
+    // shared-memory limit; their occupancy is that of the form without it
+    cudaError_t e = cudaFuncSetAttribute(k_env_run<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_run<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_env_run<L, false>, 32 * wpb, smem);
     if (e != cudaSuccess) cudaGetLastError();   // leave no pending error behind for later launches
     return e;
 }
@@ -777,8 +781,12 @@ template <int L>
 void launch_run_t(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
                   int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
 {
-    k_env_run<L><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
-        a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    if (a.hist)
+        k_env_run<L, true><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
+            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    else
+        k_env_run<L, false><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
+            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
 }
 
 void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
