@@ -44,9 +44,10 @@ def parse():
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
     p.add_argument("--gpw", type=int, default=0, help="games per warp, 1, 2, 4 or 8 (0 = tuned default)")
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--profile", action="store_true",
-                   help="time the persistent step launch only (for profiler captures): no plain path, "
-                        "end-to-end, secondary workloads or CPU baseline")
+    p.add_argument("--profile", nargs="?", const="step", default=None, choices=["step", "rollout"],
+                   help="for profiler captures: time one workload only -- the persistent step launch "
+                        "(step, the default) or the belief-sample rollouts of 4,096 positions (rollout); "
+                        "no plain path, end-to-end, other workloads or CPU baseline")
     return p.parse_args()
 
 
@@ -238,6 +239,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    if args.profile == "rollout":
+        if rank == 0:
+            profile_rollouts(st, torch, dev, args)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     N, S, R = args.games, args.plies, args.ring
     env = st.Env(N, seed=args.seed + rank, device=local)
     tuned = None
@@ -363,13 +370,11 @@ def main():
         dist.destroy_process_group()
 
 
-def secondary(st, torch, dev, args):
-    """Observation planes of 16,384 replayed positions, belief-sample
-    rollouts of 4,096 positions, the per-move search of 256 positions, and
-    the serving workload."""
+def game_positions(st, torch, dev, B=16384):
+    """64 random-policy games (seed 1) played on the GPU to their end or the
+    1,000-ply cap, and B (game, ply) items at plies uniform in [0, min(600,
+    length - 1)], sorted by (game, ply)."""
     import numpy as np
-    out = {}
-    # 64 random-policy games (seed 1) played on the GPU to their end or the 1,000-ply cap
     G = 64
     env = st.Env(G, seed=1, autoreset=False, device=dev.index)
     setups = env.export(torch.arange(G))[:, :80].contiguous()
@@ -377,14 +382,52 @@ def secondary(st, torch, dev, args):
     env.sync()
     acts = traj["action"].t().contiguous()
     lengths = (acts >= 0).sum(1).cpu().numpy()
+    env.close()
     rng = np.random.default_rng(3)
-    B = 16384
     games = rng.integers(0, G, B).astype(np.int32)
     plies = np.array([rng.integers(0, min(600, max(1, lengths[g]) - 1) + 1) for g in games], np.int16)
     order = np.lexsort((plies, games))
     games, plies = games[order], plies[order]
-    gi = torch.from_numpy(games).to(dev)
-    pl = torch.from_numpy(plies).to(dev)
+    return setups, acts, torch.from_numpy(games).to(dev), torch.from_numpy(plies).to(dev)
+
+
+def rollout_positions(st, torch, dev, setups, acts, gi, pl, P=4096):
+    """P of the items, evenly spaced, as snapshots."""
+    import numpy as np
+    sel = torch.from_numpy(np.linspace(0, gi.numel() - 1, P).astype(np.int64)).to(dev)
+    pos, _ = st.replay_positions(setups, acts, gi[sel].contiguous(), pl[sel].contiguous())
+    return pos
+
+
+def profile_rollouts(st, torch, dev, args):
+    """The belief-sample rollout workload alone (4,096 positions x 256
+    samples x depth 32), for profiler captures."""
+    pos = rollout_positions(st, torch, dev, *game_positions(st, torch, dev))
+    K, D = 256, 32
+    tallies, _ = st.rollout(pos, K, D, seed=7)
+    for _ in range(args.warmup):
+        st.rollout(pos, K, D, seed=7, out=tallies)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(args.steps):
+        st.rollout(pos, K, D, seed=7, out=tallies)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    print(json.dumps({"profile": "rollout", "positions": pos.shape[0], "K": K, "depth": D, "ms_per_call": ms,
+                      "samples_per_s": pos.shape[0] * K / (ms / 1000)}), flush=True)
+
+
+def secondary(st, torch, dev, args):
+    """Observation planes of 16,384 replayed positions, belief-sample
+    rollouts of 4,096 positions, the per-move search of 256 positions, and
+    the serving workload."""
+    import numpy as np
+    out = {}
+    setups, acts, gi, pl = game_positions(st, torch, dev)
+    B = gi.numel()
     o = st.obs_encode(setups, acts, gi, pl)
     torch.cuda.synchronize()
     reps = 5
@@ -401,8 +444,7 @@ def secondary(st, torch, dev, args):
                          "positions": B, "bytes_written_per_position": 487 * 100 * 3 + MASK_BYTES}
     # belief-sample rollouts: 4,096 positions x 256 samples x depth 32
     P, K, D = 4096, 256, 32
-    sel = np.linspace(0, B - 1, P).astype(np.int64)
-    pos, status = st.replay_positions(setups, acts, gi[sel].contiguous(), pl[sel].contiguous())
+    pos = rollout_positions(st, torch, dev, setups, acts, gi, pl, P)
     tallies, _ = st.rollout(pos, K, D, seed=7)
     torch.cuda.synchronize()
     t0.record()
@@ -416,6 +458,18 @@ def secondary(st, torch, dev, args):
     out["belief_rollout"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K, "depth": D,
                              "ply_steps_per_s_upper": P * K * D / (ms / 1000),
                              "tallies_win_loss_draw_unfinished": tl}
+    # the same rollouts with the magnet policy as the rollout policy
+    mflags = st.RULES_ALL | st.ROLLOUT_MAGNET
+    st.rollout(pos, K, D, seed=7, out=tallies, flags=mflags)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(reps):
+        st.rollout(pos, K, D, seed=7, out=tallies, flags=mflags)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    out["belief_rollout_magnet"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K,
+                                    "depth": D, "tallies_win_loss_draw_unfinished": tallies.sum(0).cpu().tolist()}
     # per-move search (App. E steps 1-4): 256 positions x every legal move x
     # 16 configurations x depth 40, then the tabular update and the sampled move
     Ps, Ss, Ds = 256, 16, 40
@@ -433,8 +487,28 @@ def secondary(st, torch, dev, args):
     out["search"] = {"positions_per_s": Ps / (ms / 1000), "rollouts_per_s": n_roll / (ms / 1000), "ms": ms,
                      "positions": Ps, "S": Ss, "depth": Ds, "rollouts": n_roll,
                      "mean_legal_moves": n_roll / Ss / Ps}
+    # historical queries: 16,384 slots recording 1,000 steps; positions at
+    # step now - 300 rebuilt by replay
+    Nh, Hh = 16384, 1000
+    henv = st.Env(Nh, seed=5, device=dev.index)
+    henv.enable_history(Hh)
+    henv.run(Hh)
+    henv.sync()
+    th = henv.current_step() - 300
+    hp = henv.history_positions(th)
+    torch.cuda.synchronize()
+    t0.record()
+    reps = 3
+    for _ in range(reps):
+        hp = henv.history_positions(th)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    rebuilt = int((hp["status"] == 0).sum().item())
+    out["history_positions"] = {"slots": Nh, "H": Hh, "step": th, "rebuilt": rebuilt, "ms": ms,
+                                "positions_per_s": rebuilt / (ms / 1000)}
+    henv.close()
     out["serving"] = serving(st, torch, dev, pos.cpu().numpy(), args)
-    env.close()
     return out
 
 

@@ -115,10 +115,12 @@ struct __align__(16) RolloutSmem {
     uint8_t types[48];
 };
 
-// A rollout team's record when no history ring is kept.
+// A rollout team's shared-memory record when no history ring is kept; its
+// chase store lives in a global scratch slot of the team (the newest four
+// entries are cached in the game record), which halves the shared memory a
+// rollout needs and doubles the teams an SM can hold.
 struct __align__(16) FlatSmem {
     SmemGame g;
-    uint64_t pi[kPiWords];
     uint8_t types[48];
 };
 

@@ -71,6 +71,7 @@ constexpr int kRootWarps = 4;
 constexpr int kFlatLanes = 8;                              // one rollout per 8-lane team
 constexpr int kFlatWarps = 2;
 constexpr int kFlatTeams = 32 * kFlatWarps / kFlatLanes;   // rollouts per block
+constexpr int kFlatMinBlocks = 12;                          // resident blocks per SM the registers allow
 
 __global__ void k_roots(const st_position* pos, int P, RootState* roots, uint8_t* status)
 {
@@ -82,25 +83,52 @@ __global__ void k_roots(const st_position* pos, int P, RootState* roots, uint8_t
     if (lane_id() == 0 && status) status[p] = roots[p].bad ? 1 : 0;
 }
 
-// One (position, sample) unit per 8-lane team; consecutive teams of a block
+// One (position, sample) unit per 8-lane team at a time, grid-stride over
+// the units with a grid of resident blocks; consecutive teams of a block
 // share a position, so its root and plan come mostly from L1.  A rollout
-// keeps no history ring (its last two moves start from the root's).
-__global__ void k_rollout_flat(const RootState* roots, int P, int K, int depth, uint32_t k0, uint32_t k1,
-                               const uint32_t* stream_ids, const uint8_t* types_in, Rules Rl, int32_t* tallies)
+// keeps no history ring (its last two moves start from the root's); its
+// chase store is the team's slot of pi_scratch.
+__global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_rollout_flat(const RootState* roots, int P, int K, int depth, uint32_t k0, uint32_t k1,
+                               const uint32_t* stream_ids, const uint8_t* types_in, Rules Rl, int32_t* tallies,
+                               uint64_t* pi_scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<kFlatLanes> T;
-    FlatSmem* S = reinterpret_cast<FlatSmem*>(smem) + threadIdx.x / kFlatLanes;
-    const long long u = (long long)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes;
-    if (u >= (long long)P * K) return;
-    const int p = (int)(u / K), k = (int)(u - (long long)p * K);
-    const RootState* R = roots + p;
-    if (R->bad) return;
-    const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
-    const uint8_t* t = types_in ? types_in + ((size_t)p * K + k) * 40 : nullptr;
-    const int out = rollout_one(&S->g, S->types, S->pi, (uint16_t*)nullptr, T, R, &R->plan, t, depth, k0, k1, stream,
-                                (uint32_t)k, Rl);
-    if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + out], 1);
+    const int team = threadIdx.x / kFlatLanes;
+    FlatSmem* S = reinterpret_cast<FlatSmem*>(smem) + team;
+    uint64_t* pi = pi_scratch + ((size_t)blockIdx.x * kFlatTeams + team) * kPiWords;
+    const long long units = (long long)P * K;
+    const long long stride = (long long)gridDim.x * kFlatTeams;
+    for (long long u = (long long)blockIdx.x * kFlatTeams + team; u < units; u += stride) {
+        const int p = (int)(u / K), k = (int)(u - (long long)p * K);
+        const RootState* R = roots + p;
+        if (R->bad) continue;
+        const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
+        const uint8_t* t = types_in ? types_in + ((size_t)p * K + k) * 40 : nullptr;
+        const int out = rollout_one(&S->g, S->types, pi, (uint16_t*)nullptr, T, R, &R->plan, t, depth, k0, k1,
+                                    stream, (uint32_t)k, Rl);
+        if (T.leader()) atomicAdd(&tallies[4 * (size_t)p + out], 1);
+        T.sync();
+    }
+}
+
+// Resident blocks per SM of the rollout kernels (both share the shape).
+int flat_blocks_per_sm()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout_flat, 32 * kFlatWarps,
+                                                          kFlatTeams * sizeof(FlatSmem)) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        cached[dev] = occ;
+    }
+    return cached[dev];
 }
 
 // ----------------------------------------------------------------- st_search
@@ -199,13 +227,14 @@ __global__ void __launch_bounds__(kOffsetThreads) k_search_offsets(const int32_t
 // One (position, move j, sample s) unit per 8-lane team, unit u of position
 // p being offs[p] + j*S + s; consecutive teams share a position and mostly a
 // move.  Grid-stride over the units.
-__global__ void k_search_rollouts(const RootState* roots, const long long* offs, int P, int S, int depth, uint32_t k0,
+__global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_search_rollouts(const RootState* roots, const long long* offs, int P, int S, int depth, uint32_t k0,
                                   uint32_t k1, const uint32_t* stream_ids, const int16_t* actions, Rules Rl,
-                                  int32_t* tallies)
+                                  int32_t* tallies, uint64_t* pi_scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<kFlatLanes> T;
     FlatSmem* F = reinterpret_cast<FlatSmem*>(smem) + threadIdx.x / kFlatLanes;
+    uint64_t* pi = pi_scratch + ((size_t)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes) * kPiWords;
     const long long total = offs[P];
     const long long stride = (long long)gridDim.x * kFlatTeams;
     for (long long u = (long long)blockIdx.x * kFlatTeams + threadIdx.x / kFlatLanes; u < total; u += stride) {
@@ -221,7 +250,7 @@ __global__ void k_search_rollouts(const RootState* roots, const long long* offs,
         const RootState* R = roots + p;
         const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
         const int first = actions[(size_t)p * kSearchMoves + j];
-        const int out = search_rollout(&F->g, F->types, F->pi, T, R, first, depth, k0, k1, stream, (uint32_t)r,
+        const int out = search_rollout(&F->g, F->types, pi, T, R, first, depth, k0, k1, stream, (uint32_t)r,
                                        (uint32_t)s, Rl);
         if (T.leader()) atomicAdd(&tallies[((size_t)p * kSearchMoves + j) * 4 + out], 1);
         T.sync();
@@ -368,13 +397,20 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
         k_roots<<<rb, 32 * kRootWarps, kRootWarps * sizeof(RolloutSmem), s>>>(pos, P, roots, item_status);
         err = cudaGetLastError();
     }
+    uint64_t* pi_scratch = nullptr;
     if (err == cudaSuccess && K > 0) {
         const long long units = (long long)P * K;
-        const long long fb = (units + kFlatTeams - 1) / kFlatTeams;
-        k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
-            roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, types, r, tallies);
-        err = cudaGetLastError();
+        const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams,
+                                      (long long)sm_count() * flat_blocks_per_sm());
+        err = cudaMallocAsync(&pi_scratch, (size_t)fb * kFlatTeams * kPiWords * sizeof(uint64_t), s);
+        if (err == cudaSuccess) {
+            k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
+                roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, types, r, tallies,
+                pi_scratch);
+            err = cudaGetLastError();
+        }
     }
+    if (pi_scratch) cudaFreeAsync(pi_scratch, s);
     cudaFreeAsync(roots, s);
     if (err != cudaSuccess) {
         stg::set_error("st_rollout: launch failed: %s", cudaGetErrorString(err));
@@ -419,10 +455,16 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
         if (err == cudaSuccess) {
             // at most 244 moves per position; grid-stride beyond 2^24 blocks
             const long long units = (long long)P * 244 * S;
-            const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams, 1LL << 24);
-            k_search_rollouts<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
-                roots, offs, P, S, depth, k0, k1, stream_ids, actions, r, tallies);
-            err = cudaGetLastError();
+            const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams,
+                                          (long long)sm_count() * flat_blocks_per_sm());
+            uint64_t* pi_scratch = nullptr;
+            err = cudaMallocAsync(&pi_scratch, (size_t)fb * kFlatTeams * kPiWords * sizeof(uint64_t), s);
+            if (err == cudaSuccess) {
+                k_search_rollouts<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
+                    roots, offs, P, S, depth, k0, k1, stream_ids, actions, r, tallies, pi_scratch);
+                err = cudaGetLastError();
+                cudaFreeAsync(pi_scratch, s);
+            }
         }
     }
     if (err == cudaSuccess) {
