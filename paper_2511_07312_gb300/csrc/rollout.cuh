@@ -215,17 +215,19 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
 }
 
 // Team: one rollout of the per-move search (App. E "Search", step 2) from
-// root R: belief sample `s` of R's plan, the searcher's move `first` (legal
+// root R: belief sample `s` of R's plan (given in `types`, or drawn), the
+// searcher's move `first` (legal
 // at the root, whatever the sample), then up to depth-1 plies of the rollout
 // policy, ply d drawing from Philox at counter (stream, c1, d, 5<<24) with
 // c1 = j*S+s.
 // No history ring is kept.  Returns the tally slot as rollout_one does.
 template <int L>
 __device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uint64_t* pi, const Team<L>& T,
-                                              const RootState* R, int first, int depth, uint32_t k0, uint32_t k1,
-                                              uint32_t stream, uint32_t c1, uint32_t s, const Rules& Rl)
+                                              const RootState* R, const uint8_t* types, int first, int depth,
+                                              uint32_t k0, uint32_t k1, uint32_t stream, uint32_t c1, uint32_t s,
+                                              const Rules& Rl)
 {
-    begin_rollout(G, types_s, pi, (uint16_t*)nullptr, T, R, &R->plan, (const uint8_t*)nullptr, k0, k1, stream, s);
+    begin_rollout(G, types_s, pi, (uint16_t*)nullptr, T, R, &R->plan, types, k0, k1, stream, s);
     const int searcher = G->c.ply & 1;
     int code = 0, winner = -1, n = 0;
     select_apply(G, T, first, 0u, (uint16_t*)nullptr, pi);

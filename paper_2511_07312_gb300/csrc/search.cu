@@ -83,6 +83,34 @@ __global__ void k_roots(const st_position* pos, int P, RootState* roots, uint8_t
     if (lane_id() == 0 && status) status[p] = roots[p].bad ? 1 : 0;
 }
 
+// Thread per (position, sample): sample k of position p's plan into
+// types[p*K + k][40] (App. E step 1), so that rollout teams only read their
+// sample.  Consecutive threads share a position, whose plan comes from L1.
+__global__ void k_draw_samples(const RootState* roots, int P, int K, uint32_t k0, uint32_t k1,
+                               const uint32_t* stream_ids, uint8_t* types)
+{
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= (long long)P * K) return;
+    const int p = (int)(u / K), k = (int)(u - (long long)p * K);
+    const RootState* R = roots + p;
+    if (R->bad) return;
+    const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
+    uint8_t t[40];
+    draw_sample(&R->plan, k0, k1, stream, (uint32_t)k, t);
+    uint2* o = reinterpret_cast<uint2*>(types + (size_t)u * 40);
+    for (int i = 0; i < 5; ++i) {
+        const uint8_t* b = t + 8 * i;
+        o[i] = make_uint2((uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) | ((uint32_t)b[3] << 24),
+                          (uint32_t)b[4] | ((uint32_t)b[5] << 8) | ((uint32_t)b[6] << 16) | ((uint32_t)b[7] << 24));
+    }
+}
+
+// Samples are drawn ahead of the rollouts for calls of at least this many
+// rollouts (below it the extra launch and allocation cost more than the
+// draws they save) while they fit this many bytes.
+constexpr long long kDrawAheadMinUnits = 16384;
+constexpr size_t kDrawAheadBytes = (size_t)1 << 30;
+
 // One (position, sample) unit per 8-lane team at a time, grid-stride over
 // the units with a grid of resident blocks; consecutive teams of a block
 // share a position, so its root and plan come mostly from L1.  A rollout
@@ -229,7 +257,7 @@ __global__ void __launch_bounds__(kOffsetThreads) k_search_offsets(const int32_t
 // move.  Grid-stride over the units.
 __global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_search_rollouts(const RootState* roots, const long long* offs, int P, int S, int depth, uint32_t k0,
                                   uint32_t k1, const uint32_t* stream_ids, const int16_t* actions, Rules Rl,
-                                  int32_t* tallies, uint64_t* pi_scratch)
+                                  int32_t* tallies, uint64_t* pi_scratch, const uint8_t* types)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<kFlatLanes> T;
@@ -250,7 +278,8 @@ __global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_search_roll
         const RootState* R = roots + p;
         const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
         const int first = actions[(size_t)p * kSearchMoves + j];
-        const int out = search_rollout(&F->g, F->types, pi, T, R, first, depth, k0, k1, stream, (uint32_t)r,
+        const uint8_t* ty = types ? types + ((size_t)p * S + s) * 40 : nullptr;
+        const int out = search_rollout(&F->g, F->types, pi, T, R, ty, first, depth, k0, k1, stream, (uint32_t)r,
                                        (uint32_t)s, Rl);
         if (T.leader()) atomicAdd(&tallies[((size_t)p * kSearchMoves + j) * 4 + out], 1);
         T.sync();
@@ -398,18 +427,30 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
         err = cudaGetLastError();
     }
     uint64_t* pi_scratch = nullptr;
+    uint8_t* drawn = nullptr;
     if (err == cudaSuccess && K > 0) {
         const long long units = (long long)P * K;
         const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams,
                                       (long long)sm_count() * flat_blocks_per_sm());
         err = cudaMallocAsync(&pi_scratch, (size_t)fb * kFlatTeams * kPiWords * sizeof(uint64_t), s);
+        // without given samples, draw them ahead in one wide launch when they fit
+        const uint8_t* ty = types;
+        if (err == cudaSuccess && !types && units >= kDrawAheadMinUnits && (size_t)units * 40 <= kDrawAheadBytes &&
+            cudaMallocAsync(&drawn, (size_t)units * 40, s) == cudaSuccess) {
+            k_draw_samples<<<(unsigned)((units + 127) / 128), 128, 0, s>>>(roots, P, K, (uint32_t)seed,
+                                                                          (uint32_t)(seed >> 32), stream_ids, drawn);
+            err = cudaGetLastError();
+            ty = drawn;
+        }
+        cudaGetLastError();   // a failed draw-ahead allocation leaves the in-kernel draw
         if (err == cudaSuccess) {
             k_rollout_flat<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
-                roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, types, r, tallies,
+                roots, P, K, depth, (uint32_t)seed, (uint32_t)(seed >> 32), stream_ids, ty, r, tallies,
                 pi_scratch);
             err = cudaGetLastError();
         }
     }
+    if (drawn) cudaFreeAsync(drawn, s);
     if (pi_scratch) cudaFreeAsync(pi_scratch, s);
     cudaFreeAsync(roots, s);
     if (err != cudaSuccess) {
@@ -458,13 +499,24 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
             const long long fb = std::min((units + kFlatTeams - 1) / kFlatTeams,
                                           (long long)sm_count() * flat_blocks_per_sm());
             uint64_t* pi_scratch = nullptr;
+            uint8_t* drawn = nullptr;
             err = cudaMallocAsync(&pi_scratch, (size_t)fb * kFlatTeams * kPiWords * sizeof(uint64_t), s);
+            // configuration s of position p serves every move: drawn once, ahead
+            const long long samples = (long long)P * S;
+            if (err == cudaSuccess && (size_t)samples * 40 <= kDrawAheadBytes &&
+                cudaMallocAsync(&drawn, (size_t)samples * 40, s) == cudaSuccess) {
+                k_draw_samples<<<(unsigned)((samples + 127) / 128), 128, 0, s>>>(roots, P, S, k0, k1, stream_ids,
+                                                                                drawn);
+                err = cudaGetLastError();
+            }
+            cudaGetLastError();   // a failed draw-ahead allocation leaves the in-kernel draw
             if (err == cudaSuccess) {
                 k_search_rollouts<<<(unsigned)fb, 32 * kFlatWarps, kFlatTeams * sizeof(FlatSmem), s>>>(
-                    roots, offs, P, S, depth, k0, k1, stream_ids, actions, r, tallies, pi_scratch);
+                    roots, offs, P, S, depth, k0, k1, stream_ids, actions, r, tallies, pi_scratch, drawn);
                 err = cudaGetLastError();
-                cudaFreeAsync(pi_scratch, s);
             }
+            if (drawn) cudaFreeAsync(drawn, s);
+            if (pi_scratch) cudaFreeAsync(pi_scratch, s);
         }
     }
     if (err == cudaSuccess) {
