@@ -577,8 +577,23 @@ def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0):
             lat2[i] = time.perf_counter() - (t0 + arrive[i])
     span2 = time.perf_counter() - t0
     plain = dict(pct(lat2), requests_per_s=n / span2, samples_per_s=float(Ks.sum()) / span2)
+    # capacity: a burst of 2,000 heavy requests (K ~ U{1024..4096}, depth
+    # 64) submitted at once, timed from the first submit to the last completion
+    nb = 2000
+    Kb = rng.integers(1024, 4097, nb)
+    srv = st.Server(device=dev.index, max_requests=512, sample_slots=1 << 18, max_batches=8)
+    tb = [srv.submit(positions[which[i]], int(Kb[i]), 64, seed, i) for i in range(nb)]
+    first, last = None, 0
+    for t in tb:
+        _, (sub, adm, done) = srv.wait(t, 120000)
+        first = sub if first is None else min(first, sub)
+        last = max(last, done)
+    srv.close()
+    spanb = (last - first) / 1e9
+    burst = {"requests": nb, "K_range": [1024, 4096], "depth": 64, "requests_per_s": nb / spanb,
+             "samples_per_s": float(Kb.sum()) / spanb, "ms": spanb * 1e3}
     return {"requests": n, "arrival_rate_per_s": rate, "K_range": [16, 1024], "depth_range": [8, 64],
-            "served": served, "plain_per_request": plain}
+            "served": served, "plain_per_request": plain, "burst_capacity": burst}
 
 
 if __name__ == "__main__":

@@ -87,54 +87,63 @@ __global__ void k_serve_roots(const BatchEntry* entries, int n, const Staged* st
 }
 
 constexpr int kServeLanes = 8;   // one rollout per 8-lane team
+constexpr int kServeWarps = 2;
+constexpr int kServeTeams = 32 * kServeWarps / kServeLanes;   // rollouts per block
+constexpr int kServeMinBlocks = 12;                           // resident blocks per SM the registers allow
 
-__global__ void k_serve_rollouts(const BatchEntry* entries, int n, long long units, const RootState* roots,
-                                 ReqDesc* descs, SampleRec* samples, Rules Rl, volatile int32_t* host_tallies,
-                                 volatile uint32_t* host_done)
+// One (request, sample) unit per 8-lane team at a time, striding over the
+// batch's units with at most a resident grid; the team's chase store is its
+// slot of this launch slot's scratch (the newest four entries stay cached
+// in shared memory).
+__global__ void __launch_bounds__(32 * kServeWarps, kServeMinBlocks)
+k_serve_rollouts(const BatchEntry* entries, int n, long long units, const RootState* roots, ReqDesc* descs,
+                 SampleRec* samples, Rules Rl, volatile int32_t* host_tallies, volatile uint32_t* host_done,
+                 uint64_t* pi_scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<kServeLanes> T;
-    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + threadIdx.x / kServeLanes;
-    const long long u = (long long)blockIdx.x * (blockDim.x / kServeLanes) + threadIdx.x / kServeLanes;
-    if (u >= units) return;
-    // the batch entry holding unit u
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (entries[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
-    }
-    const int slot = entries[lo].slot;
-    const RootState* R = roots + slot;
-    ReqDesc* d = descs + slot;
-    const int k = (int)(u - entries[lo].unit_begin);
-    const bool bad = R->bad != 0;
+    const int team = threadIdx.x / kServeLanes;
+    FlatSmem* S = reinterpret_cast<FlatSmem*>(smem) + team;
+    uint64_t* pi = pi_scratch + ((size_t)blockIdx.x * kServeTeams + team) * kPiWords;
     const int lane = T.tl;
-    if (!bad) {
-        const int outcome = rollout_one(&S->g, S->types, S->pi, (uint16_t*)nullptr, T, R, &R->plan, nullptr, d->depth,
-                                        d->k0, d->k1, d->stream, (uint32_t)k, Rl);
-        SampleRec* rec = samples + d->sample_base + k;
-        for (int i = lane; i < 10; i += kServeLanes)
-            reinterpret_cast<uint32_t*>(rec->types)[i] = reinterpret_cast<const uint32_t*>(S->types)[i];
+    const long long stride = (long long)gridDim.x * kServeTeams;
+    for (long long u = (long long)blockIdx.x * kServeTeams + team; u < units; u += stride) {
+        // the batch entry holding unit u
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (entries[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const int slot = entries[lo].slot;
+        const RootState* R = roots + slot;
+        ReqDesc* d = descs + slot;
+        const int k = (int)(u - entries[lo].unit_begin);
+        const bool bad = R->bad != 0;
+        if (!bad) {
+            const int outcome = rollout_one(&S->g, S->types, pi, (uint16_t*)nullptr, T, R, &R->plan, nullptr,
+                                            d->depth, d->k0, d->k1, d->stream, (uint32_t)k, Rl);
+            SampleRec* rec = samples + d->sample_base + k;
+            for (int i = lane; i < 10; i += kServeLanes)
+                reinterpret_cast<uint32_t*>(rec->types)[i] = reinterpret_cast<const uint32_t*>(S->types)[i];
+            if (lane == 0) {
+                rec->outcome = (int8_t)outcome;
+                atomicAdd(&d->tallies[outcome], 1);
+            }
+        }
+        // every unit of the request counts down, so the slot is reused only
+        // after all of its units are done; the last one publishes the result
         if (lane == 0) {
-            rec->outcome = (int8_t)outcome;
-            atomicAdd(&d->tallies[outcome], 1);
-        }
-    }
-    // every unit of the request counts down, so the slot is reused only
-    // after all of its warps are gone; the last one publishes the result
-    if (lane == 0) {
-        __threadfence();
-        if (atomicSub(&d->remaining, 1) == 1) {
             __threadfence();
-            for (int j = 0; j < 4; ++j) host_tallies[4 * slot + j] = bad ? -1 : atomicAdd(&d->tallies[j], 0);
-            __threadfence_system();
-            host_done[slot] = d->seq;
+            if (atomicSub(&d->remaining, 1) == 1) {
+                __threadfence();
+                for (int j = 0; j < 4; ++j) host_tallies[4 * slot + j] = bad ? -1 : atomicAdd(&d->tallies[j], 0);
+                __threadfence_system();
+                host_done[slot] = d->seq;
+            }
         }
+        T.sync();
     }
 }
-
-constexpr int kServeWarps = 2;
-constexpr int kServeTeams = 32 * kServeWarps / kServeLanes;   // rollouts per block
 
 uint64_t now_ns()
 {
@@ -171,6 +180,8 @@ struct st_server {
     uint32_t* host_done = nullptr;           // mapped [max_requests]
     int32_t* host_tallies_dev = nullptr;
     uint32_t* host_done_dev = nullptr;
+    uint64_t* pi_scratch = nullptr;          // [max_batches][max_grid * kServeTeams][kPiWords]
+    int max_grid = 0;                        // resident blocks of the rollout kernel
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> batch_done;
     std::vector<int> stream_busy;
@@ -323,10 +334,10 @@ bool schedule_once(st_server* s, std::unique_lock<std::mutex>& lk)
         err = cudaGetLastError();
     }
     if (err == cudaSuccess && units > 0) {
-        const long long fb = (units + kServeTeams - 1) / kServeTeams;
-        k_serve_rollouts<<<(unsigned)fb, 32 * kServeWarps, kServeTeams * sizeof(RolloutSmem), str>>>(
+        const long long fb = std::min((units + kServeTeams - 1) / kServeTeams, (long long)s->max_grid);
+        k_serve_rollouts<<<(unsigned)fb, 32 * kServeWarps, kServeTeams * sizeof(FlatSmem), str>>>(
             s->entries_dev + (size_t)b * R, n, units, s->roots, s->descs, s->samples, s->rules, s->host_tallies_dev,
-            s->host_done_dev);
+            s->host_done_dev, s->pi_scratch + (size_t)b * s->max_grid * kServeTeams * kPiWords);
         err = cudaGetLastError();
     }
     if (err == cudaSuccess) err = cudaEventRecord(s->batch_done[b], str);
@@ -390,6 +401,14 @@ extern "C" st_status st_serve_create(const st_serve_config* cfg, st_server** out
     if (err == cudaSuccess) err = cudaMalloc(&s->samples, (size_t)cfg->sample_slots * sizeof(SampleRec));
     if (err == cudaSuccess) err = cudaMalloc(&s->staged_dev, (size_t)R * sizeof(Staged));
     if (err == cudaSuccess) err = cudaMalloc(&s->entries_dev, (size_t)B * R * sizeof(BatchEntry));
+    if (err == cudaSuccess) {
+        int occ = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_rollouts, 32 * kServeWarps,
+                                                            kServeTeams * sizeof(FlatSmem));
+        s->max_grid = std::max(1, occ) * sm_count();
+    }
+    if (err == cudaSuccess)
+        err = cudaMalloc(&s->pi_scratch, (size_t)B * s->max_grid * kServeTeams * kPiWords * sizeof(uint64_t));
     if (err == cudaSuccess) err = cudaHostAlloc(&s->staged_host, (size_t)R * sizeof(Staged), cudaHostAllocDefault);
     if (err == cudaSuccess) err = cudaHostAlloc(&s->entries_host, (size_t)B * R * sizeof(BatchEntry), cudaHostAllocDefault);
     if (err == cudaSuccess)
@@ -523,6 +542,7 @@ extern "C" st_status st_serve_destroy(st_server* s)
         cudaEventDestroy(s->batch_done[b]);
     }
     cudaFree(s->roots); cudaFree(s->descs); cudaFree(s->samples); cudaFree(s->staged_dev); cudaFree(s->entries_dev);
+    cudaFree(s->pi_scratch);
     cudaFreeHost(s->staged_host); cudaFreeHost(s->entries_host);
     cudaFreeHost(s->host_tallies); cudaFreeHost(s->host_done);
     delete s;
