@@ -192,10 +192,16 @@ struct st_server {
     std::unordered_map<uint64_t, Ticket> tickets;
     std::vector<uint64_t> slot_ticket;       // ticket running in each request slot (0 free)
     std::map<int, int> free_ranges;          // sample records: begin -> length
-    uint64_t next_ticket = 1;
     uint32_t next_seq = 1;
     bool stop = false;
-    bool failed = false;
+    std::atomic<bool> failed{false};
+    // submissions land here under their own lock, so a submit never waits
+    // for a scheduler pass; the scheduler moves them into `tickets`/`queue`
+    std::mutex in_mu;
+    std::deque<std::pair<uint64_t, Ticket>> incoming;
+    std::atomic<uint64_t> next_ticket{1};
+    std::atomic<int64_t> n_incoming{0};
+    std::atomic<bool> idle{false};           // the scheduler is (about to be) blocked on cv
     std::string fail_msg;
     st_serve_stats stats{};
     std::thread worker;
@@ -240,6 +246,17 @@ void give_range(st_server* s, int b, int k)
 bool schedule_once(st_server* s, std::unique_lock<std::mutex>& lk)
 {
     const int R = s->cfg.max_requests;
+    // take in the new submissions, in submission order
+    if (s->n_incoming.load() > 0) {
+        std::lock_guard<std::mutex> g(s->in_mu);
+        for (auto& kv : s->incoming) {
+            s->tickets.emplace(kv.first, kv.second);
+            s->queue.push_back(kv.first);
+            s->stats.submitted += 1;
+        }
+        s->n_incoming.fetch_sub((int64_t)s->incoming.size());
+        s->incoming.clear();
+    }
     // retire requests whose completion word arrived
     for (int slot = 0; slot < R; ++slot) {
         const uint64_t t = s->slot_ticket[slot];
@@ -359,6 +376,12 @@ void worker_main(st_server* s)
         const bool busy = schedule_once(s, lk);
         if (s->failed) {
             // fail every waiting and running request; nothing more is launched
+            {
+                std::lock_guard<std::mutex> g(s->in_mu);
+                for (auto& kv : s->incoming) s->tickets.emplace(kv.first, kv.second);
+                s->n_incoming.fetch_sub((int64_t)s->incoming.size());
+                s->incoming.clear();
+            }
             for (auto& kv : s->tickets)
                 if (kv.second.state < 2) { kv.second.state = 3; kv.second.status = ST_ERR_CUDA; }
             s->queue.clear();
@@ -371,7 +394,10 @@ void worker_main(st_server* s)
             std::this_thread::yield();
             lk.lock();
         } else {
-            s->cv.wait_for(lk, std::chrono::milliseconds(5), [s] { return s->stop || !s->queue.empty(); });
+            s->idle.store(true);
+            s->cv.wait_for(lk, std::chrono::milliseconds(5),
+                           [s] { return s->stop || !s->queue.empty() || s->n_incoming.load() > 0; });
+            s->idle.store(false);
         }
     }
 }
@@ -444,30 +470,49 @@ extern "C" st_status st_serve_submit(st_server* s, const st_request* req, uint64
     ST_CHECK_ARG(req->K >= 0 && req->K <= s->cfg.sample_slots, "st_serve_submit: K %d outside 0..%d", req->K,
                  s->cfg.sample_slots);
     ST_CHECK_ARG(req->depth >= 0, "st_serve_submit: negative depth");
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->failed) {
+    if (s->failed.load()) {
+        std::lock_guard<std::mutex> lk(s->mu);
         stg::set_error("st_serve_submit: server failed: %s", s->fail_msg.c_str());
         return ST_ERR_CUDA;
     }
-    if (s->queue.size() >= 1u << 20) {
-        stg::set_error("st_serve_submit: queue full");
-        return ST_ERR_BUSY;
-    }
-    const uint64_t t = s->next_ticket++;
-    Ticket& tk = s->tickets[t];
+    Ticket tk;
     tk.req = *req;
     tk.submit_ns = now_ns();
-    s->queue.push_back(t);
-    s->stats.submitted += 1;
+    uint64_t t = 0;
+    {
+        std::lock_guard<std::mutex> g(s->in_mu);
+        if (s->incoming.size() >= 1u << 20) {
+            stg::set_error("st_serve_submit: queue full");
+            return ST_ERR_BUSY;
+        }
+        t = s->next_ticket.fetch_add(1);
+        s->incoming.emplace_back(t, tk);
+        s->n_incoming.fetch_add(1);
+    }
     *ticket = t;
-    s->cv.notify_all();
+    // wake the scheduler only if it sleeps; taking mu once orders this
+    // submission before its next look at n_incoming
+    if (s->idle.load()) {
+        { std::lock_guard<std::mutex> lk(s->mu); }
+        s->cv.notify_all();
+    }
     return ST_OK;
+}
+
+// Is the ticket submitted but not yet taken in by the scheduler?
+static bool in_incoming(st_server* s, uint64_t ticket)
+{
+    std::lock_guard<std::mutex> g(s->in_mu);
+    for (const auto& kv : s->incoming)
+        if (kv.first == ticket) return true;
+    return false;
 }
 
 static st_status take_result(st_server* s, uint64_t ticket, int32_t* tallies, st_timing* timing)
 {
     auto it = s->tickets.find(ticket);
     if (it == s->tickets.end()) {
+        if (in_incoming(s, ticket)) return ST_ERR_NOT_READY;
         stg::set_error("st_serve: unknown ticket %llu", (unsigned long long)ticket);
         return ST_ERR_INVALID;
     }
@@ -501,13 +546,18 @@ extern "C" st_status st_serve_wait(st_server* s, uint64_t ticket, int32_t timeou
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
     for (;;) {
         auto it = s->tickets.find(ticket);
-        if (it == s->tickets.end()) {
+        if (it == s->tickets.end() && !in_incoming(s, ticket)) {
             stg::set_error("st_serve_wait: unknown ticket %llu", (unsigned long long)ticket);
             return ST_ERR_INVALID;
         }
-        if (it->second.state >= 2) return take_result(s, ticket, tallies, timing);
+        if (it != s->tickets.end() && it->second.state >= 2) return take_result(s, ticket, tallies, timing);
+        if (it == s->tickets.end() && s->failed.load()) {
+            stg::set_error("st_serve_wait: server failed: %s", s->fail_msg.c_str());
+            return ST_ERR_CUDA;
+        }
         if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
-            if (s->tickets[ticket].state >= 2) return take_result(s, ticket, tallies, timing);
+            auto jt = s->tickets.find(ticket);
+            if (jt != s->tickets.end() && jt->second.state >= 2) return take_result(s, ticket, tallies, timing);
             stg::set_error("st_serve_wait: ticket %llu not done after %d ms", (unsigned long long)ticket, timeout_ms);
             return ST_ERR_TIMEOUT;
         }
@@ -519,7 +569,7 @@ extern "C" st_status st_serve_get_stats(st_server* s, st_serve_stats* out)
     ST_CHECK_ARG(s && out, "st_serve_get_stats: null argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
-    out->queued = (int64_t)s->queue.size();
+    out->queued = (int64_t)s->queue.size() + s->n_incoming.load();
     int64_t running = 0;
     for (uint64_t t : s->slot_ticket) running += t != 0;
     out->running = running;
