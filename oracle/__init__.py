@@ -66,7 +66,7 @@ def _declare(L):
     L.orx_u8_ratio.argtypes = [u32, u32]
     L.orx_u8_ratio.restype = ctypes.c_uint8
     L.orx_ratio_batch.argtypes = [vp, vp, i32, vp, vp]
-    L.orx_search.argtypes = [vp, i32, i32, i32, u64, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
+    L.orx_search.argtypes = [vp, i32, i32, i32, u64, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
                              vp, vp, vp, vp, vp, vp, vp]
 
 
@@ -303,7 +303,7 @@ SEARCH_ALPHA, SEARCH_BETA = 0.002, 0.02   # App. E, Tab. search-hyper
 
 
 def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALPHA, beta=SEARCH_BETA, k=100,
-           cap=1000, flags=ALL_RULES):
+           cap=1000, flags=ALL_RULES, q_values=None):
     """App. E search: per-candidate-move rollouts (S configurations, depth
     plies with the forced first move) and the tabular MMD update.  Returns a
     dict of n_moves [P], actions [P, 256], tallies [P, 256, 4], q and pi
@@ -313,10 +313,11 @@ def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALP
     M = SEARCH_MAX_MOVES
     sid = None if stream_ids is None else _c(stream_ids, np.uint32)
     pt = None if pi_theta is None else _c(pi_theta, np.float32)
+    qv = None if q_values is None else _c(q_values, np.float32)
     out = dict(n_moves=np.zeros(P, np.int32), actions=np.zeros((P, M), np.int16),
                tallies=np.zeros((P, M, 4), np.int32), q=np.zeros((P, M)), pi=np.zeros((P, M)),
                chosen=np.zeros(P, np.int16), status=np.zeros(P, np.uint8))
-    r = lib().orx_search(_p(pos), P, S, depth, seed, _p(sid), _p(pt), float(alpha), float(beta), k, cap, flags,
+    r = lib().orx_search(_p(pos), P, S, depth, seed, _p(sid), _p(pt), _p(qv), float(alpha), float(beta), k, cap, flags,
                          _p(out["n_moves"]), _p(out["actions"]), _p(out["tallies"]), _p(out["q"]), _p(out["pi"]),
                          _p(out["chosen"]), _p(out["status"]))
     if r != 0:

@@ -136,7 +136,7 @@ void or_belief_sample_one(const or_game* g, uint64_t seed, uint32_t stream, uint
 /* App. E search (search.c): per-candidate-move rollouts and the tabular
  * magnetic-mirror-descent update; outputs [P][OR_SEARCH_MAX_MOVES](x4). */
 int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const uint32_t* stream_ids,
-               const float* pi_theta, double alpha, double beta, int k, int cap, int flags,
+               const float* pi_theta, const float* q_given, double alpha, double beta, int k, int cap, int flags,
                int32_t* n_moves, int16_t* actions, int32_t* tallies, double* q, double* pi, int16_t* chosen,
                uint8_t* status);
 

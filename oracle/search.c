@@ -18,7 +18,9 @@
  *  R17 Step 3: a rollout's value is +1, -1, 0 for a win, loss or draw of the
  *      searcher and 0 when it is unfinished after depth plies (there is no
  *      value network); q(j) is the mean over the S rollouts of move j (0
- *      when S = 0).
+ *      when S = 0).  When the caller gives values by action (a value
+ *      network's estimates standing in for the rollouts), q(j) is the given
+ *      value of move j as a double and no rollout is run.
  *  R18 Step 4: rho (Tab. notation: the magnet policy picks a piece to move
  *      uniformly, then one of its moves uniformly) gives move j the
  *      probability 1 / (pieces with a legal move * legal moves of move j's
@@ -58,7 +60,7 @@ static int random_move(const or_game* g, const uint32_t key[2], uint32_t stream,
 }
 
 int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const uint32_t* stream_ids,
-               const float* pi_theta, double alpha, double beta, int k, int cap, int flags,
+               const float* pi_theta, const float* q_given, double alpha, double beta, int k, int cap, int flags,
                int32_t* n_moves, int16_t* actions, int32_t* tallies, double* q, double* pi, int16_t* chosen,
                uint8_t* status)
 {
@@ -93,7 +95,7 @@ int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const
         for (int j = 0; j < n; ++j) act[j] = (int16_t)mv[j];
         if (n == 0) continue;
         /* step 1 and 2: configurations and rollouts with a forced first move */
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < S && !q_given; ++s) {
             uint8_t types[40];
             or_belief_sample_one(root, seed, stream, (uint32_t)s, types);
             for (int j = 0; j < n; ++j) {
@@ -112,8 +114,10 @@ int orx_search(const uint8_t* pos, int P, int S, int depth, uint64_t seed, const
             }
         }
         /* step 3: mean values */
-        for (int j = 0; j < n; ++j)
-            qp[j] = S > 0 ? (double)(tl[4 * j] - tl[4 * j + 1]) / (double)S : 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (q_given) qp[j] = (double)q_given[(size_t)p * 10000 + mv[j]];
+            else qp[j] = S > 0 ? (double)(tl[4 * j] - tl[4 * j + 1]) / (double)S : 0.0;
+        }
         /* step 4: magnet policy, the update, the sampled move */
         int per_from[OR_NSQ];
         memset(per_from, 0, sizeof(per_from));

@@ -178,3 +178,30 @@ def test_zero_prior_moves_and_degenerate_inputs():
     bad = pos.copy()
     bad[0] = 99
     assert oracle.search(bad, 3, 4, 1)["status"][0] == 1
+
+
+def test_given_values_replace_the_rollouts():
+    # step 3 with a value estimate per move given by action (the value
+    # network's role): no rollout runs, q is the given value, and the update
+    # is still the maximiser of the regularised objective
+    pos = _pos_two_pieces()
+    acts = sorted([action("e4", t) for t in ("e3", "d4", "f4", "e5")] + [action("a1", "a2"), action("a1", "b1")])
+    qv = np.zeros((1, 10000), np.float32)
+    vals = np.array([0.01, -0.02, 0.0, 0.03, -0.005, 0.015], np.float32)
+    qv[0, acts] = vals
+    qv[0, 9999] = 5.0                       # an illegal action's entry is never read
+    r = oracle.search(pos, 8, 20, 3, q_values=qv)
+    n = r["n_moves"][0]
+    assert n == 6 and (r["tallies"][0] == 0).all()
+    order = r["actions"][0, :n]
+    np.testing.assert_array_equal(r["q"][0, :n], qv[0, order].astype(np.float64))
+    q = r["q"][0, :n]
+    pi = r["pi"][0, :n]
+    rho = np.array([0.25 if a // 100 == 0 else 0.125 for a in order])
+    pt = np.full(n, 1.0 / n)
+    g_ = q - ALPHA * (np.log(pi / rho) + 1) - BETA * (np.log(pi / pt) + 1)
+    assert np.ptp(g_) < 1e-9
+    # the move with the largest value gains the most over the prior
+    best = int(np.argmax(q))
+    assert pi[best] / (rho[best] ** (ALPHA / (ALPHA + BETA)) * pt[best] ** (BETA / (ALPHA + BETA))) == pytest.approx(
+        np.max(pi / (rho ** (ALPHA / (ALPHA + BETA)) * pt ** (BETA / (ALPHA + BETA)))), rel=1e-12)
