@@ -491,9 +491,15 @@ def secondary(st, torch, dev, args):
     # step now - 300 rebuilt by replay
     Nh, Hh = 16384, 1000
     henv = st.Env(Nh, seed=5, device=dev.index)
+    henv.set_launch(4, 0, 1, games_per_warp=4)
     henv.enable_history(Hh)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(henv.stream)
     henv.run(Hh)
+    ev1.record(henv.stream)
     henv.sync()
+    rec_ms = ev0.elapsed_time(ev1)
     th = henv.current_step() - 300
     hp = henv.history_positions(th)
     torch.cuda.synchronize()
@@ -507,6 +513,25 @@ def secondary(st, torch, dev, args):
     rebuilt = int((hp["status"] == 0).sum().item())
     out["history_positions"] = {"slots": Nh, "H": Hh, "step": th, "rebuilt": rebuilt, "ms": ms,
                                 "positions_per_s": rebuilt / (ms / 1000)}
+    # the same env stepping with and without recording (one launch each, first one includes graph capture)
+    henv.enable_history(0)
+    henv.run(Hh)
+    henv.sync()
+    ev0.record(henv.stream)
+    henv.run(Hh)
+    ev1.record(henv.stream)
+    henv.sync()
+    plain_ms = ev0.elapsed_time(ev1)
+    henv.enable_history(Hh)
+    henv.run(Hh)
+    henv.sync()
+    ev0.record(henv.stream)
+    henv.run(Hh)
+    ev1.record(henv.stream)
+    henv.sync()
+    rec_ms = ev0.elapsed_time(ev1)
+    out["history_recording"] = {"slots": Nh, "steps": Hh, "env_steps_per_s_recording": Nh * Hh / (rec_ms / 1000),
+                                "env_steps_per_s_not_recording": Nh * Hh / (plain_ms / 1000)}
     henv.close()
     out["serving"] = serving(st, torch, dev, pos.cpu().numpy(), args)
     return out

@@ -426,7 +426,8 @@ st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* r
  *      configuration s): move j, then up to depth-1 rollout-policy plies,
  *      ply d drawing from Philox at counter (stream, j*S + s, d, 5<<24);
  *   3. q[j] = mean over the S rollouts of +1 win, -1 loss, 0 draw or
- *      unfinished (for the searcher), 0 when S = 0;
+ *      unfinished (for the searcher), 0 when S = 0; or, with q_values given,
+ *      the given value of move j and no rollout (a value network's role);
  *   4. rho[j] = 1 / (pieces with a legal move * legal moves of move j's
  *      piece) (the magnet policy, Tab. notation); pi[j] proportional to
  *      exp((q[j] + alpha ln rho[j] + beta ln pi_theta[j]) / (alpha + beta)),
@@ -439,6 +440,9 @@ st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* r
  *   pi_theta[P][10000] float   move-network probabilities by action (NULL:
  *                              uniform over the legal moves); only legal
  *                              entries are read, a zero excludes the move;
+ *   q_values[P][10000] float   per-move values by action for the searcher
+ *                              (NULL: from the rollouts); only legal entries
+ *                              are read;
  *   n_moves[P] int32           the searcher's legal moves (0: none searched);
  *   actions[P][256] int16      those moves ascending, -1 after the last;
  *   tallies[P][256][4] int32   wins, losses, draws, unfinished per move;
@@ -451,7 +455,8 @@ st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* r
  * device memory.
  */
 st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth, uint64_t seed,
-                    const uint32_t* stream_ids, const float* pi_theta, double alpha, double beta,
+                    const uint32_t* stream_ids, const float* pi_theta, const float* q_values, double alpha,
+                    double beta,
                     const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies, double* q,
                     double* pi, int16_t* chosen, uint8_t* item_status, void* stream);
 

@@ -112,7 +112,7 @@ def _declare(L):
         "st_obs_encode_static": [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.POINTER(st_rules), vp, vp, vp, vp, vp],
         "st_belief_sample": [vp, i32, i32, u64, vp, vp, vp, vp],
         "st_rollout": [vp, i32, i32, i32, u64, vp, vp, ctypes.POINTER(st_rules), vp, vp, vp],
-        "st_search": [vp, i32, i32, i32, u64, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(st_rules),
+        "st_search": [vp, i32, i32, i32, u64, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(st_rules),
                       vp, vp, vp, vp, vp, vp, vp, vp],
         "st_serve_create": [ctypes.POINTER(st_serve_config), ctypes.POINTER(vp)],
         "st_serve_submit": [vp, ctypes.POINTER(st_request), ctypes.POINTER(ctypes.c_uint64)],
@@ -383,11 +383,13 @@ SEARCH_ALPHA, SEARCH_BETA = 0.002, 0.02   # App. E
 
 
 def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALPHA, beta=SEARCH_BETA, k=100,
-           cap=1000, flags=RULES_ALL, stream=None):
+           cap=1000, flags=RULES_ALL, stream=None, q_values=None):
     """Per-candidate-move search with the tabular MMD update (st_search).
 
     pos: [P, 784] uint8 CUDA tensor; pi_theta: optional [P, 10000] float32
-    CUDA tensor of move probabilities by action.  Returns a dict of CUDA
+    CUDA tensor of move probabilities by action; q_values: optional
+    [P, 10000] float32 per-move values by action, used instead of the
+    rollouts.  Returns a dict of CUDA
     tensors: n_moves [P] int32, actions [P, 256] int16, tallies [P, 256, 4]
     int32, q and pi [P, 256] float64, chosen [P] int16, status [P] uint8."""
     P = pos.shape[0]
@@ -403,7 +405,8 @@ def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALP
     }
     r = make_rules(k, cap, flags)
     _check(lib().st_search(_ptr(pos, torch.uint8), P, int(S), int(depth), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                           _ptr(stream_ids, torch.int32), _ptr(pi_theta, torch.float32), float(alpha), float(beta),
+                           _ptr(stream_ids, torch.int32), _ptr(pi_theta, torch.float32),
+                           _ptr(q_values, torch.float32), float(alpha), float(beta),
                            ctypes.byref(r), _ptr(out["n_moves"]), _ptr(out["actions"]), _ptr(out["tallies"]),
                            _ptr(out["q"]), _ptr(out["pi"]), _ptr(out["chosen"]), _ptr(out["status"]),
                            _stream(stream)))

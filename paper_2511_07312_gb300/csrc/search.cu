@@ -293,7 +293,8 @@ constexpr int kPolicyWarps = 4;
 // update is written (no contraction), so only log and exp differ from a
 // correctly rounded evaluation, by at most an ulp or two.
 __global__ void k_search_policy(int P, int S, uint32_t k0, uint32_t k1, const uint32_t* stream_ids,
-                                const float* pi_theta, double alpha, double beta, const int32_t* n_moves,
+                                const float* pi_theta, const float* q_values, double alpha, double beta,
+                                const int32_t* n_moves,
                                 const int16_t* actions, const int32_t* tallies, double* q, double* pi, int16_t* chosen,
                                 uint8_t* status)
 {
@@ -314,10 +315,15 @@ __global__ void k_search_policy(int P, int S, uint32_t k0, uint32_t k1, const ui
     const double ab = __dadd_rn(alpha, beta);
     double zmax = -CUDART_INF;
     for (int j = lane; j < n; j += 32) {
-        const int4 t = reinterpret_cast<const int4*>(tallies + (size_t)p * kSearchMoves * 4)[j];
-        const double qj = S > 0 ? __ddiv_rn((double)(t.x - t.y), (double)S) : 0.0;
-        qp[j] = qj;
         const int a = act[j], f = a / 100;
+        double qj;
+        if (q_values) {
+            qj = (double)q_values[(size_t)p * 10000 + a];
+        } else {
+            const int4 t = reinterpret_cast<const int4*>(tallies + (size_t)p * kSearchMoves * 4)[j];
+            qj = S > 0 ? __ddiv_rn((double)(t.x - t.y), (double)S) : 0.0;
+        }
+        qp[j] = qj;
         int lo = j, hi = j;
         while (lo > 0 && act[lo - 1] / 100 == f) --lo;
         while (hi + 1 < n && act[hi + 1] / 100 == f) ++hi;
@@ -461,7 +467,8 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
 }
 
 extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth, uint64_t seed,
-                               const uint32_t* stream_ids, const float* pi_theta, double alpha, double beta,
+                               const uint32_t* stream_ids, const float* pi_theta, const float* q_values,
+                               double alpha, double beta,
                                const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies,
                                double* q, double* pi, int16_t* chosen, uint8_t* item_status, void* stream)
 {
@@ -490,7 +497,7 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
             pos, P, r, roots, n_moves, actions, tallies, q, pi, chosen, item_status);
         err = cudaGetLastError();
     }
-    if (err == cudaSuccess && S > 0) {
+    if (err == cudaSuccess && S > 0 && !q_values) {
         k_search_offsets<<<1, kOffsetThreads, 0, s>>>(n_moves, P, S, offs);
         err = cudaGetLastError();
         if (err == cudaSuccess) {
@@ -521,7 +528,8 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
     }
     if (err == cudaSuccess) {
         k_search_policy<<<(P + kPolicyWarps - 1) / kPolicyWarps, 32 * kPolicyWarps, 0, s>>>(
-            P, S, k0, k1, stream_ids, pi_theta, alpha, beta, n_moves, actions, tallies, q, pi, chosen, item_status);
+            P, S, k0, k1, stream_ids, pi_theta, q_values, alpha, beta, n_moves, actions, tallies, q, pi, chosen,
+            item_status);
         err = cudaGetLastError();
     }
     if (offs) cudaFreeAsync(offs, s);

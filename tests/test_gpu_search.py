@@ -151,3 +151,21 @@ def test_search_full_size_sampled_positions():
     assert (got["status"].cpu().numpy() == 0).all()
     for p in range(len(pos)):
         assert (t[p, :n[p]].sum(-1) == S).all()
+
+
+def test_search_with_given_values():
+    pos = _positions(49, 4, 3)
+    ref0 = oracle.search(pos, 0, 1, 0)
+    rng = np.random.default_rng(9)
+    qv = rng.uniform(-1, 1, size=(len(pos), 10000)).astype(np.float32)
+    for magnet in (False, True):
+        flags = st.RULES_ALL | (st.ROLLOUT_MAGNET if magnet else 0)
+        got = st.search(torch.from_numpy(pos).cuda(), 5, 30, 17, q_values=torch.from_numpy(qv).cuda(), flags=flags)
+        torch.cuda.synchronize()
+        ref = oracle.search(pos, 5, 30, 17, q_values=qv, flags=flags)
+        _compare(got, ref, 17)
+        assert (got["tallies"].cpu().numpy() == 0).all()
+        for p in range(len(pos)):
+            n = ref0["n_moves"][p]
+            np.testing.assert_array_equal(got["q"].cpu().numpy()[p, :n],
+                                          qv[p, ref0["actions"][p, :n]].astype(np.float64))

@@ -52,9 +52,9 @@ def test_argument_errors_are_reported_without_a_gpu():
     for P, S, depth, alpha, beta, what in ((1, 4, 0, 0.002, 0.02, b"depth"), (1, -1, 4, 0.002, 0.02, b"S must"),
                                            (70000, 4, 4, 0.002, 0.02, b"P must"), (1, 4, 4, 0.0, 0.0, b"alpha"),
                                            (1, 4, 4, -1.0, 0.5, b"alpha")):
-        assert L.st_search(None, P, S, depth, 1, None, None, alpha, beta, ctypes.byref(r), *nulls, None) == 1
+        assert L.st_search(None, P, S, depth, 1, None, None, None, alpha, beta, ctypes.byref(r), *nulls, None) == 1
         assert what in L.st_last_error()
-    assert L.st_search(None, 0, 4, 4, 1, None, None, 0.002, 0.02, ctypes.byref(r), *nulls, None) == 0
+    assert L.st_search(None, 0, 4, 4, 1, None, None, None, 0.002, 0.02, ctypes.byref(r), *nulls, None) == 0
     # the rollout-policy bit is for rollouts only: the env refuses it
     magnet = st.st_env_config(8, 1, st.make_rules(flags=st.RULES_ALL | st.ROLLOUT_MAGNET), 0, 0, None)
     assert L.st_env_create(ctypes.byref(magnet), ctypes.byref(h)) == 1
