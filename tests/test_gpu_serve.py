@@ -148,3 +148,38 @@ def test_server_with_the_magnet_rollout_policy():
                                                                   flags=flags)[0])
     finally:
         srv.close()
+
+
+def test_burst_from_several_threads_and_immediate_polls():
+    # submissions return before the scheduler has seen them; a ticket polled
+    # at once is not ready (never unknown), and every result is exact
+    pos = _positions(59, 8)
+    reqs = _requests(pos, 6) * 4
+    srv = st.Server(max_requests=32, sample_slots=4096, max_batches=4)
+    tickets = [None] * len(reqs)
+    early = {}
+    try:
+        def client(j):
+            for i in range(j, len(reqs), 4):
+                p, K, D, seed, sid = reqs[i]
+                tickets[i] = srv.submit(p, K, D, seed, sid)
+                try:
+                    early[i] = srv.poll(tickets[i])[0]     # done already: the result is taken here
+                except st.StrategoError as e:
+                    assert e.code == 7, str(e)           # not ready; never unknown
+        ths = [threading.Thread(target=client, args=(j,)) for j in range(4)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        want = {}
+        for i, (p, K, D, seed, sid) in enumerate(reqs):
+            key = (i % len(pos), K, D, seed, sid)
+            if key not in want:
+                want[key] = oracle.rollout(p[None], K, D, seed, stream_ids=[sid])[0]
+            tallies = early[i] if i in early else srv.wait(tickets[i], 60000)[0]
+            np.testing.assert_array_equal(tallies, want[key])
+        with pytest.raises(st.StrategoError, match="invalid argument"):
+            srv.poll(tickets[0])                      # already taken: unknown now
+    finally:
+        srv.close()
