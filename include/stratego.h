@@ -182,6 +182,12 @@ st_status st_env_reset(st_env* env, const uint8_t* setups, const uint8_t* which)
 st_status st_env_step(st_env* env, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
                       uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out);
 
+/* The random policy's action for every slot at the current state, without
+ * playing it: actions[N] int16 (device), the action st_env_step with
+ * actions NULL would play next, -1 for an ended game or a player without a
+ * legal move (App. B.1 SampleRandomLegalAction). */
+st_status st_env_sample_actions(st_env* env, int16_t* actions);
+
 /*
  * st_env_run: n_steps random-policy plies in every slot in one persistent
  * launch, game state held on chip between plies.  Step j of the call writes

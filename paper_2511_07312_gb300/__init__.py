@@ -100,6 +100,7 @@ def _declare(L):
         "st_env_import": [vp, vp, i32, vp],
         "st_env_set_setup_pool": [vp, vp, i32, ctypes.c_uint32],
         "st_env_pin": [vp, vp, i32, vp],
+        "st_env_sample_actions": [vp, vp],
         "st_env_enable_history": [vp, i32],
         "st_env_current_step": [vp, ctypes.POINTER(ctypes.c_int64)],
         "st_env_history_positions": [vp, ctypes.c_int64, vp, vp, vp, vp],
@@ -266,6 +267,12 @@ class Env:
             raise ValueError("pool must be [2, M, 40]")
         self._launch(lib().st_env_set_setup_pool, self._h, _ptr(pool), pool.shape[1], POOL_MIRROR if mirror else 0)
 
+    def sample_actions(self):
+        """The random policy's next action per slot, not played (-1: none)."""
+        out = self._empty(self.N, torch.int16)
+        self._launch(lib().st_env_sample_actions, self._h, _ptr(out))
+        return out
+
     def enable_history(self, H):
         """Keep a record of each of the last H steps (0: off)."""
         self._launch(lib().st_env_enable_history, self._h, int(H))
@@ -361,6 +368,32 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
                             _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
                             _ptr(tallies), _ptr(status), _stream(stream)))
     return tallies, status
+
+
+_TYPE_CHARS = "S23456789MFB"   # Spy, Scout .. General, Marshal, Flag, Bomb
+_LAKES = {42, 43, 46, 47, 52, 53, 56, 57}
+
+
+def board_string(pos):
+    """A text picture of one 784-byte snapshot for debugging (App. B.1
+    BoardStrs): rank 10 on top, two characters per square -- 'r'/'b' and the
+    piece's type for red and blue pieces (upper case once revealed), '~~'
+    for lakes, '..' for empty squares."""
+    import numpy as np
+    p = np.asarray(pos.cpu() if isinstance(pos, torch.Tensor) else pos, dtype=np.uint8).reshape(-1)
+    if p.size != POS_BYTES:
+        raise ValueError("a position is %d bytes" % POS_BYTES)
+    cells = [".." if s not in _LAKES else "~~" for s in range(100)]
+    for pid in range(80):
+        fl = int(p[160 + pid])
+        if fl & 1:
+            side = "r" if pid < 40 else "b"
+            if fl & 2:
+                side = side.upper()
+            cells[int(p[80 + pid])] = side + _TYPE_CHARS[int(p[pid])]
+    ply = int(np.frombuffer(p[240:242].tobytes(), np.int16)[0])
+    rows = [" ".join(cells[10 * r:10 * r + 10]) for r in range(9, -1, -1)]
+    return "\n".join(rows + ["ply %d, %s to move" % (ply, "red" if ply % 2 == 0 else "blue")])
 
 
 def positions_mask(pos, k=100, cap=1000, flags=RULES_ALL, stream=None):

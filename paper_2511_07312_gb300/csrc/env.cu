@@ -425,6 +425,32 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
     }
 }
 
+// Warp per slot: the random policy's action at the current state (the
+// action the next step would play with actions NULL), -1 for an ended game
+// or a player without a legal move (App. B.1 SampleRandomLegalAction).
+__global__ void k_env_sample(EnvArgs A, int16_t* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Team<32> T;
+    SmemGame* G = team_game<32>(smem);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= A.N) return;
+    uint16_t* ring = A.ring + (size_t)g * kRing;
+    uint64_t* pi = A.pi + (size_t)g * kPiWords;
+    load_core(G, A.core + g, T);
+    build_board(G, T);
+    derive_state(G, ring, pi, T);
+    int a = -1;
+    if (!G->c.terminated) {
+        const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
+        if (n > 0) {
+            const uint4 w = philox(make_uint4((uint32_t)g, G->c.episode, (uint32_t)G->c.ply, 2u << 24), A.k0, A.k1);
+            a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
+        }
+    }
+    if (T.leader()) out[g] = (int16_t)a;
+}
+
 // ----------------------------------------------------------------- snapshots
 
 // Warp: the snapshot of game G (history ring `ring`) into o.
@@ -1219,6 +1245,17 @@ extern "C" st_status st_env_history_logs(st_env* e, int64_t t, int32_t L, uint8_
     const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
     k_env_hist_logs<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
         a, hist_query(e, t), L, setups, logs, plies, status);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+extern "C" st_status st_env_sample_actions(st_env* e, int16_t* actions)
+{
+    ST_CHECK_ARG(e && actions, "st_env_sample_actions: null argument");
+    DeviceGuard guard(e->device);
+    EnvArgs a = env_args(e);
+    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
+    k_env_sample<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(a, actions);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

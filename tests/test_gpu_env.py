@@ -213,3 +213,17 @@ def test_bad_snapshot_is_rejected_without_fault():
     now = env.export(torch.arange(4))
     env.sync()
     assert torch.equal(now[:3], pos[:3])
+
+
+def test_sampled_actions_are_the_next_random_plies():
+    # App. B.1 SampleRandomLegalAction: the random policy's action at the
+    # current state, not played; the next step with actions NULL plays it
+    for autoreset in (True, False):
+        env = st.Env(48, seed=12, autoreset=autoreset)
+        ref = oracle.env_run(12, 48, 400, autoreset=autoreset, want_mask=False)
+        for t in range(400):
+            sampled = _np(env.sample_actions())
+            np.testing.assert_array_equal(sampled, ref["action"][t])
+            out = env.step(want_mask=False)
+            np.testing.assert_array_equal(_np(out["action"]), sampled)
+        env.close()
