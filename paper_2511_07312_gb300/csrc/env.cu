@@ -111,6 +111,36 @@ __device__ __forceinline__ void write_mask(const SmemGame* G, const Team<L>& T, 
     for (int i = T.tl; i < kMaskBytes / 16; i += L) d[i] = src[i];
 }
 
+// The persistent step writes each 1,264-byte mask with one bulk asynchronous
+// copy (TMA) from shared memory, issued by the team's first lane, instead of
+// the team's 16-byte stores; the copy runs while the team selects and plays
+// the next move, and the mask is not touched again before mask_free.
+// Both addresses and the size are multiples of 16 bytes (the mask sits at a
+// 16-byte offset of the 16-byte-aligned game record; ring rows are 1,264
+// bytes apart from a 256-byte-aligned base).
+template <int L>
+__device__ __forceinline__ void write_mask_async(const SmemGame* G, const Team<L>& T, uint8_t* dst)
+{
+    // the lanes' mask writes (generic proxy) become visible to the copy engine
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    T.sync();
+    if (T.leader()) {
+        const uint32_t src = static_cast<uint32_t>(__cvta_generic_to_shared(G->mask));
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                     :: "l"(dst), "r"(src), "r"((uint32_t)kMaskBytes) : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+}
+
+// Before the mask is written again: the leader waits until its copies have
+// read the mask out of shared memory.
+template <int L>
+__device__ __forceinline__ void mask_free(const Team<L>& T)
+{
+    if (T.leader()) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    T.sync();
+}
+
 __device__ __forceinline__ bool setup_counts_ok(const uint8_t* s)
 {
     int cnt[2][12];
@@ -209,7 +239,8 @@ __device__ __noinline__ int restart_slot(SmemGame* G, Team<L>, ResetSrc src, uin
 // policy.
 template <int L>
 __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int& n, const EnvArgs& A, uint32_t slot,
-                                             int given, uint16_t* ring, uint64_t* pi, bool& illegal)
+                                             int given, uint16_t* ring, uint64_t* pi, bool& illegal,
+                                             bool async_mask = false)
 {
     PlyResult res;
     res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = G->c.ply;
@@ -227,9 +258,11 @@ __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int&
         }
         apply_move(G, T, a, ring, pi);
         res.action = a;
+        if (async_mask) mask_free(T);
         check_end(G, T, A.R, pi, res.code, res.winner, n);
     }
     if (res.code) {
+        if (async_mask) mask_free(T);
         if (A.R.flags & kAutoreset) {
             n = restart_slot(G, T, A.reset, A.k0, A.k1, A.R.flags, slot, G->c.episode + 1, ring, pi);
         } else {
@@ -402,7 +435,7 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
                 if (kHist) hist_before(G, T);
-                const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal);
+                const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal, mask_ring != nullptr);
                 const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
                 if (T.leader()) {
                     if (kHist) hist_after(G, A, g, r);
@@ -412,8 +445,9 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
                     if (done_ring) done_ring[o] = (uint8_t)r.code;
                     if (ply_ring) ply_ring[o] = (int16_t)r.ply_idx;
                 }
-                if (mask_ring) write_mask(G, T, mask_ring + o * kMaskBytes);
+                if (mask_ring) write_mask_async(G, T, mask_ring + o * kMaskBytes);
             }
+            if (mask_ring) mask_free(T);   // the next slot's first mask overwrites this one
             if (T.leader()) {
                 uint32_t* gs = A.stats + 8 * (size_t)g;
 #pragma unroll
@@ -423,6 +457,8 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             store_core(G, A.core + g, T);
         }
     }
+    // the team's last mask copies have landed before it leaves
+    if (mask_ring && T.leader()) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Warp per slot: the random policy's action at the current state (the
