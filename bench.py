@@ -487,6 +487,18 @@ def secondary(st, torch, dev, args):
     out["search"] = {"positions_per_s": Ps / (ms / 1000), "rollouts_per_s": n_roll / (ms / 1000), "ms": ms,
                      "positions": Ps, "S": Ss, "depth": Ds, "rollouts": n_roll,
                      "mean_legal_moves": n_roll / Ss / Ps}
+    # the oracle beside it: the same positions one at a time on one host
+    # thread, for about 5 seconds
+    import oracle
+    spos_h = spos.cpu().numpy()
+    t_start = time.perf_counter()
+    done_p = 0
+    while done_p < Ps and time.perf_counter() - t_start < 5.0:
+        oracle.search(spos_h[done_p:done_p + 1], Ss, Ds, 11, stream_ids=np.array([done_p], np.uint32))
+        done_p += 1
+    dt = time.perf_counter() - t_start
+    out["search"]["cpu_baseline"] = {"value": done_p / dt, "unit": "positions/s", "cores": 1, "kind": "oracle",
+                                     "sample": "the first %d of the %d positions" % (done_p, Ps)}
     # historical queries: 16,384 slots recording 1,000 steps; positions at
     # step now - 300 rebuilt by replay
     Nh, Hh = 16384, 1000
@@ -513,6 +525,16 @@ def secondary(st, torch, dev, args):
     rebuilt = int((hp["status"] == 0).sum().item())
     out["history_positions"] = {"slots": Nh, "H": Hh, "step": th, "rebuilt": rebuilt, "ms": ms,
                                 "positions_per_s": rebuilt / (ms / 1000)}
+    # the oracle beside it: a slot's position at step th is its environment
+    # run for th steps; slots one at a time on one host thread, ~3 seconds
+    t_start = time.perf_counter()
+    done_g = 0
+    while time.perf_counter() - t_start < 3.0:
+        oracle.env_run(5, 1, th, slot0=done_g, want_mask=False, want_final=True)
+        done_g += 1
+    dt = time.perf_counter() - t_start
+    out["history_positions"]["cpu_baseline"] = {"value": done_g / dt, "unit": "positions/s", "cores": 1,
+                                                "kind": "oracle", "sample": "slots 0..%d" % (done_g - 1)}
     # the same env stepping with and without recording (one launch each, first one includes graph capture)
     henv.enable_history(0)
     henv.run(Hh)
