@@ -12,6 +12,7 @@
 // walk the channels together, and each channel row is one coalesced 100-byte
 // uint8 store and one 200-byte bf16 store per warp.
 #include <mutex>
+#include <atomic>
 #include "engine.cuh"
 #include "features.cuh"
 #include "host_common.h"
@@ -440,14 +441,14 @@ ReplayArgs replay_args(const uint8_t* setups, const int16_t* actions, int32_t lo
     return a;
 }
 
-int g_items_per_warp = 8;   // fastest measured on GB300 for 16,384 items of 64 logs
+std::atomic<int> g_items_per_warp{8};   // fastest measured on GB300 for 16,384 items of 64 logs
 
 }  // namespace
 
 extern "C" st_status st_replay_set_chunk(int32_t items_per_warp)
 {
     ST_CHECK_ARG(items_per_warp >= 1 && items_per_warp <= 65536, "st_replay_set_chunk: 1..65536");
-    g_items_per_warp = items_per_warp;
+    g_items_per_warp.store(items_per_warp);
     return ST_OK;
 }
 
@@ -462,7 +463,7 @@ extern "C" st_status st_replay_positions(const uint8_t* setups, const int16_t* a
     ST_CHECK_ARG(setups && actions && game && ply && out, "st_replay_positions: null argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp;
+    a.items_per_warp = g_items_per_warp.load();
     a.pos_out = out;
     a.status = item_status;
     const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
@@ -497,7 +498,7 @@ extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions
         }
     }
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp;
+    a.items_per_warp = g_items_per_warp.load();
     a.state_out = scratch;
     a.mask_out = mask;
     a.status = status;
@@ -603,7 +604,7 @@ extern "C" st_status st_obs_encode_static(const uint8_t* setups, const int16_t* 
     // k_obs_emit reads them, so nothing left by an earlier call is read and
     // nothing needs clearing first.
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp;
+    a.items_per_warp = g_items_per_warp.load();
     a.state_out = need_planes ? sc.items : nullptr;
     a.mask_out = mask;
     a.status = status;

@@ -19,6 +19,7 @@
 // forms the values, the magnet policy, the update and the sampled move, one
 // warp per position.
 #include <algorithm>
+#include <atomic>
 #include <math_constants.h>
 #include "rollout.cuh"
 #include "host_common.h"
@@ -143,20 +144,20 @@ __global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_rollout_fla
 // Resident blocks per SM of the rollout kernels (both share the shape).
 int flat_blocks_per_sm()
 {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];   // 0 until looked up (threads may race to fill a slot; same value)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
-        int occ = 0;
+    int occ = cached[dev].load(std::memory_order_relaxed);
+    if (!occ) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout_flat, 32 * kFlatWarps,
                                                           kFlatTeams * sizeof(FlatSmem)) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             occ = 1;
         }
-        cached[dev] = occ;
+        cached[dev].store(occ, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return occ;
 }
 
 // ----------------------------------------------------------------- st_search
