@@ -146,12 +146,21 @@ STEP_KERNEL_SOURCES = ("paper_2511_07312_gb300/csrc/env.cu", "paper_2511_07312_g
                        "paper_2511_07312_gb300/csrc/host_common.h", "include/stratego.h")
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace runs collapsed, so
+    that editing a comment does not count as changing the kernel."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_sha256():
     import hashlib
     h = hashlib.sha256()
     for rel in STEP_KERNEL_SOURCES:
         h.update(os.path.basename(rel).encode())
-        h.update(open(os.path.join(ROOT, rel), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, rel), encoding="utf-8").read()).encode())
     return h.hexdigest()
 
 

@@ -469,7 +469,7 @@ st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth,
 /*
  * Serving: test-time search requests with continuous batching (App. E: one
  * search per move; here the search is st_rollout's belief samples and
- * random rollouts).
+ * rollouts, with the rules' rollout policy).
  *
  * The server owns, from st_serve_create on: max_requests request slots on
  * the device (root position, root state, counters), sample_slots per-sample
@@ -477,9 +477,10 @@ st_status st_search(const st_position* pos, int32_t P, int32_t S, int32_t depth,
  * streams, and a scheduler thread.  A submitted request waits in arrival
  * order until a request slot, K contiguous sample records and a stream are
  * free (admission by free device memory); every request admitted since the
- * previous launch goes into one batch (one warp per (request, sample)).
- * Batches run concurrently, so a request arriving while others run starts at
- * once instead of at a batch boundary.  A request's result is exactly
+ * previous launch goes into one batch (one 8-lane team per (request,
+ * sample), at most a resident grid striding over the batch).  Batches run
+ * concurrently, so a request arriving while others run starts at once
+ * instead of at a batch boundary.  A request's result is exactly
  * st_rollout's tallies for the same position, K, depth, seed and stream id.
  */
 typedef struct st_server st_server;
@@ -511,8 +512,9 @@ typedef struct st_serve_stats {
 } st_serve_stats;
 
 st_status st_serve_create(const st_serve_config* cfg, st_server** out);
-/* Queue a request (all HOST memory); returns a ticket.  ST_ERR_BUSY if the
- * host queue holds 2^20 requests. */
+/* Queue a request (all HOST memory); returns a ticket at once, without
+ * waiting for the scheduler.  ST_ERR_BUSY if 2^20 submissions wait to be
+ * taken in. */
 st_status st_serve_submit(st_server* srv, const st_request* req, uint64_t* ticket);
 /* ST_OK with tallies[4] (HOST) and timing (HOST, may be NULL) once done, then
  * the ticket is released; ST_ERR_NOT_READY before; ST_ERR_BAD_POSITION if the
