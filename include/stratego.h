@@ -6,7 +6,8 @@
  * Using Self-Play Reinforcement Learning and Test-Time Search") spend their
  * non-network time in: legal-move masks, move apply and battles, endings with
  * auto-reset, observation planes, belief samples of the opponent's hidden
- * pieces and fixed-depth random rollouts.  Section references are to that
+ * pieces, fixed-depth rollouts, the per-move search with its policy update,
+ * queries about past steps, and serving.  Section references are to that
  * paper: App. A (rules), App. B (simulator), App. C (information state),
  * App. D.1 (game-rule hyperparameters), App. E (search).
  *

@@ -1,7 +1,9 @@
 // rollout.cuh -- shared device code of the search path (App. E "Search",
 // steps 1-2): the hidden-piece plan of a position, one belief sample, the
-// root state of a position kept in HBM, and one warp's rollout from a sample.
-// Used by st_rollout (search.cu) and by the serving engine (serve.cu).
+// root state of a position kept in HBM, and one team's rollout from a sample
+// (plain, or with the search's forced first move).  Used by st_rollout and
+// st_search (search.cu), by the serving engine (serve.cu) and for pinned
+// restarts (env.cu).
 #pragma once
 #include "engine.cuh"
 #include "snapshot.cuh"

@@ -1,21 +1,26 @@
-// search.cu -- belief samples of the opponent's hidden pieces and random
-// rollouts from each sample (App. E "Search", steps 1-2, with the uniform
-// posterior over consistent assignments in place of the belief network and a
-// uniform random policy in place of the move network).
+// search.cu -- belief samples of the opponent's hidden pieces, rollouts from
+// each sample, and the per-move search with its policy update (App. E
+// "Search", steps 1-4, with the uniform posterior over consistent
+// assignments in place of the belief network and the uniform or magnet
+// rollout policy in place of the move network).
 //
 // k_belief: one block per position; the position is read once into shared
 // memory, its hidden-piece plan is built once, and every thread then draws
 // whole samples (Fisher-Yates over at most 40 pieces) from its own Philox
 // stream.
 // st_rollout: k_roots imports every position once (one warp each) into a
-// root record in HBM; k_rollout_flat runs one 8-lane team per (position,
-// sample), copying the root into shared memory, so a single position's
-// samples spread over the whole GPU.  A rollout keeps no history ring (its
-// last two moves start from the root's).
+// root record in HBM; k_draw_samples draws every belief sample ahead (a
+// thread per sample); k_rollout_flat runs one 8-lane team per (position,
+// sample) at a time on a resident grid, copying the root into shared memory,
+// so a single position's samples spread over the whole GPU.  A rollout keeps
+// no history ring (its last two moves start from the root's) and its chase
+// store sits in a global scratch slot of its team.
+// st_positions_mask: legal masks of snapshots (App. B.1 ComputeLegalActionMask).
 // st_search (steps 1-4): k_search_prep imports every position, lists the
 // searcher's legal moves in ascending order and clears the outputs;
-// k_search_offsets turns the move counts into unit offsets; k_search_rollouts
-// runs one 8-lane team per (position, move, sample) unit; k_search_policy
+// k_search_offsets turns the move counts into unit offsets; k_draw_samples
+// draws each configuration once; k_search_rollouts runs one 8-lane team per
+// (position, move, sample) unit at a time on a resident grid; k_search_policy
 // forms the values, the magnet policy, the update and the sampled move, one
 // warp per position.
 #include <algorithm>

@@ -12,11 +12,13 @@
 // free device memory.
 //
 // A host scheduler thread admits every request that fits, in arrival order,
-// and issues one batch (root kernel + one warp per (request, sample)
-// rollout kernel) for all requests admitted since the previous batch, on the
-// next stream of a pool.  Batches already running keep running: new requests
+// and issues one batch (root kernel + rollout kernel, one 8-lane team per
+// (request, sample) at a time on at most a resident grid) for all requests
+// admitted since the previous batch, on the next stream of a pool.
+// Submissions wait under their own small lock, so a submit never waits for
+// a scheduler pass.  Batches already running keep running: new requests
 // never wait for a batch boundary, their work overlaps the older work on the
-// GPU, and the slots of a finished request are reused at once.  The warp that
+// GPU, and the slots of a finished request are reused at once.  The team that
 // finishes a request's last rollout copies the tallies to host-mapped memory
 // and then publishes a completion word; the scheduler polls those words.  No
 // kernel ever waits on the host or on another kernel.
