@@ -164,22 +164,47 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def measured_traffic_per_env_step():
-    """DRAM bytes per env-step of the step kernel from the committed ncu
-    summary, or None when the kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "k_env_run_traffic.md")
+def profile_value(name, key):
+    """A machine-readable line `key: value` of a committed ncu summary under
+    profiles/, or None when the step kernel's code changed since the capture
+    (the summary's sources_sha256 line no longer matches)."""
     try:
-        text = open(path).read()
+        text = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     vals = {}
     for line in text.splitlines():
         parts = line.strip().split(":", 1)
-        if len(parts) == 2 and parts[0] in ("sources_sha256", "traffic_bytes_per_env_step"):
-            vals[parts[0]] = parts[1].strip()
-    if vals.get("sources_sha256") != kernel_sources_sha256() or "traffic_bytes_per_env_step" not in vals:
+        if len(parts) == 2:
+            vals[parts[0].strip()] = parts[1].strip()
+    if vals.get("sources_sha256") != kernel_sources_sha256() or key not in vals:
         return None
-    return float(vals["traffic_bytes_per_env_step"])
+    return float(vals[key])
+
+
+def measured_traffic_per_env_step():
+    """DRAM bytes per env-step of the step kernel from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    return profile_value("k_env_run_traffic.md", "traffic_bytes_per_env_step")
+
+
+# Issue slots of one GB300: 152 SMs x 4 schedulers x one warp instruction a
+# cycle at the 2,070 MHz maximum SM clock.
+ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.07e9
+
+
+def issue_view(env_steps_per_s_per_gpu, hbm_peak_gbs):
+    ipe = profile_value("k_env_run_16384games_100plies.md", "warp_inst_per_env_step")
+    lanes = profile_value("k_env_run_16384games_100plies.md", "active_lanes_per_warp_inst")
+    if ipe is None:
+        return None
+    achieved = env_steps_per_s_per_gpu * ipe
+    return {"achieved": achieved, "peak": ISSUE_PEAK_WARP_INST_PER_S, "unit": "warp-inst/s",
+            "frac": achieved / ISSUE_PEAK_WARP_INST_PER_S, "warp_inst_per_env_step": ipe,
+            "active_lanes_per_warp_inst": lanes,
+            "note": "instructions per env-step from profiles/k_env_run_16384games_100plies.md; the step's "
+                    "binding ceiling: issue allows %.2e env-steps/s, HBM %.2e" %
+                    (ISSUE_PEAK_WARP_INST_PER_S / ipe, hbm_peak_gbs * 1e9 / BYTES_PER_ENV_STEP)}
 
 
 # ---------------------------------------------------------------- oracle on the host
@@ -371,6 +396,9 @@ def main():
                                              "from a 16,384 x 400 capture (profiles/k_env_run_traffic.md)",
                              "peak_kind": peak_kind + " hbm_gbs (copy, burst)",
                              "algorithmic_bytes_per_env_step": BYTES_PER_ENV_STEP, "kernel": "k_env_run"},
+                # the same launch against the issue-slot ceiling, side by side
+                # (instructions per env-step from the committed ncu capture)
+                "issue": issue_view(value / max(1, world), peak),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
                 "cpu_baseline": cpu, "extras": extras}
         print(json.dumps(line), flush=True)
