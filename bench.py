@@ -209,20 +209,79 @@ def issue_view(env_steps_per_s_per_gpu, hbm_peak_gbs):
 
 # ---------------------------------------------------------------- oracle on the host
 
-def oracle_env_rate(seed, plies, budget_s=12.0, chunk=64):
-    """Oracle env-steps/s on one host thread over a bounded sample of slots."""
+def host_threads():
+    """Host threads for the oracle: the cores this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_env_slots(seed, slot0, n_slots, plies, threads, chunk):
+    """Run the oracle environment over slots slot0 .. slot0+n_slots-1 on
+    `threads` host threads, each taking `chunk` slots at a time (the C oracle
+    runs with the GIL released, and slots are independent).  Returns the
+    wall time in seconds."""
     import oracle
+    oracle.lib()   # load the library once, before the threads
+    nxt = [slot0]
+    lock = threading.Lock()
+
+    def worker():
+        while True:
+            with lock:
+                s = nxt[0]
+                if s >= slot0 + n_slots:
+                    return
+                n = min(chunk, slot0 + n_slots - s)
+                nxt[0] = s + n
+            oracle.env_run(seed, n, plies, slot0=s)
+
     t0 = time.perf_counter()
-    steps = 0
+    pool = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in pool:
+        t.start()
+    for t in pool:
+        t.join()
+    return time.perf_counter() - t0
+
+
+def oracle_env_rate(seed, plies, budget_s=12.0, chunk=16, threads=1):
+    """Oracle env-steps/s over a bounded sample of slots: rounds of
+    `threads` x `chunk` slots until about budget_s seconds have passed."""
+    t_all = 0.0
     slot = 0
-    while True:
-        oracle.env_run(seed, chunk, plies, slot0=slot)
-        steps += chunk * plies
-        slot += chunk
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return steps / dt, "%d slots x %d plies (masks written), slots 0..%d" % (slot, plies, slot - 1), dt
+    while t_all < budget_s:
+        n = threads * chunk
+        t_all += oracle_env_slots(seed, slot, n, plies, threads, chunk)
+        slot += n
+    return slot * plies / t_all, "%d slots x %d plies (masks written), slots 0..%d, %d host threads" % (
+        slot, plies, slot - 1, threads), t_all
+
+
+def timed_items(fn, n_items, threads, budget_s):
+    """Call fn(i) for i = 0, 1, ... on `threads` host threads until about
+    budget_s seconds have passed or all n_items are done; returns the items
+    done and the wall time in seconds."""
+    nxt = [0]
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                i = nxt[0]
+                if i >= n_items or time.perf_counter() - t0 >= budget_s:
+                    return
+                nxt[0] = i + 1
+            fn(i)
+
+    pool = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in pool:
+        t.start()
+    for t in pool:
+        t.join()
+    return nxt[0], time.perf_counter() - t0
 
 
 def run_reference(args):
@@ -232,24 +291,25 @@ def run_reference(args):
     import oracle
     oracle.lib()
     plies = args.plies
-    chunk = 16
+    chunk = 8
+    threads = host_threads()
     for _ in range(args.warmup):
-        oracle.env_run(args.seed, 4, 100)
+        oracle_env_slots(args.seed, 0, threads * 4, 100, threads, 4)
     times = []
+    per_step = threads * chunk
     for k in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.env_run(args.seed, chunk, plies, slot0=k * chunk)
-        times.append(time.perf_counter() - t0)
+        times.append(oracle_env_slots(args.seed, k * per_step, per_step, plies, threads, chunk))
     total = sum(times)
-    value = args.steps * chunk * plies / total
-    sample = "%d steps x (%d slots x %d plies) of the %d-slot workload, masks written" % (
-        args.steps, chunk, plies, args.games)
+    value = args.steps * per_step * plies / total
+    sample = "%d steps x (%d slots x %d plies) of the %d-slot workload, masks written, %d host threads" % (
+        args.steps, per_step, plies, args.games, threads)
     line = {"impl": "reference", "metric": "env steps/s at 65,536 games", "value": value, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": workload_config(args.games, plies, args.ring),
-            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -376,9 +436,13 @@ def main():
 
     cpu = None
     if rank == 0:
-        rate, sample, secs = oracle_env_rate(args.seed, S)
-        cpu = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": round(secs, 1)}
+        # all host threads (the figure of record), then one thread beside it
+        threads = host_threads()
+        rate, sample, secs = oracle_env_rate(args.seed, S, budget_s=10.0, chunk=4, threads=threads)
+        rate1, sample1, secs1 = oracle_env_rate(args.seed, S, budget_s=5.0, chunk=4, threads=1)
+        cpu = {"value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 1),
+               "single_thread": {"value": rate1, "sample": sample1, "seconds": round(secs1, 1)}}
 
     if rank == 0:
         line = {"metric": "env steps/s at 65,536 games", "value": value, "unit": "env-steps/s", "n_gpus": world,
@@ -524,18 +588,16 @@ def secondary(st, torch, dev, args):
     out["search"] = {"positions_per_s": Ps / (ms / 1000), "rollouts_per_s": n_roll / (ms / 1000), "ms": ms,
                      "positions": Ps, "S": Ss, "depth": Ds, "rollouts": n_roll,
                      "mean_legal_moves": n_roll / Ss / Ps}
-    # the oracle beside it: the same positions one at a time on one host
-    # thread, for about 5 seconds
+    # the oracle beside it: the same positions, one per call, on all host
+    # threads for about 5 seconds
     import oracle
+    oracle.lib()
     spos_h = spos.cpu().numpy()
-    t_start = time.perf_counter()
-    done_p = 0
-    while done_p < Ps and time.perf_counter() - t_start < 5.0:
-        oracle.search(spos_h[done_p:done_p + 1], Ss, Ds, 11, stream_ids=np.array([done_p], np.uint32))
-        done_p += 1
-    dt = time.perf_counter() - t_start
-    out["search"]["cpu_baseline"] = {"value": done_p / dt, "unit": "positions/s", "cores": 1, "kind": "oracle",
-                                     "sample": "the first %d of the %d positions" % (done_p, Ps)}
+    threads = host_threads()
+    done_p, dt = timed_items(lambda i: oracle.search(spos_h[i:i + 1], Ss, Ds, 11,
+                                                     stream_ids=np.array([i], np.uint32)), Ps, threads, 5.0)
+    out["search"]["cpu_baseline"] = {"value": done_p / dt, "unit": "positions/s", "cores": threads,
+                                     "kind": "oracle", "sample": "the first %d of the %d positions" % (done_p, Ps)}
     # historical queries: 16,384 slots recording 1,000 steps; positions at
     # step now - 300 rebuilt by replay
     Nh, Hh = 16384, 1000
@@ -563,14 +625,10 @@ def secondary(st, torch, dev, args):
     out["history_positions"] = {"slots": Nh, "H": Hh, "step": th, "rebuilt": rebuilt, "ms": ms,
                                 "positions_per_s": rebuilt / (ms / 1000)}
     # the oracle beside it: a slot's position at step th is its environment
-    # run for th steps; slots one at a time on one host thread, ~3 seconds
-    t_start = time.perf_counter()
-    done_g = 0
-    while time.perf_counter() - t_start < 3.0:
-        oracle.env_run(5, 1, th, slot0=done_g, want_mask=False, want_final=True)
-        done_g += 1
-    dt = time.perf_counter() - t_start
-    out["history_positions"]["cpu_baseline"] = {"value": done_g / dt, "unit": "positions/s", "cores": 1,
+    # run for th steps; one slot per call on all host threads, ~3 seconds
+    done_g, dt = timed_items(lambda i: oracle.env_run(5, 1, th, slot0=i, want_mask=False, want_final=True),
+                             Nh, threads, 3.0)
+    out["history_positions"]["cpu_baseline"] = {"value": done_g / dt, "unit": "positions/s", "cores": threads,
                                                 "kind": "oracle", "sample": "slots 0..%d" % (done_g - 1)}
     # the same env stepping with and without recording (one launch each, first one includes graph capture)
     henv.enable_history(0)
