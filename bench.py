@@ -44,10 +44,11 @@ def parse():
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
     p.add_argument("--gpw", type=int, default=0, help="games per warp, 1, 2, 4 or 8 (0 = tuned default)")
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--profile", nargs="?", const="step", default=None, choices=["step", "rollout"],
+    p.add_argument("--profile", nargs="?", const="step", default=None, choices=["step", "rollout", "obs"],
                    help="for profiler captures: time one workload only -- the persistent step launch "
-                        "(step, the default) or the belief-sample rollouts of 4,096 positions (rollout); "
-                        "no plain path, end-to-end, other workloads or CPU baseline")
+                        "(step, the default), the belief-sample rollouts of 4,096 positions (rollout) or "
+                        "the observation planes of 16,384 replayed positions (obs); no plain path, "
+                        "end-to-end, other workloads or CPU baseline")
     return p.parse_args()
 
 
@@ -333,9 +334,9 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    if args.profile == "rollout":
+    if args.profile in ("rollout", "obs"):
         if rank == 0:
-            profile_rollouts(st, torch, dev, args)
+            (profile_rollouts if args.profile == "rollout" else profile_obs)(st, torch, dev, args)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -519,6 +520,27 @@ def profile_rollouts(st, torch, dev, args):
     ms = t0.elapsed_time(t1) / args.steps
     print(json.dumps({"profile": "rollout", "positions": pos.shape[0], "K": K, "depth": D, "ms_per_call": ms,
                       "samples_per_s": pos.shape[0] * K / (ms / 1000)}), flush=True)
+
+
+def profile_obs(st, torch, dev, args):
+    """The observation workload alone (planes, bf16 copy and masks of 16,384
+    replayed positions), for profiler captures."""
+    setups, acts, gi, pl = game_positions(st, torch, dev)
+    o = st.obs_encode(setups, acts, gi, pl)
+    for _ in range(args.warmup):
+        st.obs_encode(setups, acts, gi, pl, out=o)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(args.steps):
+        st.obs_encode(setups, acts, gi, pl, out=o)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    B = gi.numel()
+    print(json.dumps({"profile": "obs", "positions": B, "ms_per_call": ms, "positions_per_s": B / (ms / 1000),
+                      "status_ok": int((o["status"] == 0).sum().item())}), flush=True)
 
 
 def secondary(st, torch, dev, args):
