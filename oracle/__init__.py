@@ -26,9 +26,11 @@ _lib = None
 
 
 def lib():
+    """The oracle library: liboracle.so built here, or the file that
+    STRATEGO_ORACLE_LIB names (a sanitizer build, for the tests)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("STRATEGO_ORACLE_LIB") or _build.build()
         _lib = ctypes.CDLL(path)
         _declare(_lib)
     return _lib

@@ -14,19 +14,22 @@ SOURCES = ["philox.c", "rules.c", "obs.c", "belief.c", "drivers.c", "search.c", 
 LIB = os.path.join(HERE, "liboracle.so")
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, out: str = LIB, extra=()) -> str:
+    """Build the library at `out` (default: liboracle.so here) with the
+    standard flags plus `extra` (the tests build a sanitizer variant into a
+    temporary directory this way)."""
     srcs = [os.path.join(HERE, s) for s in SOURCES]
     deps = srcs + [os.path.join(HERE, "oracle.h")]
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
+            return out
+    tmp = out + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
-           "-fno-fast-math", "-ffp-contract=off", "-o", tmp] + srcs
+           "-fno-fast-math", "-ffp-contract=off"] + list(extra) + ["-o", tmp] + srcs
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
