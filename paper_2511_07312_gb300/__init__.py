@@ -133,13 +133,21 @@ def _check(code):
         raise StrategoError(code, lib().st_last_error().decode())
 
 
-def _ptr(t, dtype=None, name="tensor"):
+def _ptr(t, dtype=None, name="tensor", numel=None):
+    """Device address of a contiguous CUDA tensor of the given dtype.  numel:
+    the elements the call reads or writes through it; a smaller tensor is
+    refused here, since the C entry points get bare pointers and cannot
+    check extents themselves."""
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a CUDA tensor" % name)
     if dtype is not None and t.dtype != dtype:
         raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s holds %d elements; the call uses %d" % (name, t.numel(), numel))
+    if not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     return ctypes.c_void_p(t.data_ptr())
@@ -214,8 +222,11 @@ class Env:
             out = dict(action=self._empty(self.N, torch.int16), reward=self._empty(self.N, torch.int8),
                        done=self._empty(self.N, torch.uint8), ply=self._empty(self.N, torch.int16),
                        mask=self._empty((self.N, MASK_BYTES), torch.uint8) if want_mask else None)
-        self._launch(lib().st_env_step, self._h, _ptr(actions, torch.int16, "actions"), _ptr(out["action"]),
-                     _ptr(out["reward"]), _ptr(out["done"]), _ptr(out["ply"]), _ptr(out.get("mask")))
+        N = self.N
+        self._launch(lib().st_env_step, self._h, _ptr(actions, torch.int16, "actions", N),
+                     _ptr(out["action"], torch.int16, "action", N), _ptr(out["reward"], torch.int8, "reward", N),
+                     _ptr(out["done"], torch.uint8, "done", N), _ptr(out["ply"], torch.int16, "ply", N),
+                     _ptr(out.get("mask"), torch.uint8, "mask", N * MASK_BYTES))
         return out
 
     def run(self, n_steps, ring_steps=None, want=("action", "reward", "done", "ply", "mask"), out=None):
@@ -227,8 +238,10 @@ class Env:
                        done=self._empty(shp, torch.uint8) if "done" in want else None,
                        ply=self._empty(shp, torch.int16) if "ply" in want else None,
                        mask=self._empty(shp + (MASK_BYTES,), torch.uint8) if "mask" in want else None)
-        self._launch(lib().st_env_run, self._h, int(n_steps), ring_steps, _ptr(out["action"]), _ptr(out["reward"]),
-                     _ptr(out["done"]), _ptr(out["ply"]), _ptr(out["mask"]))
+        n = ring_steps * self.N
+        self._launch(lib().st_env_run, self._h, int(n_steps), ring_steps, _ptr(out["action"], torch.int16, "action", n),
+                     _ptr(out["reward"], torch.int8, "reward", n), _ptr(out["done"], torch.uint8, "done", n),
+                     _ptr(out["ply"], torch.int16, "ply", n), _ptr(out["mask"], torch.uint8, "mask", n * MASK_BYTES))
         return out
 
     def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1, games_per_warp=1):
@@ -236,8 +249,8 @@ class Env:
                                        int(games_per_fetch)))
 
     def reset(self, setups=None, which=None):
-        self._launch(lib().st_env_reset, self._h, _ptr(setups, torch.uint8, "setups"),
-                     _ptr(which, torch.uint8, "which"))
+        self._launch(lib().st_env_reset, self._h, _ptr(setups, torch.uint8, "setups", self.N * 80),
+                     _ptr(which, torch.uint8, "which", self.N))
 
     def sync(self):
         _check(lib().st_env_sync(self._h))
@@ -255,7 +268,8 @@ class Env:
 
     def import_(self, idx, pos):
         idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
-        self._launch(lib().st_env_import, self._h, _ptr(idx), idx.numel(), _ptr(pos, torch.uint8, "positions"))
+        self._launch(lib().st_env_import, self._h, _ptr(idx), idx.numel(),
+                     _ptr(pos, torch.uint8, "positions", idx.numel() * POS_BYTES))
 
     def set_setup_pool(self, pool, mirror=False):
         """New games take their setups from pool [2, M, 40] uint8 (None: off)."""
@@ -313,7 +327,8 @@ class Env:
             self._launch(lib().st_env_pin, self._h, None, 0, None)
             return
         idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
-        self._launch(lib().st_env_pin, self._h, _ptr(idx), idx.numel(), _ptr(states, torch.uint8, "states"))
+        self._launch(lib().st_env_pin, self._h, _ptr(idx), idx.numel(),
+                     _ptr(states, torch.uint8, "states", idx.numel() * POS_BYTES))
 
 
 def _dev(t, dtype, device):
@@ -326,9 +341,10 @@ def replay_positions(setups, actions, game, ply, k=100, cap=1000, flags=RULES_AL
     out = torch.empty((B, POS_BYTES), dtype=torch.uint8, device=dev)
     status = torch.empty(B, dtype=torch.uint8, device=dev)
     r = make_rules(k, cap, flags)
-    _check(lib().st_replay_positions(_ptr(setups, torch.uint8), _ptr(actions, torch.int16), actions.shape[1],
-                                     actions.shape[0], _ptr(game, torch.int32), _ptr(ply, torch.int16), B, ctypes.byref(r),
-                                     _ptr(out), _ptr(status), _stream(stream)))
+    _check(lib().st_replay_positions(_ptr(setups, torch.uint8, "setups", actions.shape[0] * 80),
+                                     _ptr(actions, torch.int16, "actions"), actions.shape[1], actions.shape[0],
+                                     _ptr(game, torch.int32, "game"), _ptr(ply, torch.int16, "ply", B), B,
+                                     ctypes.byref(r), _ptr(out), _ptr(status), _stream(stream)))
     return out, status
 
 
@@ -342,10 +358,14 @@ def obs_encode(setups, actions, game, ply, player=None, k=100, cap=1000, flags=R
                    mask=torch.empty((B, MASK_BYTES), dtype=torch.uint8, device=dev) if want_mask else None,
                    status=torch.empty(B, dtype=torch.uint8, device=dev))
     r = make_rules(k, cap, flags)
-    _check(lib().st_obs_encode(_ptr(setups, torch.uint8), _ptr(actions, torch.int16), actions.shape[1],
-                               actions.shape[0], _ptr(game, torch.int32), _ptr(ply, torch.int16), _ptr(player, torch.int8), B,
-                               ctypes.byref(r), _ptr(out["planes"]), _ptr(out["planes_bf16"]), _ptr(out["mask"]),
-                               _ptr(out["status"]), _stream(stream)))
+    _check(lib().st_obs_encode(_ptr(setups, torch.uint8, "setups", actions.shape[0] * 80),
+                               _ptr(actions, torch.int16, "actions"), actions.shape[1], actions.shape[0],
+                               _ptr(game, torch.int32, "game"), _ptr(ply, torch.int16, "ply", B),
+                               _ptr(player, torch.int8, "player", B), B, ctypes.byref(r),
+                               _ptr(out["planes"], torch.uint8, "planes", B * NCHAN * 100),
+                               _ptr(out["planes_bf16"], torch.bfloat16, "planes_bf16", B * NCHAN * 100),
+                               _ptr(out["mask"], torch.uint8, "mask", B * MASK_BYTES),
+                               _ptr(out["status"], torch.uint8, "status", B), _stream(stream)))
     return out
 
 
@@ -353,8 +373,9 @@ def belief_sample(pos, K, seed, stream_ids=None, stream=None):
     P = pos.shape[0]
     types = torch.empty((P, K, 40), dtype=torch.uint8, device=pos.device)
     status = torch.empty(P, dtype=torch.uint8, device=pos.device)
-    _check(lib().st_belief_sample(_ptr(pos, torch.uint8), P, int(K), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                  _ptr(stream_ids, torch.int32), _ptr(types), _ptr(status), _stream(stream)))
+    _check(lib().st_belief_sample(_ptr(pos, torch.uint8, "pos", P * POS_BYTES), P, int(K),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(stream_ids, torch.int32, "stream_ids", P),
+                                  _ptr(types), _ptr(status), _stream(stream)))
     return types, status
 
 
@@ -364,9 +385,10 @@ def rollout(pos, K, depth, seed, stream_ids=None, types=None, k=100, cap=1000, f
     tallies = out if out is not None else torch.empty((P, 4), dtype=torch.int32, device=pos.device)
     status = torch.empty(P, dtype=torch.uint8, device=pos.device)
     r = make_rules(k, cap, flags)
-    _check(lib().st_rollout(_ptr(pos, torch.uint8), P, int(K), int(depth), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                            _ptr(stream_ids, torch.int32), _ptr(types, torch.uint8), ctypes.byref(r),
-                            _ptr(tallies), _ptr(status), _stream(stream)))
+    _check(lib().st_rollout(_ptr(pos, torch.uint8, "pos", P * POS_BYTES), P, int(K), int(depth),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(stream_ids, torch.int32, "stream_ids", P),
+                            _ptr(types, torch.uint8, "types", P * max(int(K), 0) * 40), ctypes.byref(r),
+                            _ptr(tallies, torch.int32, "tallies", P * 4), _ptr(status), _stream(stream)))
     return tallies, status
 
 
@@ -405,7 +427,7 @@ def positions_mask(pos, k=100, cap=1000, flags=RULES_ALL, stream=None):
                two_square=torch.empty(P, dtype=torch.uint8, device=dev),
                status=torch.empty(P, dtype=torch.uint8, device=dev))
     r = make_rules(k, cap, flags)
-    _check(lib().st_positions_mask(_ptr(pos, torch.uint8), P, ctypes.byref(r), _ptr(out["mask"]),
+    _check(lib().st_positions_mask(_ptr(pos, torch.uint8, "pos", P * POS_BYTES), P, ctypes.byref(r), _ptr(out["mask"]),
                                    _ptr(out["n_legal"]), _ptr(out["two_square"]), _ptr(out["status"]),
                                    _stream(stream)))
     return out
@@ -437,9 +459,10 @@ def search(pos, S, depth, seed, stream_ids=None, pi_theta=None, alpha=SEARCH_ALP
         "status": torch.empty(P, dtype=torch.uint8, device=dev),
     }
     r = make_rules(k, cap, flags)
-    _check(lib().st_search(_ptr(pos, torch.uint8), P, int(S), int(depth), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                           _ptr(stream_ids, torch.int32), _ptr(pi_theta, torch.float32),
-                           _ptr(q_values, torch.float32), float(alpha), float(beta),
+    _check(lib().st_search(_ptr(pos, torch.uint8, "pos", P * POS_BYTES), P, int(S), int(depth),
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(stream_ids, torch.int32, "stream_ids", P),
+                           _ptr(pi_theta, torch.float32, "pi_theta", P * 10000),
+                           _ptr(q_values, torch.float32, "q_values", P * 10000), float(alpha), float(beta),
                            ctypes.byref(r), _ptr(out["n_moves"]), _ptr(out["actions"]), _ptr(out["tallies"]),
                            _ptr(out["q"]), _ptr(out["pi"]), _ptr(out["chosen"]), _ptr(out["status"]),
                            _stream(stream)))
