@@ -135,6 +135,46 @@ def test_full_size_65536_games_2000_plies_sampled_slots():
             assert np.array_equal(ring["mask"][row % R, s], r["mask"][row, 0]), ("mask", s, row)
 
 
+def test_full_size_all_65536_slots_counters_and_final_positions():
+    # the same launch; every slot's counters (games ended by each code,
+    # plies, wins per side) and final snapshot against the oracle, the
+    # oracle stepping disjoint slots on every host thread
+    import os
+    import threading
+    from paper_2511_07312_gb300 import autotune
+    N, S = 65536, 2000
+    best = autotune.tune(N)
+    env = st.Env(N, seed=1)
+    env.set_launch(best["warps_per_block"], 0, best["games_per_fetch"], games_per_warp=best["games_per_warp"])
+    env.run(S, 16)
+    env.sync()
+    stats = _np(env.stats())
+    pos = _np(env.export(torch.arange(N, dtype=torch.int32)))
+    chunk, nxt, bad = 256, [0], []
+    lock = threading.Lock()
+
+    def worker():
+        while True:
+            with lock:
+                s0 = nxt[0]
+                nxt[0] += chunk
+            if s0 >= N:
+                return
+            r = oracle.env_run(1, chunk, S, slot0=s0, want_mask=False, want_final=True)
+            st_ok = np.array_equal(stats[s0:s0 + chunk], r["stats"].astype(np.int32))
+            pos_ok = np.array_equal(pos[s0:s0 + chunk], r["final"])
+            if not (st_ok and pos_ok):
+                with lock:
+                    bad.append((s0, st_ok, pos_ok))
+
+    threads = [threading.Thread(target=worker) for _ in range(max(1, len(os.sched_getaffinity(0))))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not bad, "chunks (first slot, counters equal, final positions equal) that differ: %s" % sorted(bad)[:8]
+
+
 def test_supplied_actions_and_illegal_action_latch():
     env = st.Env(16, seed=3)
     ref = oracle.env_run(3, 16, 40)
