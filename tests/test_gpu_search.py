@@ -134,14 +134,15 @@ def test_search_degenerate_inputs():
                       beta=args["beta"])
 
 
-def test_search_full_size_sampled_positions():
+def test_search_full_size_all_positions():
     # the benchmark's search workload (256 positions, 16 configurations,
-    # depth 40); the oracle checks a sample of the positions, each with its
-    # own stream id, which makes its results independent of the others
+    # depth 40), every position against the oracle; position p's stream id
+    # is p on both sides, so a sample keeps its own results as well
     pos = _positions(47, 64, 4, upto=600)
     S, depth, seed = 16, 40, 2024
     got = st.search(torch.from_numpy(pos).cuda(), S, depth, seed)
     torch.cuda.synchronize()
+    _compare(got, oracle.search(pos, S, depth, seed), seed)
     pick = np.array([0, 1, 63, 128, 200, 255])
     ref = oracle.search(pos[pick], S, depth, seed, stream_ids=pick.astype(np.uint32))
     sub = {k: v[torch.from_numpy(pick).cuda()] for k, v in got.items()}
