@@ -1,0 +1,180 @@
+// Test harness only: a host stand-in for the CUDA device features the
+// engine's kernels use, so that their source can be compiled with g++ and
+// run on host threads under ThreadSanitizer, AddressSanitizer and
+// UndefinedBehaviorSanitizer (compute-sanitizer is not available to this
+// project).  Every lane is a std::thread; a warp collective (__syncwarp,
+// __ballot_sync, __shfl*_sync, __reduce_add_sync) is a rendezvous of the
+// lanes named in its mask under one mutex per warp, which gives the
+// sanitizers the same ordering the hardware collective gives; a lane outside
+// the mask, a source lane outside the mask or a collective that never
+// completes aborts the run.  Shared-memory atomics are host atomics.  A bulk
+// asynchronous copy (cp.async.bulk) is performed at its wait, the latest
+// moment the hardware may read its source, so a source rewritten too early
+// shows up as wrong output.  The product library never includes this file.
+#pragma once
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <cstdio>
+#include <cassert>
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <condition_variable>
+#include <vector>
+#define __device__
+#define __global__
+#define __host__
+#define __shared__
+#define __constant__
+#define __forceinline__ inline __attribute__((always_inline))
+#define __noinline__ __attribute__((noinline))
+#define __align__(n) __attribute__((aligned(n)))
+#define __launch_bounds__(...)
+#define __restrict__ __restrict
+struct uint3 { unsigned x, y, z; };
+struct dim3 { unsigned x, y, z; };
+extern thread_local uint3 threadIdx, blockIdx;
+extern dim3 blockDim, gridDim;
+struct uint4 { unsigned x, y, z, w; };
+struct uint2 { unsigned x, y; };
+struct int4 { int x, y, z, w; };
+struct int2 { int x, y; };
+inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
+inline uint2 make_uint2(unsigned a, unsigned b) { return uint2{a, b}; }
+using std::min;
+using std::max;
+typedef struct CUstream_st* cudaStream_t;
+typedef struct CUgraphExec_st* cudaGraphExec_t;
+typedef int cudaError_t;
+
+namespace emu {
+struct Rendezvous {
+    unsigned arrived = 0;
+    int phase = 0;            // 0 collecting, 1 reading
+    int readers = 0;
+    unsigned long long gen = 0;
+    unsigned long long vals[32];
+};
+struct Warp {
+    std::mutex m;
+    std::condition_variable cv;
+    std::map<unsigned, Rendezvous> rv;
+};
+extern Warp* warps;              // [blocks][32 warps], allocated per launch
+extern unsigned char* smem_base;  // [blocks][smem_per_block]
+extern size_t smem_per_block;
+inline Warp& warp_of() { return warps[blockIdx.x * 32 + (threadIdx.x >> 5)]; }
+inline unsigned char* block_smem() { return smem_base + (size_t)blockIdx.x * smem_per_block; }
+[[noreturn]] inline void fail(const char* what, unsigned mask)
+{
+    std::fprintf(stderr, "EMU FAILURE: %s (lane %u, mask %08x)\n", what, threadIdx.x & 31, mask);
+    std::fflush(stderr);
+    std::abort();
+}
+template <class F>
+unsigned long long exchange(unsigned mask, unsigned long long v, F f)
+{
+    const unsigned lane = threadIdx.x & 31;
+    if (!((mask >> lane) & 1u)) fail("calling lane not in mask", mask);
+    Warp& W = warp_of();
+    std::unique_lock<std::mutex> lk(W.m);
+    Rendezvous& R = W.rv[mask];
+    W.cv.wait(lk, [&] { return R.phase == 0; });
+    if ((R.arrived >> lane) & 1u) fail("lane arrived twice", mask);
+    R.vals[lane] = v;
+    R.arrived |= 1u << lane;
+    const unsigned long long my = R.gen;
+    if (R.arrived == mask) {
+        R.phase = 1;
+        R.readers = __builtin_popcount(mask);
+        W.cv.notify_all();
+    } else {
+        if (!W.cv.wait_for(lk, std::chrono::seconds(20), [&] { return R.phase == 1 && R.gen == my; }))
+            fail("collective never completed (deadlock)", mask);
+    }
+    const unsigned long long out = f(R.vals, lane);
+    if (--R.readers == 0) {
+        R.arrived = 0;
+        R.phase = 0;
+        R.gen++;
+        W.cv.notify_all();
+    }
+    return out;
+}
+inline unsigned src_ok(unsigned mask, unsigned s)
+{
+    if (!((mask >> s) & 1u)) fail("source lane not in mask", mask);
+    return s;
+}
+template <class T> unsigned long long bits(T v) { unsigned long long u = 0; std::memcpy(&u, &v, sizeof(T)); return u; }
+template <class T> T from(unsigned long long u) { T v; std::memcpy(&v, &u, sizeof(T)); return v; }
+// bulk copies: performed at the wait (the latest moment the hardware may read)
+struct Pending { void* dst; const void* src; size_t n; };
+extern thread_local std::vector<Pending> pending;
+inline void bulk_copy(void* dst, const void* src, size_t n) { pending.push_back({dst, src, n}); }
+inline void bulk_wait() { for (auto& p : pending) std::memcpy(p.dst, p.src, p.n); pending.clear(); }
+}  // namespace emu
+
+inline void __syncwarp(unsigned mask = 0xffffffffu) { emu::exchange(mask, 0, [](auto*, unsigned) { return 0ull; }); }
+inline unsigned __ballot_sync(unsigned mask, int p)
+{
+    return (unsigned)emu::exchange(mask, p != 0, [mask](unsigned long long* v, unsigned) {
+        unsigned long long b = 0;
+        for (int l = 0; l < 32; ++l) if (((mask >> l) & 1u) && v[l]) b |= 1ull << l;
+        return b; });
+}
+inline int __any_sync(unsigned mask, int p) { return __ballot_sync(mask, p) != 0; }
+inline int __all_sync(unsigned mask, int p) { return __ballot_sync(mask, p) == mask; }
+inline unsigned __reduce_add_sync(unsigned mask, unsigned v)
+{
+    return (unsigned)emu::exchange(mask, v, [mask](unsigned long long* x, unsigned) {
+        unsigned s = 0;
+        for (int l = 0; l < 32; ++l) if ((mask >> l) & 1u) s += (unsigned)x[l];
+        return (unsigned long long)s; });
+}
+template <class T> T __shfl_sync(unsigned mask, T v, int src, int width = 32)
+{
+    return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, src, width](unsigned long long* x, unsigned lane) {
+        const unsigned s = (lane & ~(unsigned)(width - 1)) | ((unsigned)src & (unsigned)(width - 1));
+        return x[emu::src_ok(mask, s)]; }));
+}
+template <class T> T __shfl_up_sync(unsigned mask, T v, unsigned d, int width = 32)
+{
+    return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, d, width](unsigned long long* x, unsigned lane) {
+        const unsigned s = (lane & (unsigned)(width - 1)) >= d ? lane - d : lane;
+        return x[emu::src_ok(mask, s)]; }));
+}
+template <class T> T __shfl_down_sync(unsigned mask, T v, unsigned d, int width = 32)
+{
+    return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, d, width](unsigned long long* x, unsigned lane) {
+        const unsigned s = (lane & (unsigned)(width - 1)) + d < (unsigned)width ? lane + d : lane;
+        return x[emu::src_ok(mask, s)]; }));
+}
+template <class T> T __shfl_xor_sync(unsigned mask, T v, int m, int width = 32)
+{
+    return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, m, width](unsigned long long* x, unsigned lane) {
+        unsigned s = lane ^ (unsigned)m;
+        if ((s & ~(unsigned)(width - 1)) > (lane & ~(unsigned)(width - 1))) s = lane;
+        return x[emu::src_ok(mask, s)]; }));
+}
+inline int __popc(unsigned v) { return __builtin_popcount(v); }
+inline int __popcll(unsigned long long v) { return __builtin_popcountll(v); }
+inline int __ffs(int v) { return __builtin_ffs(v); }
+inline int __ffsll(long long v) { return __builtin_ffsll(v); }
+inline int __clz(int v) { return v == 0 ? 32 : __builtin_clz((unsigned)v); }
+inline int __clzll(long long v) { return v == 0 ? 64 : __builtin_clzll((unsigned long long)v); }
+inline unsigned __umulhi(unsigned a, unsigned b) { return (unsigned)(((unsigned long long)a * b) >> 32); }
+inline unsigned __brev(unsigned v) { unsigned r = 0; for (int i = 0; i < 32; ++i) r |= ((v >> i) & 1u) << (31 - i); return r; }
+template <class T> T atomicOr(T* p, T v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
+template <class T> T atomicAnd(T* p, T v) { return __atomic_fetch_and(p, v, __ATOMIC_SEQ_CST); }
+template <class T> T atomicAdd(T* p, T v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+template <class T> T atomicExch(T* p, T v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
+template <class T> T atomicCAS(T* p, T c, T v) { __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST); return c; }
+template <class T> T atomicMin(T* p, T v) { T o = __atomic_load_n(p, __ATOMIC_SEQ_CST); while (v < o && !__atomic_compare_exchange_n(p, &o, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {} return o; }
+template <class T> T atomicMax(T* p, T v) { T o = __atomic_load_n(p, __ATOMIC_SEQ_CST); while (v > o && !__atomic_compare_exchange_n(p, &o, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {} return o; }
+inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void __threadfence_system() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void __nanosleep(unsigned) {}
+inline unsigned long long __cvta_generic_to_shared(const void* p) { return (unsigned long long)(uintptr_t)p; }
