@@ -4,45 +4,12 @@
 // warps with teams of L lanes, every ply's outputs kept (ring of S rows) and
 // written to <out>.{action,reward,done,ply,mask,stats} for comparison with
 // the oracle.
-//   env_on_host N S L wpb gpf blocks seed out
-#include <thread>
-#include <memory>
-#include <string>
-#include "cuda_runtime.h"
-thread_local uint3 threadIdx, blockIdx;
-dim3 blockDim, gridDim;
-namespace emu {
-Warp* warps = nullptr;
-unsigned char* smem_base = nullptr;
-size_t smem_per_block = 0;
-thread_local std::vector<Pending> pending;
-}
+//   env_on_host N S L wpb gpf blocks seed out [actions]
+// With an actions file ([S][N] int16, -1 = the random policy) the plain
+// path runs instead: one k_env_step launch per ply (teams of 32 lanes, 4
+// warps per block) with those actions supplied.
+#include "host_launch.h"
 #include "env_dev.cu"
-
-template <class F>
-static void launch(unsigned blocks, unsigned threads, size_t smem, F body)
-{
-    gridDim = dim3{blocks, 1, 1};
-    blockDim = dim3{threads, 1, 1};
-    std::unique_ptr<emu::Warp[]> w(new emu::Warp[(size_t)blocks * 32]);
-    std::vector<unsigned char> sm((size_t)blocks * smem + 64);
-    std::memset(sm.data(), 0xA5, sm.size());   // uninitialised shared memory
-    emu::warps = w.get();
-    emu::smem_base = reinterpret_cast<unsigned char*>(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
-    emu::smem_per_block = smem;
-    std::vector<std::thread> th;
-    for (unsigned b = 0; b < blocks; ++b)
-        for (unsigned t = 0; t < threads; ++t)
-            th.emplace_back([=] { threadIdx = uint3{t, 0, 0}; blockIdx = uint3{b, 0, 0}; body(); emu::bulk_wait(); });
-    for (auto& x : th) x.join();
-}
-
-template <class T> static void dump(const std::string& path, const T* p, size_t n)
-{
-    FILE* f = std::fopen(path.c_str(), "wb");
-    std::fwrite(p, sizeof(T), n, f);
-    std::fclose(f);
-}
 
 template <int L>
 static void run(EnvArgs a, int32_t* queue, int S, int gpf, int wpb, int blocks, int16_t* act, int8_t* rew, uint8_t* done,
@@ -75,7 +42,20 @@ int main(int argc, char** argv)
     std::vector<int16_t> act((size_t)S * N), ply((size_t)S * N);
     std::vector<int8_t> rew((size_t)S * N);
     std::vector<uint8_t> done((size_t)S * N), mask((size_t)S * N * kMaskBytes);
-    if (L == 8) run<8>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
+    if (argc > 9) {
+        const std::vector<int16_t> given = load<int16_t>(argv[9]);
+        if ((long long)given.size() != (long long)S * N) { std::fprintf(stderr, "actions size\n"); return 2; }
+        for (int j = 0; j < S; ++j) {
+            const size_t o = (size_t)j * N;
+            const int16_t* gv = given.data() + o;
+            int16_t* ao = act.data() + o;
+            int8_t* ro = rew.data() + o;
+            uint8_t* dn = done.data() + o;
+            int16_t* po = ply.data() + o;
+            uint8_t* mo = mask.data() + o * kMaskBytes;
+            launch((N + 3) / 4, 128, 4 * sizeof(SmemGame), [=] { k_env_step<32>(a, gv, ao, ro, dn, po, mo); });
+        }
+    } else if (L == 8) run<8>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
     else if (L == 4) run<4>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
     else if (L == 16) run<16>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
     else run<32>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());

@@ -43,6 +43,8 @@ struct int4 { int x, y, z, w; };
 struct int2 { int x, y; };
 inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
 inline uint2 make_uint2(unsigned a, unsigned b) { return uint2{a, b}; }
+inline int4 make_int4(int a, int b, int c, int d) { return int4{a, b, c, d}; }
+inline int2 make_int2(int a, int b) { return int2{a, b}; }
 using std::min;
 using std::max;
 typedef struct CUstream_st* cudaStream_t;
@@ -62,6 +64,15 @@ struct Warp {
     std::condition_variable cv;
     std::map<unsigned, Rendezvous> rv;
 };
+struct Block {                    // __syncthreads: every thread of the block that has not returned
+    std::mutex m;
+    std::condition_variable cv;
+    unsigned arrived = 0, exited = 0;
+    unsigned long long gen = 0;
+    std::map<int, void*> statics;  // the block's static __shared__ variables, by source line
+    ~Block() { for (auto& kv : statics) std::free(kv.second); }
+};
+extern Block* blocks;             // [blocks], allocated per launch
 extern Warp* warps;              // [blocks][32 warps], allocated per launch
 extern unsigned char* smem_base;  // [blocks][smem_per_block]
 extern size_t smem_per_block;
@@ -174,6 +185,61 @@ template <class T> T atomicExch(T* p, T v) { return __atomic_exchange_n(p, v, __
 template <class T> T atomicCAS(T* p, T c, T v) { __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST); return c; }
 template <class T> T atomicMin(T* p, T v) { T o = __atomic_load_n(p, __ATOMIC_SEQ_CST); while (v < o && !__atomic_compare_exchange_n(p, &o, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {} return o; }
 template <class T> T atomicMax(T* p, T v) { T o = __atomic_load_n(p, __ATOMIC_SEQ_CST); while (v > o && !__atomic_compare_exchange_n(p, &o, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {} return o; }
+namespace emu {
+// A static __shared__ variable: one object per block (first use allocates it,
+// filled with garbage like uninitialised shared memory).
+template <class T> T* block_static(int key)
+{
+    Block& B = blocks[blockIdx.x];
+    std::lock_guard<std::mutex> lk(B.m);
+    auto it = B.statics.find(key);
+    if (it == B.statics.end()) {
+        void* p = std::aligned_alloc(64, (sizeof(T) + 63) / 64 * 64);
+        std::memset(p, 0xA5, sizeof(T));
+        it = B.statics.emplace(key, p).first;
+    }
+    return reinterpret_cast<T*>(it->second);
+}
+}  // namespace emu
+inline void __syncthreads()
+{
+    emu::Block& B = emu::blocks[blockIdx.x];
+    std::unique_lock<std::mutex> lk(B.m);
+    const unsigned long long my = B.gen;
+    if (++B.arrived + B.exited == blockDim.x) {
+        B.arrived = 0;
+        B.gen++;
+        B.cv.notify_all();
+    } else if (!B.cv.wait_for(lk, std::chrono::seconds(20), [&] { return B.gen != my; })) {
+        emu::fail("__syncthreads never completed", 0);
+    }
+}
+namespace emu {
+inline void thread_exit()         // a returned thread no longer holds up __syncthreads
+{
+    Block& B = blocks[blockIdx.x];
+    std::lock_guard<std::mutex> lk(B.m);
+    ++B.exited;
+    if (B.arrived > 0 && B.arrived + B.exited == blockDim.x) {
+        B.arrived = 0;
+        B.gen++;
+        B.cv.notify_all();
+    }
+}
+}  // namespace emu
+inline float __fdiv_rn(float a, float b) { return a / b; }
+inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
+inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }
+inline double __dadd_rn(double a, double b) { return a + b; }
+inline double __dmul_rn(double a, double b) { return a * b; }
+inline double __ddiv_rn(double a, double b) { return a / b; }
+inline double __longlong_as_double(long long v) { double d; std::memcpy(&d, &v, 8); return d; }
+inline long long __double_as_longlong(double d) { long long v; std::memcpy(&v, &d, 8); return v; }
+// runtime calls reached by host helpers next to the kernels
+enum { cudaSuccess = 0 };
+inline cudaError_t cudaGetDevice(int* d) { *d = 0; return 0; }
+inline cudaError_t cudaGetLastError() { return 0; }
+template <class K> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, K, int, size_t) { *n = 1; return 0; }
 inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void __threadfence_system() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void __nanosleep(unsigned) {}
