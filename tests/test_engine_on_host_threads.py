@@ -1,8 +1,8 @@
 """The CUDA kernels' source run on host threads under sanitizers.
 
 compute-sanitizer is not available to this project, so the device code of
-the env (csrc/engine.cuh, the reset, plain and persistent step kernels of
-csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
+the env (csrc/engine.cuh; the reset, pin, plain, persistent and recording
+step and history-position kernels of csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
 rollouts (k_roots, k_draw_samples, k_rollout_flat) and of the search
 (k_search_prep, k_search_offsets, k_search_rollouts, k_search_policy) is
 also compiled with g++ against a host stand-in for the CUDA features it uses
@@ -52,14 +52,14 @@ def _host_source(text):
 
 def _device_part(name):
     """The kernels of a .cu file without its C entry points: env.cu up to its
-    snapshot section (the rest is host code), obs.cu and search.cu up to
-    their first extern "C" function."""
+    host helpers (env_args onwards), obs.cu and search.cu up to their first
+    extern "C" function."""
     text = open(os.path.join(CSRC, name)).read().replace('#include "host_common.h"', '#include "stratego.h"')
     lines = text.split("\n")
     keep = lambda l: True
     if name == "env.cu":
         start = next(i for i, l in enumerate(lines) if l.startswith("namespace {"))
-        end = next(i for i, l in enumerate(lines) if l.startswith("// ") and "snapshots" in l and "-----" in l)
+        end = next(i for i, l in enumerate(lines) if l.startswith("EnvArgs env_args("))
         pre = [l for l in lines[:start] if (l.startswith("#include") or l.startswith("using namespace")) and keep(l)]
         return "\n".join(pre + lines[start:end]) + "\n}  // namespace\n"
     end = next(i for i, l in enumerate(lines) if l.startswith('extern "C"'))
@@ -319,3 +319,44 @@ def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, san):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
     mask = np.fromfile(out + ".mask", np.uint8).reshape(S, N, oracle.MASK_BYTES)
     np.testing.assert_array_equal(mask, ref["mask"])
+
+
+@pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
+def test_reset_sources_and_history_under_sanitizers(tmp_path, san):
+    # history on, a mirrored setup pool, two pinned slots (a forced flag
+    # capture and a mid-game position), the recording persistent step on two
+    # blocks, then positions rebuilt at four past steps
+    from tests.helpers import BOMB, FLAG, MINER, SERGEANT, make_position, sq
+    flags, env = SANITIZERS[san]
+    exe = _build(str(tmp_path), flags, "env_sources", driver="env_sources_on_host.cpp")
+    N, S, H, seed, M = 16, 200, 200, 23, 3
+    pool = np.zeros((2, M, 40), np.uint8)
+    for m in range(M):
+        t = oracle.setup_types(3000, m)
+        pool[0, m], pool[1, m] = t[:40], t[40:]
+    g = oracle.play_games(72, 1)
+    mid = oracle.replay_positions(g["setups"], g["actions"], np.array([0]),
+                                  np.array([min(200, g["lengths"][0] - 1)], np.int16))[0]
+    forced = make_position([(0, MINER, sq("e8"), 0), (0, BOMB, sq("d8"), 0), (0, BOMB, sq("f8"), 0),
+                            (0, BOMB, sq("e7"), 0), (0, FLAG, sq("a1"), 0), (1, FLAG, sq("e9"), 0),
+                            (1, SERGEANT, sq("j9"), 0)], ply=300, battleless=12)
+    pins = {3: forced, 7: mid}
+    inp, out = str(tmp_path / "in"), str(tmp_path / "o")
+    pool.tofile(inp + ".pool")
+    np.stack([pins[i] for i in sorted(pins)]).tofile(inp + ".pins")
+    np.array(sorted(pins), np.int32).tofile(inp + ".idx")
+    steps = [200, 150, 60, 0]
+    _run_driver(exe, [inp, out, N, S, 8, 2, 1, 2, seed, H, M, 1, len(pins)] + steps, env,
+                known_ply_races(str(tmp_path / "src")))
+    ref = oracle.env_run(seed, N, S, pool=pool, mirror=True, episode0=1, pins=pins)
+    for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
+        np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
+    np.testing.assert_array_equal(np.fromfile(out + ".mask", np.uint8).reshape(S, N, oracle.MASK_BYTES), ref["mask"])
+    np.testing.assert_array_equal(np.fromfile(out + ".stats", np.uint32).reshape(N, 8), ref["stats"])
+    for t in steps:
+        status = np.fromfile(out + ".hist%d.status" % t, np.uint8)
+        pos = np.fromfile(out + ".hist%d.pos" % t, np.uint8).reshape(N, oracle.POS_BYTES)
+        assert (status == 0).all(), (t, status)
+        fin = oracle.env_run(seed, N, t, want_mask=False, want_final=True, pool=pool, mirror=True, episode0=1,
+                             pins=pins)["final"]
+        np.testing.assert_array_equal(pos, fin, err_msg="step %d" % t)
