@@ -153,21 +153,36 @@ def _run_and_compare(exe, tmp, N, S, L, wpb, gpf, blocks, seed, env=None):
 
 
 @pytest.fixture(scope="module")
-def tsan_exe(tmp_path_factory):
-    tmp = str(tmp_path_factory.mktemp("tsan"))
-    return _build(tmp, ["-fsanitize=thread"], "env_tsan"), tmp
+def built(tmp_path_factory):
+    """build(driver, flags) -> (executable, prepared source dir), each
+    (driver, flags) pair compiled once per test module."""
+    cache = {}
+
+    def get(driver, flags):
+        key = (driver, tuple(flags))
+        if key not in cache:
+            tmp = str(tmp_path_factory.mktemp(driver.split(".")[0]))
+            cache[key] = (_build(tmp, list(flags), "exe", driver=driver), os.path.join(tmp, "src"))
+        return cache[key]
+    return get
+
+
+@pytest.fixture(scope="module")
+def tsan_exe(built):
+    exe, src = built("env_on_host.cpp", ["-fsanitize=thread"])
+    return exe, os.path.dirname(src)
 
 
 @pytest.mark.parametrize("L,wpb,gpf,blocks", [(8, 1, 1, 1), (4, 1, 2, 1), (16, 2, 1, 2), (32, 2, 1, 1)])
 def test_step_kernel_under_threadsanitizer(tsan_exe, L, wpb, gpf, blocks):
     exe, tmp = tsan_exe
-    _run_and_compare(exe, tmp, 12, 160, L, wpb, gpf, blocks, 7, env={"TSAN_OPTIONS": "halt_on_error=0"})
+    _run_and_compare(exe, tmp, 8, 120, L, wpb, gpf, blocks, 7, env={"TSAN_OPTIONS": "halt_on_error=0"})
 
 
-def test_step_kernel_under_address_and_ub_sanitizers(tmp_path):
-    exe = _build(str(tmp_path), ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"], "env_asan")
+def test_step_kernel_under_address_and_ub_sanitizers(tmp_path, built):
+    exe, _ = built("env_on_host.cpp", SANITIZERS[1][0])
     for L, wpb, gpf, blocks in ((8, 2, 1, 2), (4, 1, 1, 1)):
-        _run_and_compare(exe, str(tmp_path), 12, 200, L, wpb, gpf, blocks, 11,
+        _run_and_compare(exe, str(tmp_path), 8, 150, L, wpb, gpf, blocks, 11,
                          env={"ASAN_OPTIONS": "detect_leaks=0"})
 
 
@@ -208,12 +223,12 @@ SANITIZERS = [
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
-def test_observation_kernels_under_sanitizers(tmp_path, san):
+def test_observation_kernels_under_sanitizers(tmp_path, built, san):
     # k_replay (chunks of 4 items per warp) then k_obs_emit: planes, bf16
     # planes and masks of every item, the acting or a given player's view;
     # two items that cannot be replayed come back with status 1 and zeros
     flags, env = SANITIZERS[san]
-    exe = _build(str(tmp_path), flags, "obs", driver="obs_on_host.cpp")
+    exe, src = built("obs_on_host.cpp", flags)
     g = oracle.play_games(41, 6)
     rng = np.random.default_rng(3)
     B = 30
@@ -248,13 +263,13 @@ def test_observation_kernels_under_sanitizers(tmp_path, san):
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
-def test_rollout_kernels_under_sanitizers(tmp_path, san):
+def test_rollout_kernels_under_sanitizers(tmp_path, built, san):
     # k_roots, then k_rollout_flat on two resident blocks striding over the
     # units (each team's chase store reused from unit to unit), with samples
     # drawn in the kernel or ahead by k_draw_samples, uniform and magnet
     # rollout policies
     flags, env = SANITIZERS[san]
-    exe = _build(str(tmp_path), flags, "rollout", driver="rollout_on_host.cpp")
+    exe, src = built("rollout_on_host.cpp", flags)
     g = oracle.play_games(43, 4)
     rng = np.random.default_rng(5)
     games = np.repeat(np.arange(4), 2).astype(np.int32)
@@ -273,13 +288,13 @@ def test_rollout_kernels_under_sanitizers(tmp_path, san):
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
-def test_search_kernels_under_sanitizers(tmp_path, san):
+def test_search_kernels_under_sanitizers(tmp_path, built, san):
     # k_search_prep, the single-block offsets scan (__syncthreads), samples
     # drawn ahead, k_search_rollouts on two resident blocks and the policy
     # update; the host's exp and log stand in for the device's, so pi is
     # compared within the GPU tests' 1e-12 relative bound
     flags, env = SANITIZERS[san]
-    exe = _build(str(tmp_path), flags, "search", driver="search_on_host.cpp")
+    exe, src = built("search_on_host.cpp", flags)
     g = oracle.play_games(47, 3)
     rng = np.random.default_rng(5)
     games = np.repeat(np.arange(3), 2).astype(np.int32)
@@ -290,7 +305,7 @@ def test_search_kernels_under_sanitizers(tmp_path, san):
     pos.tofile(inp + ".pos")
     for rflags in (oracle.ALL_RULES, oracle.ALL_RULES | oracle.ROLLOUT_MAGNET):
         out = str(tmp_path / ("out%d" % rflags))
-        _run_driver(exe, [inp, P, S, depth, seed, 2, rflags, out], env, known_ply_races(str(tmp_path / "src")))
+        _run_driver(exe, [inp, P, S, depth, seed, 2, rflags, out], env, known_ply_races(src))
         ref = oracle.search(pos, S, depth, seed, flags=rflags)
         M = oracle.SEARCH_MAX_MOVES
         for k, dt, shape in (("n_moves", np.int32, (P,)), ("actions", np.int16, (P, M)),
@@ -301,11 +316,11 @@ def test_search_kernels_under_sanitizers(tmp_path, san):
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
-def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, san):
+def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, built, san):
     # the plain path (one k_env_step launch per ply) with actions supplied for
     # most slots and plies and the random policy for the rest
     flags, env = SANITIZERS[san]
-    exe = _build(str(tmp_path), flags, "env_plain")
+    exe, src = built("env_on_host.cpp", flags)
     N, S, seed = 8, 60, 5
     ref = oracle.env_run(seed, N, S)
     acts = ref["action"].astype(np.int16)
@@ -314,7 +329,7 @@ def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, san):
     out = str(tmp_path / "o")
     r = subprocess.run([exe, str(N), str(S), "32", "4", "1", "1", str(seed), out, str(tmp_path / "acts")],
                        capture_output=True, text=True, timeout=900, env=dict(os.environ, **env))
-    _check_report(r, known_ply_races(str(tmp_path / "src")))
+    _check_report(r, known_ply_races(src))
     for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
     mask = np.fromfile(out + ".mask", np.uint8).reshape(S, N, oracle.MASK_BYTES)
@@ -322,13 +337,13 @@ def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, san):
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
-def test_reset_sources_and_history_under_sanitizers(tmp_path, san):
+def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
     # history on, a mirrored setup pool, two pinned slots (a forced flag
     # capture and a mid-game position), the recording persistent step on two
     # blocks, then positions rebuilt at four past steps
     from tests.helpers import BOMB, FLAG, MINER, SERGEANT, make_position, sq
     flags, env = SANITIZERS[san]
-    exe = _build(str(tmp_path), flags, "env_sources", driver="env_sources_on_host.cpp")
+    exe, src = built("env_sources_on_host.cpp", flags)
     N, S, H, seed, M = 16, 200, 200, 23, 3
     pool = np.zeros((2, M, 40), np.uint8)
     for m in range(M):
@@ -347,7 +362,7 @@ def test_reset_sources_and_history_under_sanitizers(tmp_path, san):
     np.array(sorted(pins), np.int32).tofile(inp + ".idx")
     steps = [200, 150, 60, 0]
     _run_driver(exe, [inp, out, N, S, 8, 2, 1, 2, seed, H, M, 1, len(pins)] + steps, env,
-                known_ply_races(str(tmp_path / "src")))
+                known_ply_races(src))
     ref = oracle.env_run(seed, N, S, pool=pool, mirror=True, episode0=1, pins=pins)
     for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
