@@ -2,7 +2,9 @@
 // draw-ahead k_draw_samples when asked, k_rollout_flat on a grid of `fb`
 // resident blocks striding over the units) on host threads through
 // include/cuda_runtime.h of this directory, on P positions read from
-// <in>.pos, and writes <out>.{tallies,status}.
+// <in>.pos, and writes <out>.{tallies,status}; then st_belief_sample's
+// k_belief (a block per position, __syncthreads) into <out>.types and
+// st_positions_mask's k_positions_mask into <out>.{mask,n_legal,two_square}.
 //   rollout_on_host in P K depth seed draw_ahead fb flags out
 #include "host_launch.h"
 #include "search_dev.cu"
@@ -45,6 +47,22 @@ int main(int argc, char** argv)
            [=] { k_rollout_flat(rp, P, K, depth, k0, k1, nullptr, ty, r, tp, sc); });
     dump(out + ".tallies", tallies.data(), tallies.size());
     dump(out + ".status", status.data(), status.size());
+    std::vector<uint8_t> types((size_t)P * K * 40, 0xEE), bstatus((size_t)P, 0xEE);
+    uint8_t* tp2 = types.data();
+    uint8_t* bs = bstatus.data();
+    launch((unsigned)P, 128, 0, [=] { k_belief(pp, P, K, k0, k1, nullptr, tp2, bs); });
+    dump(out + ".types", types.data(), types.size());
+    std::vector<uint8_t> mask((size_t)P * kMaskBytes, 0xEE), two((size_t)P, 0xEE), mstatus((size_t)P, 0xEE);
+    std::vector<int32_t> n_legal((size_t)P, -7);
+    uint8_t* mp = mask.data();
+    uint8_t* twp = two.data();
+    uint8_t* msp = mstatus.data();
+    int32_t* nlp = n_legal.data();
+    launch((P + kRootWarps - 1) / kRootWarps, 32 * kRootWarps, kRootWarps * sizeof(RolloutSmem),
+           [=] { k_positions_mask(pp, P, r, mp, nlp, twp, msp); });
+    dump(out + ".mask", mask.data(), mask.size());
+    dump(out + ".n_legal", n_legal.data(), n_legal.size());
+    dump(out + ".two_square", two.data(), two.size());
     std::printf("done\n");
     return 0;
 }

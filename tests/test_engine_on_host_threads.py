@@ -3,7 +3,8 @@
 compute-sanitizer is not available to this project, so the device code of
 the env (csrc/engine.cuh; the reset, pin, plain, persistent and recording
 step and history-position kernels of csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
-rollouts (k_roots, k_draw_samples, k_rollout_flat) and of the search
+belief samples and rollouts (k_belief, k_roots, k_draw_samples,
+k_rollout_flat), of the snapshot masks (k_positions_mask) and of the search
 (k_search_prep, k_search_offsets, k_search_rollouts, k_search_policy) is
 also compiled with g++ against a host stand-in for the CUDA features it uses
 (tests/simt_host: one std::thread per lane, warp collectives as rendezvous
@@ -267,7 +268,7 @@ def test_rollout_kernels_under_sanitizers(tmp_path, built, san):
     # k_roots, then k_rollout_flat on two resident blocks striding over the
     # units (each team's chase store reused from unit to unit), with samples
     # drawn in the kernel or ahead by k_draw_samples, uniform and magnet
-    # rollout policies
+    # rollout policies; then k_belief and k_positions_mask
     flags, env = SANITIZERS[san]
     exe, src = built("rollout_on_host.cpp", flags)
     g = oracle.play_games(43, 4)
@@ -285,6 +286,17 @@ def test_rollout_kernels_under_sanitizers(tmp_path, built, san):
         assert (np.fromfile(out + ".status", np.uint8) == 0).all()
         tallies = np.fromfile(out + ".tallies", np.int32).reshape(P, 4)
         np.testing.assert_array_equal(tallies, oracle.rollout(pos, K, depth, seed, flags=rflags))
+    # the belief samples of st_belief_sample and the masks of st_positions_mask
+    types = np.fromfile(out + ".types", np.uint8).reshape(P, K, 40)
+    np.testing.assert_array_equal(types, oracle.belief_sample(pos, K, seed))
+    mask = np.fromfile(out + ".mask", np.uint8).reshape(P, oracle.MASK_BYTES)
+    n_legal = np.fromfile(out + ".n_legal", np.int32)
+    two = np.fromfile(out + ".two_square", np.uint8)
+    for i in range(P):
+        moves = oracle.legal_moves(pos[i])
+        bits = np.unpackbits(mask[i], bitorder="little")
+        assert set(np.nonzero(bits)[0]) == set(moves.tolist()) and n_legal[i] == len(moves)
+        assert two[i] == oracle.two_square_applies(pos[i])
 
 
 @pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
