@@ -5,7 +5,9 @@
 // recording persistent step (k_env_run<L, true>), then the positions at
 // each queried step (k_env_hist_positions).  Inputs <in>.pool ([2][M][40]),
 // <in>.pins ([n][784]) and <in>.idx ([n] int32); outputs
-// <out>.{action,reward,done,ply,mask,stats} and <out>.hist<t>.{pos,status}.
+// <out>.{action,reward,done,ply,mask,stats}, <out>.hist<t>.{pos,status},
+// <out>.steps<t>.{action,done,reward} (t before now) and <out>.export (the
+// snapshots of slots N-1 .. 0 now, k_env_export).
 //   env_sources_on_host in out N S L wpb gpf blocks seed H M mirror n t...
 #include "host_launch.h"
 #include "env_dev.cu"
@@ -93,6 +95,28 @@ int main(int argc, char** argv)
         launch((N + 3) / 4, 128, 4 * sizeof(RolloutSmem), [=] { k_env_hist_positions(a, q, hpp, hsp, ep, sp); });
         dump(out + ".hist" + std::to_string(t) + ".pos", hp.data(), hp.size());
         dump(out + ".hist" + std::to_string(t) + ".status", hs.data(), hs.size());
+        if (t < d_now) {   // the record of step t
+            std::vector<int16_t> ha((size_t)N);
+            std::vector<uint8_t> hd((size_t)N), hm((size_t)N);
+            std::vector<int8_t> hr((size_t)N);
+            int16_t* hap = ha.data();
+            uint8_t* hdp = hd.data();
+            int8_t* hrp = hr.data();
+            uint8_t* hmp = hm.data();
+            launch((N + 255) / 256, 256, 0, [=] { k_env_hist_steps(N, q, hap, hdp, hrp, hmp); });
+            dump(out + ".steps" + std::to_string(t) + ".action", ha.data(), ha.size());
+            dump(out + ".steps" + std::to_string(t) + ".done", hd.data(), hd.size());
+            dump(out + ".steps" + std::to_string(t) + ".reward", hr.data(), hr.size());
+        }
+    }
+    {   // snapshots of every slot now
+        std::vector<int32_t> idx((size_t)N);
+        for (int g = 0; g < N; ++g) idx[(size_t)g] = N - 1 - g;
+        std::vector<st_position> snap((size_t)N);
+        const int32_t* ip = idx.data();
+        st_position* sp = snap.data();
+        launch((N + 3) / 4, 128, 4 * sizeof(SmemGame), [=] { k_env_export(a, ip, N, sp); });
+        dump(out + ".export", snap.data(), snap.size());
     }
     std::printf("status %d %d\ndone\n", status[0], status[1]);
     return 0;

@@ -2,7 +2,7 @@
 
 compute-sanitizer is not available to this project, so the device code of
 the env (csrc/engine.cuh; the reset, pin, plain, persistent and recording
-step and history-position kernels of csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
+step, history-position, history-record and export kernels of csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
 belief samples and rollouts (k_belief, k_roots, k_draw_samples,
 k_rollout_flat), of the snapshot masks (k_positions_mask) and of the search
 (k_search_prep, k_search_offsets, k_search_rollouts, k_search_policy) is
@@ -352,7 +352,8 @@ def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, built, san)
 def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
     # history on, a mirrored setup pool, two pinned slots (a forced flag
     # capture and a mid-game position), the recording persistent step on two
-    # blocks, then positions rebuilt at four past steps
+    # blocks, then positions rebuilt at four past steps, the records of those
+    # steps and the snapshots of every slot (k_env_export)
     from tests.helpers import BOMB, FLAG, MINER, SERGEANT, make_position, sq
     flags, env = SANITIZERS[san]
     exe, src = built("env_sources_on_host.cpp", flags)
@@ -387,3 +388,10 @@ def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
         fin = oracle.env_run(seed, N, t, want_mask=False, want_final=True, pool=pool, mirror=True, episode0=1,
                              pins=pins)["final"]
         np.testing.assert_array_equal(pos, fin, err_msg="step %d" % t)
+        if t < S:
+            for k, dt in (("action", np.int16), ("done", np.uint8), ("reward", np.int8)):
+                np.testing.assert_array_equal(np.fromfile(out + ".steps%d.%s" % (t, k), dt), ref[k][t],
+                                              err_msg="step record %d %s" % (t, k))
+    now = oracle.env_run(seed, N, S, want_mask=False, want_final=True, pool=pool, mirror=True, episode0=1,
+                         pins=pins)["final"]
+    np.testing.assert_array_equal(np.fromfile(out + ".export", np.uint8).reshape(N, oracle.POS_BYTES), now[::-1])
