@@ -4,7 +4,8 @@ compute-sanitizer is not available to this project, so the device code of
 the env (csrc/engine.cuh; the reset, pin, plain, persistent and recording
 step, history-position, history-record and export kernels of csrc/env.cu), of the observation planes (k_replay, k_obs_emit), of the
 belief samples and rollouts (k_belief, k_roots, k_draw_samples,
-k_rollout_flat), of the snapshot masks (k_positions_mask) and of the search
+k_rollout_flat), of the snapshot masks (k_positions_mask), of a serving
+batch (k_serve_roots, k_serve_rollouts) and of the search
 (k_search_prep, k_search_offsets, k_search_rollouts, k_search_policy) is
 also compiled with g++ against a host stand-in for the CUDA features it uses
 (tests/simt_host: one std::thread per lane, warp collectives as rendezvous
@@ -63,7 +64,10 @@ def _device_part(name):
         end = next(i for i, l in enumerate(lines) if l.startswith("EnvArgs env_args("))
         pre = [l for l in lines[:start] if (l.startswith("#include") or l.startswith("using namespace")) and keep(l)]
         return "\n".join(pre + lines[start:end]) + "\n}  // namespace\n"
-    end = next(i for i, l in enumerate(lines) if l.startswith('extern "C"'))
+    if name == "serve.cu":   # the kernels' namespace only (the server's host state follows)
+        end = next(i for i, l in enumerate(lines) if l.startswith("}  // namespace")) + 1
+    else:
+        end = next(i for i, l in enumerate(lines) if l.startswith('extern "C"'))
     return "\n".join(l for l in lines[:end] if keep(l)) + "\n"
 
 
@@ -74,7 +78,8 @@ def _prepare(dst, edit=None):
             text = edit(f, text)
         with open(os.path.join(dst, f), "w") as o:
             o.write(text)
-    for f, dev in (("env.cu", "env_dev.cu"), ("obs.cu", "obs_dev.cu"), ("search.cu", "search_dev.cu")):
+    for f, dev in (("env.cu", "env_dev.cu"), ("obs.cu", "obs_dev.cu"), ("search.cu", "search_dev.cu"),
+                   ("serve.cu", "serve_dev.cu")):
         with open(os.path.join(dst, dev), "w") as o:
             o.write(_host_source(_device_part(f)))
 
@@ -395,3 +400,38 @@ def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
     now = oracle.env_run(seed, N, S, want_mask=False, want_final=True, pool=pool, mirror=True, episode0=1,
                          pins=pins)["final"]
     np.testing.assert_array_equal(np.fromfile(out + ".export", np.uint8).reshape(N, oracle.POS_BYTES), now[::-1])
+
+
+@pytest.mark.parametrize("san", [0, 1], ids=["tsan", "asan_ubsan"])
+def test_serving_batch_under_sanitizers(tmp_path, built, san):
+    # one batch of the server: k_serve_roots, then k_serve_rollouts on two
+    # resident blocks; each request's last unit publishes its tallies and
+    # completion word; a request with no samples is published by the roots
+    # kernel, one with a corrupt position with -1 tallies
+    flags, env = SANITIZERS[san]
+    exe, src = built("serve_on_host.cpp", flags)
+    g = oracle.play_games(44, 3)
+    rng = np.random.default_rng(9)
+    games = np.array([0, 1, 2, 0, 1], np.int32)
+    plies = np.array([rng.integers(0, min(300, g["lengths"][k] - 1) + 1) for k in games], np.int16)
+    pos = oracle.replay_positions(g["setups"], g["actions"], games, plies)
+    bad = pos[0].copy()
+    bad[0] = 99
+    pos = np.concatenate([pos, bad[None]])
+    R = len(pos)
+    #                K  depth seed-lo seed-hi stream
+    req = np.array([[9, 200, 77, 0, 5], [0, 12, 78, 0, 6], [13, 20, 79, 1, 7], [5, 1, 80, 0, 8],
+                    [11, 160, 81, 0, 9], [4, 8, 82, 0, 10]], np.int32)
+    inp, out = str(tmp_path / "in"), str(tmp_path / "o")
+    pos.tofile(inp + ".pos")
+    req.tofile(inp + ".req")
+    _run_driver(exe, [inp, R, 2, out], env, known_ply_races(src))
+    tallies = np.fromfile(out + ".tallies", np.int32).reshape(R, 4)
+    np.testing.assert_array_equal(np.fromfile(out + ".done", np.uint32), 1000 + np.arange(R))
+    for i in range(R - 1):
+        K, depth, lo, hi, sid = (int(v) for v in req[i])
+        seed = (hi << 32) | (lo & 0xFFFFFFFF)
+        ref = (oracle.rollout(pos[i:i + 1], K, depth, seed, stream_ids=np.array([sid], np.uint32))[0] if K > 0
+               else np.zeros(4, np.int32))
+        np.testing.assert_array_equal(tallies[i], ref, err_msg="request %d" % i)
+    assert (tallies[R - 1] == -1).all()
