@@ -224,3 +224,65 @@ def test_history_planes_orientation():
     assert x[455, sq("a3")] == 1 and x[455, sq("b3")] == 255
     assert x[456, sq("b2")] == 1 and x[456, sq("a2")] == 255
     assert x[457].sum() == 0
+
+
+# ------------------------------------------------------------------ causes of death, one per case
+
+def _deaths_at(x, square):
+    """(channel, value) of every death channel (131-250) set at `square`."""
+    return sorted((int(c), int(x[c, square])) for c in range(131, 251) if x[c, square])
+
+
+# App. C.1 "Causes of death": the attacker A dies by cause 1 (defender
+# revealed, A lost), 2 (defender revealed, a tie) or 3 (defender hidden, A
+# lost or tied); the defender D dies by cause 4 (D revealed, lost), 5 (D
+# revealed, a tie) or 6 (D hidden).  Channel 131 + 10*(cause-1) + rank index
+# for own pieces, 191 + ... for the opponent's, at the battle square.
+@pytest.mark.parametrize("name,att,dfn,d_flags,red_cause,blue_cause", [
+    ("revealed defender wins", SERGEANT, CAPTAIN, F_REVEALED, 1, None),
+    ("tie with a revealed defender", CAPTAIN, CAPTAIN, F_REVEALED, 2, 5),
+    ("hidden defender wins", SERGEANT, CAPTAIN, 0, 3, None),
+    ("tie with a hidden defender", CAPTAIN, CAPTAIN, 0, 3, 6),
+    ("revealed defender loses", MARSHAL, CAPTAIN, F_REVEALED, None, 4),
+    ("hidden defender loses", MARSHAL, CAPTAIN, 0, None, 6),
+])
+def test_death_cause_of_each_case(name, att, dfn, d_flags, red_cause, blue_cause):
+    pcs = [(0, att, sq("e4"), 0), (0, SCOUT, sq("a2"), 0), (0, FLAG, sq("j1"), 0),
+           (1, dfn, sq("e5"), d_flags), (1, SCOUT, sq("a9"), 0), (1, FLAG, sq("j10"), 0)]
+    red, blue = 0, 40                      # the attacker and the defender are each side's first piece
+    out, x = _planes_after(pcs, [action("e4", "e5")])
+    # the snapshot keeps the cause in flag bits 4-6 and the battle square
+    for pid, cause in ((red, red_cause), (blue, blue_cause)):
+        if cause is None:
+            assert out[160 + pid] & 1 and out[160 + pid] & F_REVEALED, name
+        else:
+            assert not (out[160 + pid] & 1), name
+            assert (out[160 + pid] >> 4) & 7 == cause, name
+            assert out[80 + pid] == sq("e5"), name
+    # blue (the defender's side) to move: own deaths 131.., opponent deaths 191..
+    want_blue = []
+    if blue_cause is not None:
+        want_blue.append((131 + 10 * (blue_cause - 1) + dfn, 1))
+    if red_cause is not None:
+        want_blue.append((191 + 10 * (red_cause - 1) + att, 1))
+    assert _deaths_at(x, sq("e5")) == sorted(want_blue), name
+    # red's view after a quiet blue move: the same deaths with own and opponent swapped
+    out, x = _planes_after(pcs, [action("e4", "e5"), action("a9", "a8")])
+    want_red = []
+    if red_cause is not None:
+        want_red.append((131 + 10 * (red_cause - 1) + att, 1))
+    if blue_cause is not None:
+        want_red.append((191 + 10 * (blue_cause - 1) + dfn, 1))
+    assert _deaths_at(x, sq("e5")) == sorted(want_red), name
+
+
+def test_bomb_death_has_no_death_channel_but_a_capture_plane():
+    # a Miner defuses a revealed Bomb: cause 4 in the snapshot; the death
+    # channels list ten ranks per cause (Bomb dropped), the captured planes
+    # 109-130 keep the Bomb (index 10) on its start square
+    pcs = [(0, MINER, sq("e4"), 0), (0, FLAG, sq("j1"), 0),
+           (1, BOMB, sq("e5"), F_REVEALED), (1, SCOUT, sq("a9"), 0), (1, FLAG, sq("j10"), 0)]
+    out, x = _planes_after(pcs, [action("e4", "e5")])
+    assert not (out[160 + 40] & 1) and (out[160 + 40] >> 4) & 7 == 4
+    assert _deaths_at(x, sq("e5")) == []
+    assert x[109 + 10, 60] == 1           # blue's own captured Bomb at the start square of piece 40 (a7)
