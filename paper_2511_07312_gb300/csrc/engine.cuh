@@ -31,6 +31,7 @@
 // pairs (splitmix64 finalizer over the pair index); a hash equality stands
 // for board equality.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,7 @@ constexpr uint8_t kNone = 0xFF;
 constexpr int kMaskBytes = 1264;
 constexpr int kMaskWordsAlloc = 316;   // the output layout: 1,264 bytes
 constexpr int kSegMax = 25;            // from-square segments (one per lane; 25 of 4 squares for 32 lanes)
+constexpr int kCntBytes = 128;         // per-square move counts: 100 squares padded to 128 bytes
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
 constexpr int kPiWords = 2 * kPiCap;   // each: hash of the chaser's pieces, hash of the chased side's pieces
 constexpr int kRing = 256;             // moves of history per game
@@ -100,15 +102,17 @@ struct __align__(16) SmemGame {
     uint16_t h0, h1;          // actions played 1 and 2 plies ago (0xFFFF none)
     uint8_t flag_pid[2];
     uint8_t scout_pid[2][8];  // the Scouts of each side in piece-id order (kNone after the last)
-    uint8_t pad[2];
-    uint32_t seg_cnt[kSegMax];// moves per from-square segment in G->mask (written with the mask)
+    uint8_t pad[6];
     uint64_t pi_theirs[4];    // chased-side hash of chase positions n_pi-4 .. n_pi-1 (slot i & 3)
     uint64_t pi_mine[4];      // the chaser's hash of the same positions
     uint32_t stat[8];         // counters of the current launch (kept by the env's step loop)
+    uint8_t sq_cnt[kCntBytes];// moves per from-square in G->mask (written with the mask; zero past square 99)
     uint32_t mask[kMaskWordsAlloc];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 2 + 4 * kSegMax + 64 + 32 + 4 * kMaskWordsAlloc,
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 6 + 64 + 32 + kCntBytes + 4 * kMaskWordsAlloc,
               "SmemGame layout");
+static_assert(offsetof(SmemGame, sq_cnt) % 16 == 0 && offsetof(SmemGame, mask) == offsetof(SmemGame, sq_cnt) + kCntBytes,
+              "per-square counts and mask are zeroed as one run of 16-byte words");
 static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
 
@@ -465,10 +469,11 @@ __device__ __forceinline__ Set128 filter_dests(const SmemGame* G, int P, int fro
     return d;
 }
 
-// OR a 128-bit set over to-squares into the mask row of from-square s.
-__device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d)
+// OR bits 0..127 of d into the mask at bit offset base (bit i of d is mask
+// bit base + i); only words that receive a set bit are touched.
+__device__ __forceinline__ void or_bits(uint32_t* mask, int base, Set128 d)
 {
-    const int base = 100 * s, w0 = base >> 5, sh = base & 31;
+    const int w0 = base >> 5, sh = base & 31;
     const uint32_t w[4] = {(uint32_t)d.lo, (uint32_t)(d.lo >> 32), (uint32_t)d.hi, (uint32_t)(d.hi >> 32)};
     uint32_t prev = 0;
 #pragma unroll
@@ -479,6 +484,9 @@ __device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d)
     }
     if (prev) atomicOr(&mask[w0 + 4], prev);
 }
+
+// OR a 128-bit set over to-squares into the mask row of from-square s.
+__device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d) { or_bits(mask, 100 * s, d); }
 
 // ----------------------------------------------------------------- square sets
 constexpr uint64_t col_bits(int c, int half)
@@ -519,7 +527,7 @@ template <int L> struct Seg {
 };
 
 // ----------------------------------------------------------------- move generation
-// Counts (and, if write_mask, records in G->mask and G->seg_cnt) the moves of
+// Counts (and, if write_mask, records in G->mask and G->sq_cnt) the moves of
 // player P.  physical: movement rules only (App. A "Piece details");
 // otherwise the two-square and chasing rules filter as rule_flags says.
 // Team-uniform result.
@@ -527,19 +535,26 @@ template <int L> struct Seg {
 // Non-Scout moves come from four shifted square sets over the whole board;
 // each lane records those of its own segment, one window of at most 21 mask
 // bits per from-square (to-squares s-10, s-1, s+1, s+10 are bits 101s-10,
-// 101s-1, 101s+1, 101s+10).  Scouts take one lane each.  Destinations that
-// a rule may forbid (those of the piece under the two-square rule; all moves
-// while a chase position can recur) go through filter_dests.
+// 101s-1, 101s+1, 101s+10).  Scouts take one lane each; a Scout's row and
+// column slides are one run of mask bits around bit 101s (to-squares s+j on
+// its row are bits 101s+j, those on its column bits 101s+10k).  Destinations
+// that a rule may forbid (those of the piece under the two-square rule; all
+// moves while a chase position can recur) go through filter_dests.
 template <int L>
 __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule_flags, bool physical,
                                       bool write_mask, const uint64_t* pi)
 {
     const Team<L> T;
-    constexpr int SW = Seg<L>::W, NS = Seg<L>::N;
+    constexpr int SW = Seg<L>::W;
     if (write_mask) {
-        uint4* m4 = reinterpret_cast<uint4*>(G->mask);
-        for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
-        if (T.tl < NS) G->seg_cnt[T.tl] = 0;
+        // the per-square counts and the mask are one run of 16-byte words
+        constexpr int kZero = (kCntBytes + 4 * kMaskWordsAlloc) / 16;
+        uint4* z = reinterpret_cast<uint4*>(G->sq_cnt);
+#pragma unroll
+        for (int k = 0; k < (kZero + L - 1) / L; ++k) {
+            const int i = T.tl + k * L;
+            if (i < kZero) z[i] = make_uint4(0, 0, 0, 0);
+        }
     }
     const int ts_pid = G->c.ts_pid[P];
     const bool ts_on = !physical && (rule_flags & kTwoSquare) && ts_pid != kNone && G->c.ts_len[P] == 4 &&
@@ -572,8 +587,12 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             if ((fe >> c) & 1u) d = or128(d, bit128(s + 1));
             if ((fn >> c) & 1u) d = or128(d, bit128(s + 10));
             d = filter_dests(G, P, s, s == ts_from, true, x, pi, d);
-            cnt += popc128(d);
-            if (write_mask) or_row(G->mask, s, d);
+            const int k = popc128(d);
+            cnt += k;
+            if (write_mask) {
+                or_row(G->mask, s, d);
+                G->sq_cnt[s] = (uint8_t)k;
+            }
         }
     } else {
         // the piece under the two-square rule (if in this segment) is the only
@@ -587,8 +606,12 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             if ((fe >> c) & 1u) d = or128(d, bit128(s + 1));
             if ((fn >> c) & 1u) d = or128(d, bit128(s + 10));
             d = filter_dests(G, P, s, true, false, x, pi, d);
-            cnt += popc128(d);
-            if (write_mask) or_row(G->mask, s, d);
+            const int k = popc128(d);
+            cnt += k;
+            if (write_mask) {
+                or_row(G->mask, s, d);
+                G->sq_cnt[s] = (uint8_t)k;
+            }
             moving &= ~ts_bit;
             fe &= ~ts_bit; fw &= ~ts_bit; fn &= ~ts_bit; fs &= ~ts_bit;
         }
@@ -600,6 +623,7 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                 const int s = off + c;
                 uint32_t pat = ((fs >> c) & 1u) | (((fw >> c) & 1u) << 9) | (((fe >> c) & 1u) << 11) |
                                (((fn >> c) & 1u) << 20);
+                G->sq_cnt[s] = (uint8_t)__popc(pat);
                 int base = 101 * s - 10;
                 if (s == 0) { pat >>= 10; base = 0; }   // square 0 has no south or west move
                 const uint64_t v = (uint64_t)pat << (base & 31);
@@ -608,7 +632,6 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             }
         }
     }
-    if (write_mask && cnt && T.tl < NS) atomicAdd(&G->seg_cnt[T.tl], (uint32_t)cnt);
     // Scouts, one per lane: slides along the row and the column, stopping
     // before a lake or an own piece and on the first enemy piece.
     for (int si = T.tl; si < 8; si += L) {
@@ -644,88 +667,23 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                 cnt_sc = popc128(d);
                 if (write_mask) or_row(G->mask, s, d);
             } else if (cnt_sc && write_mask) {
-                // along the row: to-squares s-nw .. s+ne except s, one run of mask
-                // bits around bit 101s
-                const int b = 101 * s - nw;
-                const uint64_t v = (((1ull << (nw + ne + 1)) - 1ull) & ~(1ull << nw)) << (b & 31);
-                if (v) {
-                    atomicOr(&G->mask[b >> 5], (uint32_t)v);
-                    if (v >> 32) atomicOr(&G->mask[(b >> 5) + 1], (uint32_t)(v >> 32));
-                }
-                // along the column: to-squares s+10k, mask bits 101s+10k
-                for (int k = -ns; k <= nn; ++k) {
-                    const int m = 101 * s + 10 * k;
-                    if (k) atomicOr(&G->mask[m >> 5], 1u << (m & 31));
-                }
+                // mask bits 101s+j (row, j in [-nw, ne]) and 101s+10k (column,
+                // k in [-ns, nn]), j, k != 0, as one run of at most 100 bits
+                // starting at bit 101s - a
+                const int a = max(10 * ns, nw);
+                const Set128 every10{0x1004010040100401ull, 0x0100401004010040ull};   // bits 0, 10, ..., 120
+                Set128 v = shl128(and128(every10, range128(0, 10 * (ns + nn) + 1)), a - 10 * ns);
+                v = or128(v, shl128(Set128{lowbits64(nw + ne + 1), 0ull}, a - nw));
+                if (a < 64) v.lo &= ~(1ull << a); else v.hi &= ~(1ull << (a - 64));
+                or_bits(G->mask, 101 * s - a, v);
             }
-            if (write_mask && cnt_sc) atomicAdd(&G->seg_cnt[s / SW], (uint32_t)cnt_sc);
+            if (write_mask && cnt_sc) G->sq_cnt[s] = (uint8_t)cnt_sc;
             cnt += cnt_sc;
         }
     }
     const int total = T.sum(cnt);
     T.sync();
     return total;
-}
-
-// The idx-th set bit (ascending) of G->mask; team-uniform result.  The
-// from-squares of segment j own the consecutive actions
-// [100*W*j, 100*W*(j+1)), so the per-segment counts written with the mask
-// pick the segment first and only its mask words are scanned.
-template <int L>
-__device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
-{
-    const Team<L> T;
-    constexpr int SW = Seg<L>::W, NS = Seg<L>::N;
-    const int t = T.tl;
-    const int cs = t < NS ? (int)G->seg_cnt[t] : 0;
-    int cincl = cs;
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-        const int v = __shfl_up_sync(T.mask, cincl, o, L);
-        if (t >= o) cincl += v;
-    }
-    const uint32_t segs = T.ballot((int)idx >= cincl - cs && (int)idx < cincl);
-    const int g = segs ? __ffs(segs) - 1 : 0;
-    const int local = (int)idx - T.shfl(cincl - cs, g);
-    const int b0 = 100 * SW * g, b1 = min(b0 + 100 * SW, 100 * kSquares);   // the segment's bits: [b0, b1)
-    const int w0 = b0 >> 5, w1 = (b1 - 1) >> 5;                              // its words, inclusive
-    const int nw = w1 - w0 + 1;
-    constexpr int C = (100 * SW / 32 + 2 + L - 1) / L;                       // words per lane
-    uint32_t w[C];
-    int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        const int wi = t * C + j;
-        uint32_t v = wi < nw ? G->mask[w0 + wi] : 0u;
-        if (wi == 0) v &= ~0u << (b0 & 31);                             // bits of the previous row
-        if (wi == nw - 1 && (b1 & 31)) v &= (1u << (b1 & 31)) - 1u;     // bits of the next row
-        w[j] = v;
-        cnt += __popc(v);
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-        const int v = __shfl_up_sync(T.mask, incl, o, L);
-        if (t >= o) incl += v;
-    }
-    const int excl = incl - cnt;
-    const uint32_t own = T.ballot(local >= excl && local < incl);
-    int a = -1;
-    if (own & (1u << t)) {
-        int k = local - excl;
-        int j = 0;
-#pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int ci = __popc(w[i]);
-            if (j == i && k >= ci) { k -= ci; j = i + 1; }
-        }
-        j = min(j, C - 1);
-        uint32_t wj = w[0];
-#pragma unroll
-        for (int i = 1; i < C; ++i) if (j == i) wj = w[i];
-        a = (w0 + t * C + j) * 32 + nth_set_bit(wj, k);
-    }
-    return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
 
 // The four mask words holding from-square s's row (actions 100s .. 100s+99),
@@ -740,6 +698,68 @@ __device__ __forceinline__ int row_words(const SmemGame* G, int s, uint32_t r[4]
     r[3] = G->mask[w + 3] & (hb >= 32 ? ~0u : ((1u << hb) - 1u));
     return w;
 }
+
+// The idx-th set bit (ascending) of G->mask; team-uniform result.  Lane t
+// owns squares [Q*t, Q*t + Q) (Q = 128 / L) and sums their move counts from
+// G->sq_cnt; a scan over the team finds the lane holding move idx, that
+// lane finds the square (per-byte prefix sums of its count words) and then
+// the bit within the square's mask row.
+template <int L>
+__device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
+{
+    const Team<L> T;
+    constexpr int NW = kCntBytes / L / 4;   // count words per lane: 8, 4, 2, 1
+    const int t = T.tl;
+    uint32_t w[NW];
+    if constexpr (NW >= 4) {
+        const uint4* c4 = reinterpret_cast<const uint4*>(G->sq_cnt) + (NW / 4) * t;
+#pragma unroll
+        for (int j = 0; j < NW / 4; ++j) {
+            const uint4 v = c4[j];
+            w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+        }
+    } else if constexpr (NW == 2) {
+        const uint2 v = reinterpret_cast<const uint2*>(G->sq_cnt)[t];
+        w[0] = v.x; w[1] = v.y;
+    } else {
+        w[0] = reinterpret_cast<const uint32_t*>(G->sq_cnt)[t];
+    }
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) sum = (int)__dp4a(w[j], 0x01010101u, (unsigned)sum);
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const int v = __shfl_up_sync(T.mask, incl, o, L);
+        if (t >= o) incl += v;
+    }
+    const uint32_t own = T.ballot((int)idx >= incl - sum && (int)idx < incl);
+    int a = -1;
+    if (own & (1u << t)) {
+        int k = (int)idx - (incl - sum);
+        // the count word holding move k
+        int j = 0;
+        uint32_t wj = w[0];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const int ci = (int)__dp4a(w[i], 0x01010101u, 0u);
+            if (j == i && k >= ci && i + 1 < NW) { k -= ci; j = i + 1; wj = w[i + 1]; }
+        }
+        // the square within it: byte b of pre is the sum of bytes 0..b (at
+        // most 4 x 18 moves, no carries), the first byte above k holds move k
+        const uint32_t pre = wj * 0x01010101u;
+        const int b = (__ffs(__vcmpgtu4(pre, 0x01010101u * (uint32_t)k)) - 1) >> 3;
+        if (b > 0) k -= (int)((pre >> (8 * (b - 1))) & 0xFFu);
+        const int s = 4 * (NW * t + j) + b;
+        uint32_t r[4];
+        const int w0 = row_words(G, s, r);
+        int i = 0;
+        while (i < 3 && k >= __popc(r[i])) { k -= __popc(r[i]); ++i; }
+        a = 32 * (w0 + i) + nth_set_bit(r[i], k);
+    }
+    return T.shfl(a, own ? __ffs(own) - 1 : 0);
+}
+
 
 // The magnet policy's move (Tab. notation rho) from the mask of the player
 // to move: piece number uniform_below(w0, pieces with a legal move) in

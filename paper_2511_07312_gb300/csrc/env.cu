@@ -243,7 +243,9 @@ __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int&
                                              bool async_mask = false)
 {
     PlyResult res;
-    res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = G->c.ply;
+    // the ply index is read by the leader alone, which is the lane that
+    // writes it and the only one whose result is used
+    res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = T.leader() ? G->c.ply : 0;
     illegal = false;
     if (G->c.terminated) return res;
     if (n == 0) {
@@ -284,11 +286,12 @@ __device__ __forceinline__ int reward_of(const PlyResult& r)
 __device__ __forceinline__ void count_result(uint32_t* st, const PlyResult& r)
 {
     st[5] += r.action >= 0;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) st[k] += r.code == k + 1;
-    const int rw = reward_of(r);
-    st[6] += rw > 0;
-    st[7] += rw < 0;
+    if (r.code) {
+        st[r.code - 1] += 1;
+        const int rw = reward_of(r);
+        if (rw > 0) st[6] += 1;
+        else if (rw < 0) st[7] += 1;
+    }
 }
 
 template <int L>
@@ -432,11 +435,13 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             // that every engine call would have to save
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
             if (kHist && T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
+            int row = 0;   // output ring row of ply j: j mod ring_steps
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
                 if (kHist) hist_before(G, T);
                 const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal, mask_ring != nullptr);
-                const size_t o = (size_t)(j % ring_steps) * (size_t)A.N + (size_t)g;
+                const size_t o = (size_t)row * (size_t)A.N + (size_t)g;
+                if (++row == ring_steps) row = 0;
                 if (T.leader()) {
                     if (kHist) hist_after(G, A, g, r);
                     count_result(G->stat, r);
@@ -866,6 +871,7 @@ void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_s
 
 extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
 {
+    ST_NVTX("st_env_create");
     ST_CHECK_ARG(cfg && out, "st_env_create: null argument");
     ST_CHECK_ARG(cfg->num_games >= 1 && cfg->num_games <= ST_MAX_GAMES, "st_env_create: num_games %d out of range",
                  cfg->num_games);
@@ -923,6 +929,7 @@ extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
 
 extern "C" st_status st_env_destroy(st_env* e)
 {
+    ST_NVTX("st_env_destroy");
     if (!e) return ST_OK;
     DeviceGuard guard(e->device);
     cudaStreamSynchronize(e->stream);
@@ -937,6 +944,7 @@ extern "C" st_status st_env_destroy(st_env* e)
 
 extern "C" st_status st_env_reset(st_env* e, const uint8_t* setups, const uint8_t* which)
 {
+    ST_NVTX("st_env_reset");
     ST_CHECK_ARG(e, "st_env_reset: null env");
     DeviceGuard guard(e->device);
     EnvArgs a = env_args(e);
@@ -949,6 +957,7 @@ extern "C" st_status st_env_reset(st_env* e, const uint8_t* setups, const uint8_
 extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
                                  uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out)
 {
+    ST_NVTX("st_env_step");
     ST_CHECK_ARG(e, "st_env_step: null env");
     ST_CHECK_ARG(!mask_out || aligned16(mask_out), "st_env_step: mask_out must be 16-byte aligned");
     DeviceGuard guard(e->device);
@@ -968,6 +977,7 @@ extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* act
 extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32_t blocks_per_sm,
                                        int32_t games_per_warp, int32_t games_per_fetch)
 {
+    ST_NVTX("st_env_set_launch");
     ST_CHECK_ARG(e, "st_env_set_launch: null env");
     ST_CHECK_ARG(warps_per_block >= 1 && warps_per_block <= kRunMaxWarps, "st_env_set_launch: warps_per_block 1..%d",
                  kRunMaxWarps);
@@ -996,6 +1006,7 @@ extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32
 extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
                                 int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
 {
+    ST_NVTX("st_env_run");
     ST_CHECK_ARG(e, "st_env_run: null env");
     ST_CHECK_ARG(n_steps >= 0, "st_env_run: n_steps < 0");
     ST_CHECK_ARG(ring_steps >= 1, "st_env_run: ring_steps must be >= 1");
@@ -1055,6 +1066,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
 
 extern "C" st_status st_env_sync(st_env* e)
 {
+    ST_NVTX("st_env_sync");
     ST_CHECK_ARG(e, "st_env_sync: null env");
     DeviceGuard guard(e->device);
     int32_t h[2];
@@ -1072,6 +1084,7 @@ extern "C" st_status st_env_sync(st_env* e)
 
 extern "C" st_status st_env_stats(st_env* e, uint32_t* stats_out)
 {
+    ST_NVTX("st_env_stats");
     ST_CHECK_ARG(e && stats_out, "st_env_stats: null argument");
     DeviceGuard guard(e->device);
     ST_CUDA(cudaMemcpyAsync(stats_out, e->stats, (size_t)e->N * 8 * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
@@ -1081,6 +1094,7 @@ extern "C" st_status st_env_stats(st_env* e, uint32_t* stats_out)
 
 extern "C" st_status st_env_export(st_env* e, const int32_t* idx, int32_t n, st_position* out)
 {
+    ST_NVTX("st_env_export");
     ST_CHECK_ARG(e && (n == 0 || (idx && out)), "st_env_export: null argument");
     ST_CHECK_ARG(n >= 0, "st_env_export: n < 0");
     if (n == 0) return ST_OK;
@@ -1094,6 +1108,7 @@ extern "C" st_status st_env_export(st_env* e, const int32_t* idx, int32_t n, st_
 
 extern "C" st_status st_env_import(st_env* e, const int32_t* idx, int32_t n, const st_position* in)
 {
+    ST_NVTX("st_env_import");
     ST_CHECK_ARG(e && (n == 0 || (idx && in)), "st_env_import: null argument");
     ST_CHECK_ARG(n >= 0, "st_env_import: n < 0");
     if (n == 0) return ST_OK;
@@ -1107,6 +1122,7 @@ extern "C" st_status st_env_import(st_env* e, const int32_t* idx, int32_t n, con
 
 extern "C" st_status st_env_set_setup_pool(st_env* e, const uint8_t* pool, int32_t M, uint32_t flags)
 {
+    ST_NVTX("st_env_set_setup_pool");
     ST_CHECK_ARG(e, "st_env_set_setup_pool: null env");
     ST_CHECK_ARG(M >= 0 && M <= ST_MAX_POOL, "st_env_set_setup_pool: M must be in [0, %d]", ST_MAX_POOL);
     ST_CHECK_ARG((flags & ~ST_POOL_MIRROR) == 0, "st_env_set_setup_pool: unknown flags");
@@ -1152,6 +1168,7 @@ extern "C" st_status st_env_set_setup_pool(st_env* e, const uint8_t* pool, int32
 
 extern "C" st_status st_env_pin(st_env* e, const int32_t* idx, int32_t n, const st_position* states)
 {
+    ST_NVTX("st_env_pin");
     ST_CHECK_ARG(e, "st_env_pin: null env");
     ST_CHECK_ARG(n >= 0 && n <= e->N, "st_env_pin: n must be in [0, N]");
     ST_CHECK_ARG(n == 0 || (idx && states), "st_env_pin: null argument");
@@ -1196,6 +1213,7 @@ extern "C" st_status st_env_pin(st_env* e, const int32_t* idx, int32_t n, const 
 
 extern "C" st_status st_env_enable_history(st_env* e, int32_t H)
 {
+    ST_NVTX("st_env_enable_history");
     ST_CHECK_ARG(e, "st_env_enable_history: null env");
     ST_CHECK_ARG(H >= 0 && H <= ST_MAX_HISTORY, "st_env_enable_history: H must be in [0, %d]", ST_MAX_HISTORY);
     DeviceGuard guard(e->device);
@@ -1228,6 +1246,7 @@ extern "C" st_status st_env_enable_history(st_env* e, int32_t H)
 
 extern "C" st_status st_env_current_step(st_env* e, int64_t* now)
 {
+    ST_NVTX("st_env_current_step");
     ST_CHECK_ARG(e && now, "st_env_current_step: null argument");
     *now = e->now;
     return ST_OK;
@@ -1246,6 +1265,7 @@ static st_status hist_window(st_env* e, int64_t t, bool need_row, const char* fn
 extern "C" st_status st_env_history_positions(st_env* e, int64_t t, st_position* out, uint8_t* status,
                                               uint8_t* ended, int32_t* since)
 {
+    ST_NVTX("st_env_history_positions");
     const st_status w = hist_window(e, t, false, "st_env_history_positions");
     if (w != ST_OK) return w;
     ST_CHECK_ARG(out, "st_env_history_positions: null out");
@@ -1261,6 +1281,7 @@ extern "C" st_status st_env_history_positions(st_env* e, int64_t t, st_position*
 extern "C" st_status st_env_history_steps(st_env* e, int64_t t, int16_t* action, uint8_t* done, int8_t* reward,
                                           uint8_t* start)
 {
+    ST_NVTX("st_env_history_steps");
     const st_status w = hist_window(e, t, true, "st_env_history_steps");
     if (w != ST_OK) return w;
     DeviceGuard guard(e->device);
@@ -1272,6 +1293,7 @@ extern "C" st_status st_env_history_steps(st_env* e, int64_t t, int16_t* action,
 extern "C" st_status st_env_history_logs(st_env* e, int64_t t, int32_t L, uint8_t* setups, int16_t* logs,
                                          int16_t* plies, uint8_t* status)
 {
+    ST_NVTX("st_env_history_logs");
     const st_status w = hist_window(e, t, false, "st_env_history_logs");
     if (w != ST_OK) return w;
     ST_CHECK_ARG(L >= 1 && L <= 32767, "st_env_history_logs: L must be in [1, 32767]");
@@ -1287,6 +1309,7 @@ extern "C" st_status st_env_history_logs(st_env* e, int64_t t, int32_t L, uint8_
 
 extern "C" st_status st_env_sample_actions(st_env* e, int16_t* actions)
 {
+    ST_NVTX("st_env_sample_actions");
     ST_CHECK_ARG(e && actions, "st_env_sample_actions: null argument");
     DeviceGuard guard(e->device);
     EnvArgs a = env_args(e);

@@ -230,7 +230,9 @@ __device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uin
                                               const Rules& Rl)
 {
     begin_rollout(G, types_s, pi, (uint16_t*)nullptr, T, R, &R->plan, types, k0, k1, stream, s);
-    const int searcher = G->c.ply & 1;
+    // the root's side to move, from the root record (the game record's ply
+    // changes when the forced first move is played)
+    const int searcher = R->c.ply & 1;
     int code = 0, winner = -1, n = 0;
     select_apply(G, T, first, 0u, (uint16_t*)nullptr, pi);
     check_end(G, T, Rl, pi, code, winner, n);

@@ -15,8 +15,8 @@ ThreadSanitizer and under AddressSanitizer with UndefinedBehaviorSanitizer.
 Every output must equal the oracle's.  Only the bulk-copy inline assembly
 and the shared-memory declarations are rewritten for the host.
 
-Two data races are known and allowed by name (known_ply_races); any other
-report fails.  A planted missing team barrier must be reported."""
+Any sanitizer report fails the test.  A planted missing team barrier must
+be reported."""
 import os
 import re
 import subprocess
@@ -107,26 +107,9 @@ def _line_of(src_dir, name, text, after=None):
     return "%s:%d" % (name, next(i for i in range(start, len(lines)) if text in lines[i]) + 1)
 
 
-def known_ply_races(src_dir):
-    """The two races the harness finds in the current sources.  A team-wide
-    read of the ply counter (G->c.ply) with no team barrier before the first
-    lane's apply increments it: in search_rollout (the searcher's side,
-    before the forced first move) and in env_ply (the ply index of the
-    result, on the supplied-action path, where no selection collective
-    separates the two).  Only the first lane's copy of either value is ever
-    used (for the tally slot, for the ply output), so no output depends on
-    the race; a team-uniform read is the fix."""
-    inc = _line_of(src_dir, "engine.cuh", "c.ply = (int16_t)(c.ply + 1);")
-    return {
-        tuple(sorted((_line_of(src_dir, "rollout.cuh", "const int searcher = G->c.ply & 1;",
-                               after="search_rollout("), inc))),
-        tuple(sorted((_line_of(src_dir, "env_dev.cu", "res.ply_idx = G->c.ply;"), inc))),
-    }
-
-
 def _check_report(r, known=()):
-    """No sanitizer report other than the known races (pairs of the two
-    accesses' innermost file:line)."""
+    """No sanitizer report other than the races listed in `known` (pairs of
+    the two accesses' innermost file:line); the kernels' own runs list none."""
     report = r.stdout + r.stderr
     if r.returncode != 0 and "FATAL: ThreadSanitizer" in report and "memory" in report:
         pytest.skip("ThreadSanitizer cannot start here: %s" % report[-300:])
@@ -212,7 +195,7 @@ def test_harness_reports_a_planted_missing_sync(tmp_path):
         pytest.skip("ThreadSanitizer cannot start here")
     assert "WARNING: ThreadSanitizer: data race" in report and "build_board" in report, report[-3000:]
     with pytest.raises(AssertionError, match="unexpected data race"):
-        _check_report(r, known_ply_races(str(tmp_path / "src")))
+        _check_report(r, ())
 
 
 def _run_driver(exe, args, env, known=()):
@@ -322,7 +305,7 @@ def test_search_kernels_under_sanitizers(tmp_path, built, san):
     pos.tofile(inp + ".pos")
     for rflags in (oracle.ALL_RULES, oracle.ALL_RULES | oracle.ROLLOUT_MAGNET):
         out = str(tmp_path / ("out%d" % rflags))
-        _run_driver(exe, [inp, P, S, depth, seed, 2, rflags, out], env, known_ply_races(src))
+        _run_driver(exe, [inp, P, S, depth, seed, 2, rflags, out], env, ())
         ref = oracle.search(pos, S, depth, seed, flags=rflags)
         M = oracle.SEARCH_MAX_MOVES
         for k, dt, shape in (("n_moves", np.int32, (P,)), ("actions", np.int16, (P, M)),
@@ -346,7 +329,7 @@ def test_plain_step_with_supplied_actions_under_sanitizers(tmp_path, built, san)
     out = str(tmp_path / "o")
     r = subprocess.run([exe, str(N), str(S), "32", "4", "1", "1", str(seed), out, str(tmp_path / "acts")],
                        capture_output=True, text=True, timeout=900, env=dict(os.environ, **env))
-    _check_report(r, known_ply_races(src))
+    _check_report(r, ())
     for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
     mask = np.fromfile(out + ".mask", np.uint8).reshape(S, N, oracle.MASK_BYTES)
@@ -380,7 +363,7 @@ def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
     np.array(sorted(pins), np.int32).tofile(inp + ".idx")
     steps = [200, 150, 60, 0]
     _run_driver(exe, [inp, out, N, S, 8, 2, 1, 2, seed, H, M, 1, len(pins)] + steps, env,
-                known_ply_races(src))
+                ())
     ref = oracle.env_run(seed, N, S, pool=pool, mirror=True, episode0=1, pins=pins)
     for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
@@ -425,7 +408,7 @@ def test_serving_batch_under_sanitizers(tmp_path, built, san):
     inp, out = str(tmp_path / "in"), str(tmp_path / "o")
     pos.tofile(inp + ".pos")
     req.tofile(inp + ".req")
-    _run_driver(exe, [inp, R, 2, out], env, known_ply_races(src))
+    _run_driver(exe, [inp, R, 2, out], env, ())
     tallies = np.fromfile(out + ".tallies", np.int32).reshape(R, 4)
     np.testing.assert_array_equal(np.fromfile(out + ".done", np.uint32), 1000 + np.arange(R))
     for i in range(R - 1):
