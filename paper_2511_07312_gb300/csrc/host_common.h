@@ -5,9 +5,21 @@
 #include <cstdio>
 #include <string>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "stratego.h"
 
 namespace stg {
+
+// An NVTX range named after the C entry point, open for the duration of the
+// call (visible in Nsight Systems and Nsight Compute range filters; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define ST_NVTX(name) ::stg::NvtxRange st_nvtx_range_(name)
 
 void set_error(const char* fmt, ...);
 

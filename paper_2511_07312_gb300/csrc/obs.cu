@@ -447,6 +447,7 @@ std::atomic<int> g_items_per_warp{8};   // fastest measured on GB300 for 16,384 
 
 extern "C" st_status st_replay_set_chunk(int32_t items_per_warp)
 {
+    ST_NVTX("st_replay_set_chunk");
     ST_CHECK_ARG(items_per_warp >= 1 && items_per_warp <= 65536, "st_replay_set_chunk: 1..65536");
     g_items_per_warp.store(items_per_warp);
     return ST_OK;
@@ -457,6 +458,7 @@ extern "C" st_status st_replay_positions(const uint8_t* setups, const int16_t* a
                                          const st_rules* rules, st_position* out, uint8_t* item_status,
                                          void* stream)
 {
+    ST_NVTX("st_replay_positions");
     ST_CHECK_ARG(rules_ok(rules), "st_replay_positions: invalid rules");
     ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_replay_positions: negative size");
     if (B == 0) return ST_OK;
@@ -478,6 +480,7 @@ extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions
                                    const st_rules* rules, uint8_t* planes, uint16_t* planes_bf16, uint8_t* mask,
                                    uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_obs_encode");
     ST_CHECK_ARG(rules_ok(rules), "st_obs_encode: invalid rules");
     ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_obs_encode: negative size");
     if (B == 0) return ST_OK;
@@ -582,6 +585,7 @@ extern "C" st_status st_obs_encode_static(const uint8_t* setups, const int16_t* 
                                           const int8_t* player, int32_t B, const st_rules* rules, uint8_t* planes,
                                           uint16_t* planes_bf16, uint8_t* mask, uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_obs_encode_static");
     ST_CHECK_ARG(rules_ok(rules), "st_obs_encode_static: invalid rules");
     ST_CHECK_ARG(B >= 0 && log_len >= 0 && num_logs >= 0, "st_obs_encode_static: negative size");
     ST_CHECK_ARG(B <= ST_OBS_STATIC_MAX_ITEMS,

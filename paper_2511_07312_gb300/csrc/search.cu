@@ -406,6 +406,7 @@ __global__ void k_positions_mask(const st_position* pos, int P, Rules Rl, uint8_
 extern "C" st_status st_belief_sample(const st_position* pos, int32_t P, int32_t K, uint64_t seed,
                                       const uint32_t* stream_ids, uint8_t* types, uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_belief_sample");
     ST_CHECK_ARG(P >= 0 && K >= 0, "st_belief_sample: negative size");
     if (P == 0 || K == 0) return ST_OK;
     ST_CHECK_ARG(pos && types, "st_belief_sample: null argument");
@@ -420,6 +421,7 @@ extern "C" st_status st_rollout(const st_position* pos, int32_t P, int32_t K, in
                                 const uint32_t* stream_ids, const uint8_t* types, const st_rules* rules,
                                 int32_t* tallies, uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_rollout");
     ST_CHECK_ARG(rules_ok(rules, true), "st_rollout: invalid rules");
     ST_CHECK_ARG(P >= 0 && K >= 0 && depth >= 0, "st_rollout: negative size");
     if (P == 0) return ST_OK;
@@ -478,6 +480,7 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
                                const st_rules* rules, int32_t* n_moves, int16_t* actions, int32_t* tallies,
                                double* q, double* pi, int16_t* chosen, uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_search");
     ST_CHECK_ARG(rules_ok(rules, true), "st_search: invalid rules");
     ST_CHECK_ARG(P >= 0 && P <= 65535, "st_search: P must be in [0, 65535]");
     ST_CHECK_ARG(S >= 0 && S <= (1 << 24), "st_search: S must be in [0, 2^24]");
@@ -550,6 +553,7 @@ extern "C" st_status st_search(const st_position* pos, int32_t P, int32_t S, int
 extern "C" st_status st_positions_mask(const st_position* pos, int32_t P, const st_rules* rules, uint8_t* mask,
                                        int32_t* n_legal, uint8_t* two_square, uint8_t* item_status, void* stream)
 {
+    ST_NVTX("st_positions_mask");
     ST_CHECK_ARG(rules_ok(rules), "st_positions_mask: invalid rules");
     ST_CHECK_ARG(P >= 0, "st_positions_mask: P < 0");
     if (P == 0) return ST_OK;

@@ -408,6 +408,7 @@ void worker_main(st_server* s)
 
 extern "C" st_status st_serve_create(const st_serve_config* cfg, st_server** out)
 {
+    ST_NVTX("st_serve_create");
     ST_CHECK_ARG(cfg && out, "st_serve_create: null argument");
     ST_CHECK_ARG(cfg->max_requests >= 1 && cfg->max_requests <= 65536, "st_serve_create: max_requests 1..65536");
     ST_CHECK_ARG(cfg->sample_slots >= 1 && cfg->sample_slots <= (1 << 26), "st_serve_create: sample_slots 1..2^26");
@@ -468,6 +469,7 @@ extern "C" st_status st_serve_create(const st_serve_config* cfg, st_server** out
 
 extern "C" st_status st_serve_submit(st_server* s, const st_request* req, uint64_t* ticket)
 {
+    ST_NVTX("st_serve_submit");
     ST_CHECK_ARG(s && req && ticket, "st_serve_submit: null argument");
     ST_CHECK_ARG(req->K >= 0 && req->K <= s->cfg.sample_slots, "st_serve_submit: K %d outside 0..%d", req->K,
                  s->cfg.sample_slots);
@@ -534,6 +536,7 @@ static st_status take_result(st_server* s, uint64_t ticket, int32_t* tallies, st
 
 extern "C" st_status st_serve_poll(st_server* s, uint64_t ticket, int32_t* tallies, st_timing* timing)
 {
+    ST_NVTX("st_serve_poll");
     ST_CHECK_ARG(s, "st_serve_poll: null server");
     std::lock_guard<std::mutex> lk(s->mu);
     return take_result(s, ticket, tallies, timing);
@@ -542,6 +545,7 @@ extern "C" st_status st_serve_poll(st_server* s, uint64_t ticket, int32_t* talli
 extern "C" st_status st_serve_wait(st_server* s, uint64_t ticket, int32_t timeout_ms, int32_t* tallies,
                                    st_timing* timing)
 {
+    ST_NVTX("st_serve_wait");
     ST_CHECK_ARG(s, "st_serve_wait: null server");
     ST_CHECK_ARG(timeout_ms >= 0, "st_serve_wait: negative timeout");
     std::unique_lock<std::mutex> lk(s->mu);
@@ -568,6 +572,7 @@ extern "C" st_status st_serve_wait(st_server* s, uint64_t ticket, int32_t timeou
 
 extern "C" st_status st_serve_get_stats(st_server* s, st_serve_stats* out)
 {
+    ST_NVTX("st_serve_get_stats");
     ST_CHECK_ARG(s && out, "st_serve_get_stats: null argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
@@ -580,6 +585,7 @@ extern "C" st_status st_serve_get_stats(st_server* s, st_serve_stats* out)
 
 extern "C" st_status st_serve_destroy(st_server* s)
 {
+    ST_NVTX("st_serve_destroy");
     if (!s) return ST_OK;
     {
         std::lock_guard<std::mutex> lk(s->mu);
