@@ -15,6 +15,7 @@ Warp* warps = nullptr;
 unsigned char* smem_base = nullptr;
 size_t smem_per_block = 0;
 thread_local std::vector<Pending> pending;
+std::atomic<unsigned long long> site_warnings{0};
 }  // namespace emu
 
 template <class F>

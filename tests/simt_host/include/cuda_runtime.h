@@ -6,8 +6,11 @@
 // __ballot_sync, __shfl*_sync, __reduce_add_sync) is a rendezvous of the
 // lanes named in its mask under one mutex per warp, which gives the
 // sanitizers the same ordering the hardware collective gives; a lane outside
-// the mask, a source lane outside the mask or a collective that never
-// completes aborts the run.  Shared-memory atomics are host atomics.  A bulk
+// the mask, a source lane outside the mask, lanes of one mask that meet at
+// different kinds of collective (a ballot and a shuffle, say) or a
+// collective that never completes aborts the run, and lanes that meet at the
+// same kind of collective from different source lines are reported on
+// stderr ("EMU WARNING") and counted.  Shared-memory atomics are host atomics.  A bulk
 // asynchronous copy (cp.async.bulk) is performed at its wait, the latest
 // moment the hardware may read its source, so a source rewritten too early
 // shows up as wrong output.  The product library never includes this file.
@@ -21,6 +24,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <atomic>
 #include <condition_variable>
 #include <vector>
 #define __device__
@@ -52,13 +56,26 @@ typedef struct CUgraphExec_st* cudaGraphExec_t;
 typedef int cudaError_t;
 
 namespace emu {
+// The kind of a warp collective: lanes of one mask that meet must all be at
+// the same kind (on the hardware, lanes of one mask at different collectives
+// is undefined behaviour and can hang or corrupt values).
+enum Op : int { kOpSync = 1, kOpBallot, kOpReduce, kOpShfl, kOpShflUp, kOpShflDown, kOpShflXor };
+inline const char* op_name(int op)
+{
+    static const char* names[] = {"?", "syncwarp", "ballot", "reduce", "shfl", "shfl_up", "shfl_down", "shfl_xor"};
+    return names[op >= 0 && op < 8 ? op : 0];
+}
 struct Rendezvous {
     unsigned arrived = 0;
     int phase = 0;            // 0 collecting, 1 reading
     int readers = 0;
     unsigned long long gen = 0;
     unsigned long long vals[32];
+    int op = 0;               // the collective of the first lane to arrive in this round
+    const char* file = nullptr;
+    int line = 0;
 };
+extern std::atomic<unsigned long long> site_warnings;
 struct Warp {
     std::mutex m;
     std::condition_variable cv;
@@ -85,7 +102,7 @@ inline unsigned char* block_smem() { return smem_base + (size_t)blockIdx.x * sme
     std::abort();
 }
 template <class F>
-unsigned long long exchange(unsigned mask, unsigned long long v, F f)
+unsigned long long exchange(unsigned mask, unsigned long long v, F f, int op, const char* file, int line)
 {
     const unsigned lane = threadIdx.x & 31;
     if (!((mask >> lane) & 1u)) fail("calling lane not in mask", mask);
@@ -94,6 +111,17 @@ unsigned long long exchange(unsigned mask, unsigned long long v, F f)
     Rendezvous& R = W.rv[mask];
     W.cv.wait(lk, [&] { return R.phase == 0; });
     if ((R.arrived >> lane) & 1u) fail("lane arrived twice", mask);
+    if (R.arrived == 0) {
+        R.op = op; R.file = file; R.line = line;
+    } else if (R.op != op) {
+        std::fprintf(stderr, "EMU FAILURE: lanes of one mask met at different collectives: %s at %s:%d and %s at %s:%d\n",
+                     op_name(R.op), R.file, R.line, op_name(op), file, line);
+        fail("mismatched collectives", mask);
+    } else if (R.line != line || std::strcmp(R.file, file) != 0) {
+        std::fprintf(stderr, "EMU WARNING: lanes of one mask met at one collective (%s) from different sites: %s:%d and %s:%d\n",
+                     op_name(op), R.file, R.line, file, line);
+        site_warnings++;
+    }
     R.vals[lane] = v;
     R.arrived |= 1u << lane;
     const unsigned long long my = R.gen;
@@ -128,47 +156,51 @@ inline void bulk_copy(void* dst, const void* src, size_t n) { pending.push_back(
 inline void bulk_wait() { for (auto& p : pending) std::memcpy(p.dst, p.src, p.n); pending.clear(); }
 }  // namespace emu
 
-inline void __syncwarp(unsigned mask = 0xffffffffu) { emu::exchange(mask, 0, [](auto*, unsigned) { return 0ull; }); }
-inline unsigned __ballot_sync(unsigned mask, int p)
+#define EMU_SITE const char* file_ = __builtin_FILE(), int line_ = __builtin_LINE()
+inline void __syncwarp(unsigned mask = 0xffffffffu, EMU_SITE)
+{
+    emu::exchange(mask, 0, [](auto*, unsigned) { return 0ull; }, emu::kOpSync, file_, line_);
+}
+inline unsigned __ballot_sync(unsigned mask, int p, EMU_SITE)
 {
     return (unsigned)emu::exchange(mask, p != 0, [mask](unsigned long long* v, unsigned) {
         unsigned long long b = 0;
         for (int l = 0; l < 32; ++l) if (((mask >> l) & 1u) && v[l]) b |= 1ull << l;
-        return b; });
+        return b; }, emu::kOpBallot, file_, line_);
 }
-inline int __any_sync(unsigned mask, int p) { return __ballot_sync(mask, p) != 0; }
-inline int __all_sync(unsigned mask, int p) { return __ballot_sync(mask, p) == mask; }
-inline unsigned __reduce_add_sync(unsigned mask, unsigned v)
+inline int __any_sync(unsigned mask, int p, EMU_SITE) { return __ballot_sync(mask, p, file_, line_) != 0; }
+inline int __all_sync(unsigned mask, int p, EMU_SITE) { return __ballot_sync(mask, p, file_, line_) == mask; }
+inline unsigned __reduce_add_sync(unsigned mask, unsigned v, EMU_SITE)
 {
     return (unsigned)emu::exchange(mask, v, [mask](unsigned long long* x, unsigned) {
         unsigned s = 0;
         for (int l = 0; l < 32; ++l) if ((mask >> l) & 1u) s += (unsigned)x[l];
-        return (unsigned long long)s; });
+        return (unsigned long long)s; }, emu::kOpReduce, file_, line_);
 }
-template <class T> T __shfl_sync(unsigned mask, T v, int src, int width = 32)
+template <class T> T __shfl_sync(unsigned mask, T v, int src, int width = 32, EMU_SITE)
 {
     return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, src, width](unsigned long long* x, unsigned lane) {
         const unsigned s = (lane & ~(unsigned)(width - 1)) | ((unsigned)src & (unsigned)(width - 1));
-        return x[emu::src_ok(mask, s)]; }));
+        return x[emu::src_ok(mask, s)]; }, emu::kOpShfl, file_, line_));
 }
-template <class T> T __shfl_up_sync(unsigned mask, T v, unsigned d, int width = 32)
+template <class T> T __shfl_up_sync(unsigned mask, T v, unsigned d, int width = 32, EMU_SITE)
 {
     return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, d, width](unsigned long long* x, unsigned lane) {
         const unsigned s = (lane & (unsigned)(width - 1)) >= d ? lane - d : lane;
-        return x[emu::src_ok(mask, s)]; }));
+        return x[emu::src_ok(mask, s)]; }, emu::kOpShflUp, file_, line_));
 }
-template <class T> T __shfl_down_sync(unsigned mask, T v, unsigned d, int width = 32)
+template <class T> T __shfl_down_sync(unsigned mask, T v, unsigned d, int width = 32, EMU_SITE)
 {
     return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, d, width](unsigned long long* x, unsigned lane) {
         const unsigned s = (lane & (unsigned)(width - 1)) + d < (unsigned)width ? lane + d : lane;
-        return x[emu::src_ok(mask, s)]; }));
+        return x[emu::src_ok(mask, s)]; }, emu::kOpShflDown, file_, line_));
 }
-template <class T> T __shfl_xor_sync(unsigned mask, T v, int m, int width = 32)
+template <class T> T __shfl_xor_sync(unsigned mask, T v, int m, int width = 32, EMU_SITE)
 {
     return emu::from<T>(emu::exchange(mask, emu::bits(v), [mask, m, width](unsigned long long* x, unsigned lane) {
         unsigned s = lane ^ (unsigned)m;
         if ((s & ~(unsigned)(width - 1)) > (lane & ~(unsigned)(width - 1))) s = lane;
-        return x[emu::src_ok(mask, s)]; }));
+        return x[emu::src_ok(mask, s)]; }, emu::kOpShflXor, file_, line_));
 }
 inline int __popc(unsigned v) { return __builtin_popcount(v); }
 inline int __popcll(unsigned long long v) { return __builtin_popcountll(v); }

@@ -114,6 +114,9 @@ def _check_report(r, known=()):
     if r.returncode != 0 and "FATAL: ThreadSanitizer" in report and "memory" in report:
         pytest.skip("ThreadSanitizer cannot start here: %s" % report[-300:])
     assert "runtime error" not in report and "ERROR: AddressSanitizer" not in report, report[-6000:]
+    # collectives: lanes of one mask always meet at the same kind of
+    # collective from the same source line
+    assert "EMU FAILURE" not in report and "EMU WARNING" not in report, report[-6000:]
     races = report.split("WARNING: ThreadSanitizer: data race")[1:]
     for block in races:
         tops = re.findall(r"(?:Read|Write|read|write) of size \d+ at .*?\n\s+#0 \S+ .*?([\w.]+\.(?:cuh|cu|cpp|h):\d+)",
@@ -196,6 +199,28 @@ def test_harness_reports_a_planted_missing_sync(tmp_path):
     assert "WARNING: ThreadSanitizer: data race" in report and "build_board" in report, report[-3000:]
     with pytest.raises(AssertionError, match="unexpected data race"):
         _check_report(r, ())
+
+
+def test_harness_reports_mismatched_collectives(tmp_path):
+    # plant, on the host only, a team whose lanes reach different kinds of
+    # collective with one mask: the odd lanes reduce, the even lanes ballot
+    # (undefined on the hardware); the harness must stop with a report that
+    # names both collectives
+    total = "    const int total = T.sum(cnt);\n    T.sync();\n    return total;"
+
+    def mismatch(name, text):
+        if name != "engine.cuh":
+            return text
+        assert total in text
+        return text.replace(total, "    const int total = (T.tl & 1) ? T.sum(cnt) : (int)T.ballot(cnt > 0);\n"
+                                   "    T.sync();\n    return total;")
+
+    exe = _build(str(tmp_path), [], "env_mismatch", edit=mismatch)
+    r = subprocess.run([exe, "4", "5", "8", "1", "1", "1", "7", str(tmp_path / "o")], capture_output=True,
+                       text=True, timeout=600)
+    report = r.stdout + r.stderr
+    assert r.returncode != 0
+    assert "different collectives: " in report and "reduce" in report and "ballot" in report, report[-3000:]
 
 
 def _run_driver(exe, args, env, known=()):
