@@ -563,8 +563,26 @@ def secondary(st, torch, dev, args):
     t1.synchronize()
     ms = t0.elapsed_time(t1) / reps
     byts = B * (487 * 100 * 3 + MASK_BYTES)
-    out["obs_encode"] = {"positions_per_s": B / (ms / 1000), "ms": ms, "GB_per_s_written": byts / (ms / 1000) / 1e9,
-                         "positions": B, "bytes_written_per_position": 487 * 100 * 3 + MASK_BYTES}
+    peak, peak_kind = peaks()
+    gbs = byts / (ms / 1000) / 1e9
+    out["obs_encode"] = {"positions_per_s": B / (ms / 1000), "ms": ms, "GB_per_s_written": gbs,
+                         "positions": B, "bytes_written_per_position": 487 * 100 * 3 + MASK_BYTES,
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                      "frac": gbs / peak, "peak_kind": peak_kind + " hbm_gbs (copy, burst)",
+                                      "algorithmic_bytes_per_position": 487 * 100 * 3 + MASK_BYTES,
+                                      "kernels": "k_replay + k_obs_emit, one call"}}
+    # the oracle beside it: the same items, one per call, on all host threads
+    # for about 5 seconds (each item replayed from its game's start)
+    import oracle
+    oracle.lib()
+    threads = host_threads()
+    setups_h, acts_h = setups.cpu().numpy(), acts.cpu().numpy()
+    gi_h, pl_h = gi.cpu().numpy(), pl.cpu().numpy()
+    done_o, dt = timed_items(lambda i: oracle.obs_encode(setups_h, acts_h, gi_h[i:i + 1], pl_h[i:i + 1]), B, threads,
+                             5.0)
+    out["obs_encode"]["cpu_baseline"] = {"value": done_o / dt, "unit": "positions/s", "cores": threads,
+                                         "kind": "oracle", "sample": "items 0..%d of the %d (uint8 and bf16 planes, "
+                                         "masks), one item per call" % (done_o - 1, B)}
     # belief-sample rollouts: 4,096 positions x 256 samples x depth 32
     P, K, D = 4096, 256, 32
     pos = rollout_positions(st, torch, dev, setups, acts, gi, pl, P)
@@ -581,6 +599,14 @@ def secondary(st, torch, dev, args):
     out["belief_rollout"] = {"samples_per_s": P * K / (ms / 1000), "ms": ms, "positions": P, "K": K, "depth": D,
                              "ply_steps_per_s_upper": P * K * D / (ms / 1000),
                              "tallies_win_loss_draw_unfinished": tl}
+    # the oracle beside it: one position (all K samples) per call, on all host
+    # threads for about 5 seconds
+    pos_h = pos.cpu().numpy()
+    done_r, dt = timed_items(lambda i: oracle.rollout(pos_h[i:i + 1], K, D, 7, stream_ids=np.array([i], np.uint32)),
+                             P, threads, 5.0)
+    out["belief_rollout"]["cpu_baseline"] = {"value": done_r * K / dt, "unit": "samples/s", "cores": threads,
+                                             "kind": "oracle", "sample": "positions 0..%d of the %d, K=%d, depth %d"
+                                             % (done_r - 1, P, K, D)}
     # the same rollouts with the magnet policy as the rollout policy
     mflags = st.RULES_ALL | st.ROLLOUT_MAGNET
     st.rollout(pos, K, D, seed=7, out=tallies, flags=mflags)
@@ -612,10 +638,7 @@ def secondary(st, torch, dev, args):
                      "mean_legal_moves": n_roll / Ss / Ps}
     # the oracle beside it: the same positions, one per call, on all host
     # threads for about 5 seconds
-    import oracle
-    oracle.lib()
     spos_h = spos.cpu().numpy()
-    threads = host_threads()
     done_p, dt = timed_items(lambda i: oracle.search(spos_h[i:i + 1], Ss, Ds, 11,
                                                      stream_ids=np.array([i], np.uint32)), Ps, threads, 5.0)
     out["search"]["cpu_baseline"] = {"value": done_p / dt, "unit": "positions/s", "cores": threads,
@@ -673,13 +696,18 @@ def secondary(st, torch, dev, args):
                                 "env_steps_per_s_not_recording": Nh * Hh / (plain_ms / 1000)}
     henv.close()
     out["serving"] = serving(st, torch, dev, pos.cpu().numpy(), args)
+    # the same request mix at ten times the arrival rate, where requests
+    # arrive while others run and batches of several requests form
+    out["serving"]["high_rate"] = serving(st, torch, dev, pos.cpu().numpy(), args, duration_s=2.0, rate=20000.0,
+                                          compare=False)
     return out
 
 
-def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0):
+def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0, compare=True):
     """Serving: Poisson arrivals (mean 2,000/s) of search requests, K ~
     U{16..1024}, depth ~ U{8..64}, from positions of the 64 replayed games; the
-    continuous-batching server against one launch + sync per request."""
+    continuous-batching server against one launch + sync per request, and a
+    burst of heavy requests for capacity (compare=False: the server alone)."""
     import numpy as np
     rng = np.random.default_rng(5)
     n = int(duration_s * rate)
@@ -719,7 +747,11 @@ def serving(st, torch, dev, positions, args, duration_s=10.0, rate=2000.0):
     stats = srv.stats()
     srv.close()
     served = dict(pct(lat), requests_per_s=n / span, samples_per_s=float(Ks.sum()) / span,
-                  batches=stats["batches"], max_batch_requests=stats["max_batch_requests"])
+                  batches=stats["batches"], max_batch_requests=stats["max_batch_requests"],
+                  mean_batch_requests=n / max(1, stats["batches"]))
+    if not compare:
+        return {"requests": n, "arrival_rate_per_s": rate, "K_range": [16, 1024], "depth_range": [8, 64],
+                "served": served}
     # plain: one launch + sync per request, in arrival order
     pos_h = torch.from_numpy(positions).pin_memory()
     pos_d = torch.empty((1, positions.shape[1]), dtype=torch.uint8, device=dev)

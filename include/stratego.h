@@ -361,7 +361,12 @@ st_status st_obs_encode(const uint8_t* setups, const int16_t* actions, int32_t l
  *    allocating routine.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture on that device.
+ *    before any stream capture on that device.  The address is kept for the
+ *    life of the process: the entry point assumes the device's primary
+ *    context (the one the CUDA runtime uses) throughout, and that
+ *    cudaDeviceReset is not called on the device afterwards (a reset
+ *    reloads the library's device image, and the kept address would be
+ *    stale).
  *  - All calls share the one array: calls whose work overlaps on the GPU
  *    (different streams, or threads, without ordering between them) race
  *    and may corrupt each other's outputs.  Order them on one stream.

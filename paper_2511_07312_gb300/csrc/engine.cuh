@@ -485,6 +485,19 @@ __device__ __forceinline__ void or_bits(uint32_t* mask, int base, Set128 d)
     if (prev) atomicOr(&mask[w0 + 4], prev);
 }
 
+// Bits a..b of a 32-bit word (clipped to 0..31; none if a > b after clipping).
+__device__ __forceinline__ uint32_t range32(int a, int b)
+{
+    a = max(a, 0);
+    b = min(b, 31);
+    return a > b ? 0u : ((2u << b) - (1u << a));
+}
+// Square q (0..127) of a 128-bit set.
+__device__ __forceinline__ bool test128(Set128 x, int q)
+{
+    return ((q < 64 ? x.lo >> q : x.hi >> (q - 64)) & 1ull) != 0;
+}
+
 // OR a 128-bit set over to-squares into the mask row of from-square s.
 __device__ __forceinline__ void or_row(uint32_t* mask, int s, Set128 d) { or_bits(mask, 100 * s, d); }
 
@@ -642,21 +655,22 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             const uint32_t rowocc = bits_at(Set128{own.lo | enm.lo, own.hi | enm.hi}, 10 * r, 10) | lake;
             // slide lengths: empty squares east/west/north/south, then whether
             // the blocker is an enemy (a capture ends the slide)
+            // (the blocker is an enemy piece when its square is in enm; a lake is in neither)
             const uint32_t e = rowocc >> (c + 1);
             const int runE = e ? __ffs(e) - 1 : 9 - c;
-            const int capE = (e && enemy_of(G->board[s + runE + 1], P)) ? 1 : 0;
+            const int capE = (e && test128(enm, s + runE + 1)) ? 1 : 0;
             const uint32_t w = rowocc & ((1u << c) - 1u);
             const int hw = w ? 31 - __clz(w) : -1;
             const int runW = c - 1 - hw;
-            const int capW = (hw >= 0 && enemy_of(G->board[10 * r + hw], P)) ? 1 : 0;
+            const int capW = (hw >= 0 && test128(enm, 10 * r + hw)) ? 1 : 0;
             const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
             const uint32_t n = colocc >> (r + 1);
             const int runN = n ? __ffs(n) - 1 : 9 - r;
-            const int capN = (n && enemy_of(G->board[s + 10 * (runN + 1)], P)) ? 1 : 0;
+            const int capN = (n && test128(enm, s + 10 * (runN + 1))) ? 1 : 0;
             const uint32_t so = colocc & ((1u << r) - 1u);
             const int hs = so ? 31 - __clz(so) : -1;
             const int runS = r - 1 - hs;
-            const int capS = (hs >= 0 && enemy_of(G->board[10 * hs + c], P)) ? 1 : 0;
+            const int capS = (hs >= 0 && test128(enm, 10 * hs + c)) ? 1 : 0;
             const int ne = runE + capE, nw = runW + capW, nn = runN + capN, ns = runS + capS;
             int cnt_sc = ne + nw + nn + ns;
             if (cnt_sc && (chase_on || s == ts_from)) {
@@ -668,14 +682,20 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                 if (write_mask) or_row(G->mask, s, d);
             } else if (cnt_sc && write_mask) {
                 // mask bits 101s+j (row, j in [-nw, ne]) and 101s+10k (column,
-                // k in [-ns, nn]), j, k != 0, as one run of at most 100 bits
-                // starting at bit 101s - a
-                const int a = max(10 * ns, nw);
-                const Set128 every10{0x1004010040100401ull, 0x0100401004010040ull};   // bits 0, 10, ..., 120
-                Set128 v = shl128(and128(every10, range128(0, 10 * (ns + nn) + 1)), a - 10 * ns);
-                v = or128(v, shl128(Set128{lowbits64(nw + ne + 1), 0ull}, a - nw));
-                if (a < 64) v.lo &= ~(1ull << a); else v.hi &= ~(1ull << (a - 64));
-                or_bits(G->mask, 101 * s - a, v);
+                // k in [-ns, nn]), j, k != 0, word by word: the column bits are
+                // the bits of [101s-10ns, 101s+10nn] equal to s, so to c, modulo
+                // 10, in word w the bits (c - 2w) mod 10 + 10i (32 = 2 mod 10)
+                const int ctr = 101 * s;
+                const int clo = ctr - 10 * ns, chi = ctr + 10 * nn, rlo = ctr - nw, rhi = ctr + ne;
+                const int wlo = min(clo, rlo) >> 5, whi = max(chi, rhi) >> 5;
+                int m = (c + 640 - 2 * wlo) % 10;
+                for (int wi = wlo; wi <= whi; ++wi) {
+                    const int b0 = 32 * wi;
+                    uint32_t v = ((0x40100401u << m) & range32(clo - b0, chi - b0)) | range32(rlo - b0, rhi - b0);
+                    if (ctr >= b0 && ctr < b0 + 32) v &= ~(1u << (ctr - b0));
+                    if (v) atomicOr(&G->mask[wi], v);
+                    m = m >= 2 ? m - 2 : m + 8;
+                }
             }
             if (write_mask && cnt_sc) G->sq_cnt[s] = (uint8_t)cnt_sc;
             cnt += cnt_sc;
