@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--wpb", type=int, default=0, help="warps per block (0 = tuned default)")
     p.add_argument("--gpf", type=int, default=0, help="games per queue fetch (0 = tuned default)")
     p.add_argument("--gpw", type=int, default=0, help="games per warp, 1, 2, 4 or 8 (0 = tuned default)")
+    p.add_argument("--bps", type=int, default=0, help="resident blocks per SM with --wpb/--gpw (0 = as many as fit)")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", nargs="?", const="step", default=None, choices=["step", "rollout", "obs"],
                    help="for profiler captures: time one workload only -- the persistent step launch "
@@ -344,12 +345,13 @@ def main():
     env = st.Env(N, seed=args.seed + rank, device=local)
     tuned = None
     if args.wpb and args.gpw:
-        wpb, gpw, gpf = args.wpb, args.gpw, args.gpf or 1
+        wpb, gpw, gpf, bps = args.wpb, args.gpw, args.gpf or 1, args.bps
     else:
         from paper_2511_07312_gb300 import autotune
         tuned = autotune.tune(N, device=local)
         wpb, gpw, gpf = tuned["warps_per_block"], tuned["games_per_warp"], tuned["games_per_fetch"]
-    env.set_launch(wpb, 0, gpf, games_per_warp=gpw)
+        bps = tuned.get("blocks_per_sm", 0)
+    env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
     ring = env.run(1, R)   # allocates the ring; later calls reuse it
     env.sync()
 
@@ -452,6 +454,7 @@ def main():
                 "data": "synthetic",
                 "config": dict(workload_config(N, S, R),
                                launch={"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
+                                       "blocks_per_sm": bps or "max",
                                        "chosen_by": "autotuner" if tuned else "command line"}),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,

@@ -1,10 +1,12 @@
 """Launch-shape autotuner of the persistent environment step (st_env_run).
 
 Times short runs of every candidate shape -- warps per block x games per
-warp (1, 2 or 4 games side by side in one warp) x slots per queue fetch --
-on a scratch env of the caller's size and picks the fastest.  Results are
-cached in a JSON file keyed by (device name, number of games, library
-version), so a shape is tuned once per machine and size.
+warp (1, 2, 4 or 8 games side by side in one warp) x slots per queue fetch
+x resident blocks per SM (the most that fit, or fewer: with fewer resident
+games the last wave of slots can be fuller) -- on a scratch env of the
+caller's size and picks the fastest.  Results are cached in a JSON file
+keyed by (device name, number of games, library version), so a shape is
+tuned once per machine and size.
 """
 import json
 import os
@@ -17,6 +19,8 @@ from . import Env, version
 WARPS_PER_BLOCK = (1, 2, 4, 8)
 GAMES_PER_WARP = (1, 2, 4, 8)
 GAMES_PER_FETCH = (1, 4)
+# 0: as many as fit; the others cap it (tried for 4 and 8 games per warp)
+BLOCKS_PER_SM = (0, 4, 5)
 
 
 def _cache_path():
@@ -39,7 +43,8 @@ def load(num_games, device=0):
 
 def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False):
     """Return {"warps_per_block", "games_per_warp", "games_per_fetch",
-    "env_steps_per_s"} of the fastest shape, timed with CUDA events."""
+    "blocks_per_sm", "env_steps_per_s"} of the fastest shape, timed with
+    CUDA events."""
     if not force:
         hit = load(num_games, device)
         if hit:
@@ -50,26 +55,27 @@ def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False):
     for wpb in WARPS_PER_BLOCK:
         for gpw in GAMES_PER_WARP:
             for gpf in GAMES_PER_FETCH:
-                try:
-                    env.set_launch(wpb, 0, gpf, games_per_warp=gpw)
-                except RuntimeError:
-                    continue
-                env.run(plies, 4, out=ring)        # warm-up, captures the graph
-                start = torch.cuda.Event(enable_timing=True)
-                end = torch.cuda.Event(enable_timing=True)
-                start.record(env.stream)
-                for _ in range(reps):
-                    env.run(plies, 4, out=ring)
-                end.record(env.stream)
-                end.synchronize()
-                rate = num_games * plies * reps / (start.elapsed_time(end) / 1000.0)
-                results.append((rate, wpb, gpw, gpf))
-                if verbose:
-                    print("wpb %2d gpw %d gpf %d: %.3e env-steps/s" % (wpb, gpw, gpf, rate), flush=True)
+                for bps in (BLOCKS_PER_SM if gpw >= 4 else (0,)):
+                    try:
+                        env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
+                    except RuntimeError:
+                        continue
+                    env.run(plies, 4, out=ring)        # warm-up, captures the graph
+                    start = torch.cuda.Event(enable_timing=True)
+                    end = torch.cuda.Event(enable_timing=True)
+                    start.record(env.stream)
+                    for _ in range(reps):
+                        env.run(plies, 4, out=ring)
+                    end.record(env.stream)
+                    end.synchronize()
+                    rate = num_games * plies * reps / (start.elapsed_time(end) / 1000.0)
+                    results.append((rate, wpb, gpw, gpf, bps))
+                    if verbose:
+                        print("wpb %2d gpw %d gpf %d bps %d: %.3e env-steps/s" % (wpb, gpw, gpf, bps, rate), flush=True)
     env.close()
-    rate, wpb, gpw, gpf = max(results)
-    best = {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf, "env_steps_per_s": rate,
-            "plies": plies, "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    rate, wpb, gpw, gpf, bps = max(results)
+    best = {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf, "blocks_per_sm": bps,
+            "env_steps_per_s": rate, "plies": plies, "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%S")}
     path = _cache_path()
     try:
         data = json.load(open(path))

@@ -2,22 +2,30 @@
 //
 // A team of L lanes (L = 32, 16, 8 or 4: 1, 2, 4 or 8 games per warp) owns
 // one game at a time.  The game lives in a team-private shared-memory record
-// (SmemGame): the 288-byte per-game state that persists in HBM between
-// launches, the board (piece id per square), 128-bit square sets kept up to
-// date ply by ply (own pieces, movable non-Scouts and Scouts per player),
-// occupancy per column, and the 1,264-byte legal-move mask of the player to
-// move.
+// (SmemGame, 1,168 bytes): the 288-byte per-game state that persists in HBM
+// between launches, the board (piece id per square), 128-bit square sets
+// kept up to date ply by ply (own pieces, movable non-Scouts and Scouts per
+// player), occupancy per column, and the moves of the player to move as a
+// count and a descriptor per from-square.  The 1,264-byte legal mask is an
+// output only: the move generator writes it straight into the caller's row
+// in global memory (no shared-memory copy of it is kept).
 //
 // Move generation: non-Scout moves of the whole board come from four shifted
 // square sets; lane j of the team records those of its segment of 25, 13, 7
 // or 4 from-squares (L = 4, 8, 16, 32), each from-square's (at most four)
-// destinations OR-ed into the mask as one window of at most 21 bits (one or
-// two shared atomics).  Each Scout takes one lane (two on 4-lane teams); its
-// slides come from the row and column occupancy with find-first-set.  The
-// scalar part of a ply (apply, battle, rule state) runs on the team's first
-// lane; all collectives are team-masked, so the teams of a warp run in
-// lockstep when their games take the same path and serialize harmlessly when
-// they do not.
+// destinations as one window of at most 21 mask bits (plain stores: two
+// windows never share a 32-bit word).  Each Scout takes one lane (two on
+// 4-lane teams); its slides come from the row and column occupancy with
+// find-first-set, and its mask bits are ORed in word by word.  A move is
+// chosen from the per-square counts (which square) and the square's
+// descriptor (which destination), not from the mask.  The scalar part of a
+// ply (apply, battle, rule state) runs on the team's first lane; all
+// collectives are team-masked, so the teams of a warp run in lockstep when
+// their games take the same path and serialize harmlessly when they do not.
+// A team's lanes reach every collective together: where lanes read a value
+// that a later phase rewrites (the ending of a ply before a restart, the
+// records before an illegal action's re-generation) a team barrier separates
+// the reads from the writes.
 //
 // Rules follow App. A of arXiv 2511.07312 (Tab. pieces, Tab. chase), the
 // two-square and chasing state machines of App. B.2-B.3, the k-move rule and
@@ -46,6 +54,13 @@ constexpr int kMaskBytes = 1264;
 constexpr int kMaskWordsAlloc = 316;   // the output layout: 1,264 bytes
 constexpr int kSegMax = 25;            // from-square segments (one per lane; 25 of 4 squares for 32 lanes)
 constexpr int kCntBytes = 128;         // per-square move counts: 100 squares padded to 128 bytes
+// Move descriptor of a from-square (SmemGame::desc, 16 bits): a non-Scout's
+// legal moves as kDescStep | bits 0-3 (to s-10, s-1, s+1, s+10); a Scout's as
+// south | west << 4 | east << 8 | north << 12 (squares slid in each
+// direction, the capture included: at most 9 each, so neither marker is a
+// Scout's); a Scout some of whose moves a rule forbids as kDescFiltered (its
+// moves are rebuilt on demand).
+constexpr uint16_t kDescStep = 0xFFF0u, kDescFiltered = 0xEEEEu;
 constexpr int kPiCap = 128;            // chase positions per game (k <= 255 -> <= 128 threats)
 constexpr int kPiWords = 2 * kPiCap;   // each: hash of the chaser's pieces, hash of the chased side's pieces
 constexpr int kRing = 256;             // moves of history per game
@@ -102,17 +117,37 @@ struct __align__(16) SmemGame {
     uint16_t h0, h1;          // actions played 1 and 2 plies ago (0xFFFF none)
     uint8_t flag_pid[2];
     uint8_t scout_pid[2][8];  // the Scouts of each side in piece-id order (kNone after the last)
-    uint8_t pad[6];
+    uint8_t gen_chase;        // the last generation filtered all moves by the chasing rule
+    uint8_t pad[5];
     uint64_t pi_theirs[4];    // chased-side hash of chase positions n_pi-4 .. n_pi-1 (slot i & 3)
     uint64_t pi_mine[4];      // the chaser's hash of the same positions
     uint32_t stat[8];         // counters of the current launch (kept by the env's step loop)
-    uint8_t sq_cnt[kCntBytes];// moves per from-square in G->mask (written with the mask; zero past square 99)
-    uint32_t mask[kMaskWordsAlloc];
+    uint8_t sq_cnt[kCntBytes];// legal moves per from-square of the player to move (zero past square 99)
+    // -- the descriptors come last: code that records moves as mask rows
+    //    (gen_moves<L, true>, the persistent step) never touches them and
+    //    keeps its records kRowsGameBytes apart
+    uint16_t desc[kSquares];  // move descriptor per from-square (valid where sq_cnt > 0, see kDescStep)
+    uint8_t pad2[8];
 };
-static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 6 + 64 + 32 + kCntBytes + 4 * kMaskWordsAlloc,
+static_assert(sizeof(SmemGame) == 288 + 112 + 96 + 20 + 4 + 2 + 16 + 6 + 64 + 32 + kCntBytes + 2 * kSquares + 8,
               "SmemGame layout");
-static_assert(offsetof(SmemGame, sq_cnt) % 16 == 0 && offsetof(SmemGame, mask) == offsetof(SmemGame, sq_cnt) + kCntBytes,
-              "per-square counts and mask are zeroed as one run of 16-byte words");
+static_assert(offsetof(SmemGame, sq_cnt) % 16 == 0, "per-square counts are read as 16-byte words");
+// A game record whose moves are recorded as mask rows (row mode, the
+// persistent step) has no descriptors: its kRowsGameBytes are followed
+// directly by the 1,264-byte mask of the player to move (rows_of), so that
+// the per-square counts and the mask are one run of 16-byte words.
+constexpr int kRowsGameBytes = (int)offsetof(SmemGame, desc);
+constexpr int kRowsRecordBytes = kRowsGameBytes + kMaskBytes;
+static_assert(kRowsGameBytes % 16 == 0 && kRowsGameBytes == (int)offsetof(SmemGame, sq_cnt) + kCntBytes,
+              "row-mode records: counts then mask, 16-byte aligned");
+__device__ __forceinline__ uint32_t* rows_of(SmemGame* G)
+{
+    return reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(G) + kRowsGameBytes);
+}
+__device__ __forceinline__ const uint32_t* rows_of(const SmemGame* G)
+{
+    return reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(G) + kRowsGameBytes);
+}
 static_assert(sizeof(SmemGame) % 16 == 0, "SmemGame alignment");
 constexpr int kGameHead = 288 + 112;   // core + board: the part copied from a root
 
@@ -208,6 +243,14 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
     c = __popc(m & 0x3u);    if (n >= c) { n -= c; m >>= 2;  pos += 2; }
     c = (int)(m & 1u);       if (n >= c) { pos += 1; }
     return pos;
+}
+
+// The n-th set bit (ascending) of a 64-bit word.
+__device__ __forceinline__ int nth_set_bit64(uint64_t x, int n)
+{
+    const uint32_t lo = (uint32_t)x;
+    const int cl = __popc(lo);
+    return n < cl ? nth_set_bit(lo, n) : 32 + nth_set_bit((uint32_t)(x >> 32), n - cl);
 }
 
 __device__ __forceinline__ bool enemy_of(uint8_t o, int P) { return o < kPieces && (int)(o / 40) != P; }
@@ -540,33 +583,97 @@ template <int L> struct Seg {
 };
 
 // ----------------------------------------------------------------- move generation
-// Counts (and, if write_mask, records in G->mask and G->sq_cnt) the moves of
-// player P.  physical: movement rules only (App. A "Piece details");
-// otherwise the two-square and chasing rules filter as rule_flags says.
-// Team-uniform result.
+// Slides of the Scout on square s of player P: squares it can slide south,
+// west, east and north, stopping before a lake or an own piece and on the
+// first enemy piece (included).  occ: every piece; enm: the enemy pieces.
+struct Runs {
+    int ns, nw, ne, nn;
+};
+__device__ __forceinline__ Runs scout_runs(const SmemGame* G, int s, Set128 occ, Set128 enm)
+{
+    const int r = s / 10, c = s - 10 * r;
+    const uint32_t rowocc = bits_at(occ, 10 * r, 10) | ((r == 4 || r == 5) ? kLakeRow : 0u);
+    const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
+    // empty squares in each direction, then whether the blocker is an enemy
+    // piece (its square is in enm; a lake is in neither set)
+    const uint32_t e = rowocc >> (c + 1);
+    const int runE = e ? __ffs(e) - 1 : 9 - c;
+    const int capE = (e && test128(enm, s + runE + 1)) ? 1 : 0;
+    const uint32_t w = rowocc & ((1u << c) - 1u);
+    const int hw = w ? 31 - __clz(w) : -1;
+    const int capW = (hw >= 0 && test128(enm, 10 * r + hw)) ? 1 : 0;
+    const uint32_t n = colocc >> (r + 1);
+    const int runN = n ? __ffs(n) - 1 : 9 - r;
+    const int capN = (n && test128(enm, s + 10 * (runN + 1))) ? 1 : 0;
+    const uint32_t so = colocc & ((1u << r) - 1u);
+    const int hs = so ? 31 - __clz(so) : -1;
+    const int capS = (hs >= 0 && test128(enm, 10 * hs + c)) ? 1 : 0;
+    Runs R;
+    R.ne = runE + capE;
+    R.nw = c - 1 - hw + capW;
+    R.nn = runN + capN;
+    R.ns = r - 1 - hs + capS;
+    return R;
+}
+
+// The destinations (a set over to-squares) of a Scout with slides R.
+__device__ __forceinline__ Set128 scout_set(int s, const Runs& R)
+{
+    const int r = s / 10, c = s - 10 * r;
+    Set128 d = or128(range128(s + 1, R.ne), range128(s - R.nw, R.nw));
+    d = or128(d, column128(c, r + 1, r + R.nn));
+    return or128(d, column128(c, r - R.ns, r - 1));
+}
+
+// Counts (and, if write_mask, records) the moves of player P; with mdst,
+// also writes them as the 1,264-byte legal mask of the output layout to
+// mdst (bit a&7 of byte a>>3 for action a = from*100 + to; the row is cleared
+// first).  physical: movement rules only (App. A "Piece details"); otherwise
+// the two-square and chasing rules filter as rule_flags says.  Team-uniform
+// result.  The records are the moves per from-square (G->sq_cnt) and either
+// a descriptor per from-square (G->desc; mdst, if any, is an output row in
+// global memory) or, with kRows, the mask itself in mdst (a shared-memory
+// buffer that the caller's selection reads; mdst is required then).
 //
 // Non-Scout moves come from four shifted square sets over the whole board;
-// each lane records those of its own segment, one window of at most 21 mask
-// bits per from-square (to-squares s-10, s-1, s+1, s+10 are bits 101s-10,
-// 101s-1, 101s+1, 101s+10).  Scouts take one lane each; a Scout's row and
-// column slides are one run of mask bits around bit 101s (to-squares s+j on
-// its row are bits 101s+j, those on its column bits 101s+10k).  Destinations
-// that a rule may forbid (those of the piece under the two-square rule; all
-// moves while a chase position can recur) go through filter_dests.
-template <int L>
+// each lane records those of its own segment of from-squares.  A non-Scout's
+// moves are one window of at most 21 mask bits (to-squares s-10, s-1, s+1,
+// s+10 are bits 101s-10, 101s-1, 101s+1, 101s+10); two windows never share a
+// 32-bit word, so an output row gets each with plain stores, before the
+// Scouts' bits (shared-memory rows take atomic ORs throughout).  Scouts take
+// one lane each; a Scout's row and column slides are written word by word
+// with atomic ORs.  Moves that a rule may forbid (those of the piece under
+// the two-square rule; all moves while a chase position can recur) go
+// through filter_dests.
+template <int L, bool kRows = false>
 __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule_flags, bool physical,
-                                      bool write_mask, const uint64_t* pi)
+                                      bool write_mask, const uint64_t* pi, uint32_t* mdst)
 {
     const Team<L> T;
     constexpr int SW = Seg<L>::W;
+    if constexpr (kRows) mdst = rows_of(G);   // row mode: the mask follows the record (mdst is ignored)
+    if (!write_mask) mdst = nullptr;
     if (write_mask) {
-        // the per-square counts and the mask are one run of 16-byte words
-        constexpr int kZero = (kCntBytes + 4 * kMaskWordsAlloc) / 16;
-        uint4* z = reinterpret_cast<uint4*>(G->sq_cnt);
+        if constexpr (kRows) {
+            // the per-square counts and the mask: one run of 16-byte words
+            constexpr int kZero = (kCntBytes + kMaskBytes) / 16;
+            uint4* z = reinterpret_cast<uint4*>(G->sq_cnt);
 #pragma unroll
-        for (int k = 0; k < (kZero + L - 1) / L; ++k) {
-            const int i = T.tl + k * L;
-            if (i < kZero) z[i] = make_uint4(0, 0, 0, 0);
+            for (int k = 0; k < (kZero + L - 1) / L; ++k) {
+                const int i = T.tl + k * L;
+                if (i < kZero) z[i] = make_uint4(0, 0, 0, 0);
+            }
+        } else {
+            uint4* z = reinterpret_cast<uint4*>(G->sq_cnt);
+            for (int i = T.tl; i < kCntBytes / 16; i += L) z[i] = make_uint4(0, 0, 0, 0);
+            if (mdst) {
+                uint4* m4 = reinterpret_cast<uint4*>(mdst);
+#pragma unroll
+                for (int k = 0; k < (kMaskBytes / 16 + L - 1) / L; ++k) {
+                    const int i = T.tl + k * L;
+                    if (i < kMaskBytes / 16) m4[i] = make_uint4(0, 0, 0, 0);
+                }
+            }
         }
     }
     const int ts_pid = G->c.ts_pid[P];
@@ -575,8 +682,9 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
     const int ts_from = ts_on ? G->c.sq[ts_pid] : -1;
     const bool chase_on = !physical && (rule_flags & kChase) && G->c.chaser == P && G->c.n_pi > 0 &&
                           chase_live(G, T, pi, P);
+    if (!kRows && write_mask && T.leader()) G->gen_chase = chase_on ? 1 : 0;
     const PlyCtx x = make_ctx(G);
-    T.sync();   // mask zeroed before any atomic
+    T.sync();   // counts and mask row cleared before anything is recorded
     const Set128 own = ld128(G->bocc[P]), enm = ld128(G->bocc[1 - P]), mv = ld128(G->bmov[P]);
     // empty or enemy squares
     const Set128 fre{~own.lo & ~kLakesLo, ~own.hi & kValidHi};
@@ -602,9 +710,13 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             d = filter_dests(G, P, s, s == ts_from, true, x, pi, d);
             const int k = popc128(d);
             cnt += k;
-            if (write_mask) {
-                or_row(G->mask, s, d);
+            if (write_mask && k) {
                 G->sq_cnt[s] = (uint8_t)k;
+                if (!kRows)
+                    G->desc[s] = (uint16_t)(kDescStep | (s >= 10 && test128(d, s - 10) ? 1u : 0u) |
+                                            (s >= 1 && test128(d, s - 1) ? 2u : 0u) | (test128(d, s + 1) ? 4u : 0u) |
+                                            (test128(d, s + 10) ? 8u : 0u));
+                if (mdst) or_row(mdst, s, d);
             }
         }
     } else {
@@ -621,9 +733,13 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
             d = filter_dests(G, P, s, true, false, x, pi, d);
             const int k = popc128(d);
             cnt += k;
-            if (write_mask) {
-                or_row(G->mask, s, d);
+            if (write_mask && k) {
                 G->sq_cnt[s] = (uint8_t)k;
+                if (!kRows)
+                    G->desc[s] = (uint16_t)(kDescStep | (s >= 10 && test128(d, s - 10) ? 1u : 0u) |
+                                            (s >= 1 && test128(d, s - 1) ? 2u : 0u) | (test128(d, s + 1) ? 4u : 0u) |
+                                            (test128(d, s + 10) ? 8u : 0u));
+                if (mdst) or_row(mdst, s, d);
             }
             moving &= ~ts_bit;
             fe &= ~ts_bit; fw &= ~ts_bit; fn &= ~ts_bit; fs &= ~ts_bit;
@@ -634,67 +750,67 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                 const int c = __ffs(moving) - 1;
                 moving &= moving - 1;
                 const int s = off + c;
-                uint32_t pat = ((fs >> c) & 1u) | (((fw >> c) & 1u) << 9) | (((fe >> c) & 1u) << 11) |
-                               (((fn >> c) & 1u) << 20);
-                G->sq_cnt[s] = (uint8_t)__popc(pat);
-                int base = 101 * s - 10;
-                if (s == 0) { pat >>= 10; base = 0; }   // square 0 has no south or west move
-                const uint64_t v = (uint64_t)pat << (base & 31);
-                atomicOr(&G->mask[base >> 5], (uint32_t)v);
-                if (v >> 32) atomicOr(&G->mask[(base >> 5) + 1], (uint32_t)(v >> 32));
+                if constexpr (kRows) {
+                    uint32_t pat = ((fs >> c) & 1u) | (((fw >> c) & 1u) << 9) | (((fe >> c) & 1u) << 11) |
+                                   (((fn >> c) & 1u) << 20);
+                    G->sq_cnt[s] = (uint8_t)__popc(pat);
+                    int base = 101 * s - 10;
+                    if (s == 0) { pat >>= 10; base = 0; }   // square 0 has no south or west move
+                    const uint64_t v = (uint64_t)pat << (base & 31);
+                    atomicOr(&mdst[base >> 5], (uint32_t)v);
+                    if (v >> 32) atomicOr(&mdst[(base >> 5) + 1], (uint32_t)(v >> 32));
+                } else {
+                    const uint32_t dirs = ((fs >> c) & 1u) | (((fw >> c) & 1u) << 1) | (((fe >> c) & 1u) << 2) |
+                                          (((fn >> c) & 1u) << 3);
+                    G->sq_cnt[s] = (uint8_t)__popc(dirs);
+                    G->desc[s] = (uint16_t)(kDescStep | dirs);
+                    if (mdst) {
+                        uint32_t pat = (dirs & 1u) | ((dirs & 2u) << 8) | ((dirs & 4u) << 9) | ((dirs & 8u) << 17);
+                        int base = 101 * s - 10;
+                        if (s == 0) { pat >>= 10; base = 0; }   // square 0 has no south or west move
+                        const uint64_t v = (uint64_t)pat << (base & 31);
+                        mdst[base >> 5] = (uint32_t)v;
+                        if (v >> 32) mdst[(base >> 5) + 1] = (uint32_t)(v >> 32);
+                    }
+                }
             }
         }
     }
-    // Scouts, one per lane: slides along the row and the column, stopping
-    // before a lake or an own piece and on the first enemy piece.
+    if (!kRows && mdst) T.sync();   // the windows are in place before the Scouts' bits are ORed in
+    // Scouts, one per lane
+    const Set128 occ{own.lo | enm.lo, own.hi | enm.hi};
     for (int si = T.tl; si < 8; si += L) {
         const int spid = G->scout_pid[P][si];
         if (spid != kNone && (G->c.flags[spid] & 1)) {
-            const int s = G->c.sq[spid], r = s / 10, c = s - 10 * r;
-            const uint32_t lake = (r == 4 || r == 5) ? kLakeRow : 0u;
-            const uint32_t rowocc = bits_at(Set128{own.lo | enm.lo, own.hi | enm.hi}, 10 * r, 10) | lake;
-            // slide lengths: empty squares east/west/north/south, then whether
-            // the blocker is an enemy (a capture ends the slide)
-            // (the blocker is an enemy piece when its square is in enm; a lake is in neither)
-            const uint32_t e = rowocc >> (c + 1);
-            const int runE = e ? __ffs(e) - 1 : 9 - c;
-            const int capE = (e && test128(enm, s + runE + 1)) ? 1 : 0;
-            const uint32_t w = rowocc & ((1u << c) - 1u);
-            const int hw = w ? 31 - __clz(w) : -1;
-            const int runW = c - 1 - hw;
-            const int capW = (hw >= 0 && test128(enm, 10 * r + hw)) ? 1 : 0;
-            const uint32_t colocc = G->colocc[c] | ((c == 2 || c == 3 || c == 6 || c == 7) ? kLakeCol : 0u);
-            const uint32_t n = colocc >> (r + 1);
-            const int runN = n ? __ffs(n) - 1 : 9 - r;
-            const int capN = (n && test128(enm, s + 10 * (runN + 1))) ? 1 : 0;
-            const uint32_t so = colocc & ((1u << r) - 1u);
-            const int hs = so ? 31 - __clz(so) : -1;
-            const int runS = r - 1 - hs;
-            const int capS = (hs >= 0 && test128(enm, 10 * hs + c)) ? 1 : 0;
-            const int ne = runE + capE, nw = runW + capW, nn = runN + capN, ns = runS + capS;
-            int cnt_sc = ne + nw + nn + ns;
+            const int s = G->c.sq[spid];
+            const Runs R = scout_runs(G, s, occ, enm);
+            int cnt_sc = R.ne + R.nw + R.nn + R.ns;
             if (cnt_sc && (chase_on || s == ts_from)) {
-                Set128 d = or128(range128(s + 1, ne), range128(s - nw, nw));
-                d = or128(d, column128(c, r + 1, r + nn));
-                d = or128(d, column128(c, r - ns, r - 1));
-                d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, d);
+                const Set128 d = filter_dests(G, P, s, s == ts_from, chase_on, x, pi, scout_set(s, R));
                 cnt_sc = popc128(d);
-                if (write_mask) or_row(G->mask, s, d);
+                if (write_mask && cnt_sc) {
+                    if (!kRows) G->desc[s] = kDescFiltered;
+                    if (mdst) or_row(mdst, s, d);
+                }
             } else if (cnt_sc && write_mask) {
-                // mask bits 101s+j (row, j in [-nw, ne]) and 101s+10k (column,
-                // k in [-ns, nn]), j, k != 0, word by word: the column bits are
-                // the bits of [101s-10ns, 101s+10nn] equal to s, so to c, modulo
-                // 10, in word w the bits (c - 2w) mod 10 + 10i (32 = 2 mod 10)
-                const int ctr = 101 * s;
-                const int clo = ctr - 10 * ns, chi = ctr + 10 * nn, rlo = ctr - nw, rhi = ctr + ne;
-                const int wlo = min(clo, rlo) >> 5, whi = max(chi, rhi) >> 5;
-                int m = (c + 640 - 2 * wlo) % 10;
-                for (int wi = wlo; wi <= whi; ++wi) {
-                    const int b0 = 32 * wi;
-                    uint32_t v = ((0x40100401u << m) & range32(clo - b0, chi - b0)) | range32(rlo - b0, rhi - b0);
-                    if (ctr >= b0 && ctr < b0 + 32) v &= ~(1u << (ctr - b0));
-                    if (v) atomicOr(&G->mask[wi], v);
-                    m = m >= 2 ? m - 2 : m + 8;
+                if (!kRows) G->desc[s] = (uint16_t)(R.ns | (R.nw << 4) | (R.ne << 8) | (R.nn << 12));
+                if (mdst) {
+                    // mask bits 101s+j (row, j in [-nw, ne]) and 101s+10k (column,
+                    // k in [-ns, nn]), j, k != 0, word by word: the column bits are
+                    // the bits of [101s-10ns, 101s+10nn] equal to s, so to c, modulo
+                    // 10, in word w the bits (c - 2w) mod 10 + 10i (32 = 2 mod 10)
+                    const int c = s - 10 * (s / 10);
+                    const int ctr = 101 * s;
+                    const int clo = ctr - 10 * R.ns, chi = ctr + 10 * R.nn, rlo = ctr - R.nw, rhi = ctr + R.ne;
+                    const int wlo = min(clo, rlo) >> 5, whi = max(chi, rhi) >> 5;
+                    int m = (c + 640 - 2 * wlo) % 10;
+                    for (int wi = wlo; wi <= whi; ++wi) {
+                        const int b0 = 32 * wi;
+                        uint32_t v = ((0x40100401u << m) & range32(clo - b0, chi - b0)) | range32(rlo - b0, rhi - b0);
+                        if (ctr >= b0 && ctr < b0 + 32) v &= ~(1u << (ctr - b0));
+                        if (v) atomicOr(&mdst[wi], v);
+                        m = m >= 2 ? m - 2 : m + 8;
+                    }
                 }
             }
             if (write_mask && cnt_sc) G->sq_cnt[s] = (uint8_t)cnt_sc;
@@ -706,26 +822,79 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
     return total;
 }
 
+// The destinations of the piece on from-square s of the player to move, as
+// the last generation recorded them: the k-th (ascending) of its G->sq_cnt[s]
+// moves.  A Scout whose moves a rule filters has them rebuilt (same inputs as
+// at generation: nothing moved since).
+__device__ __forceinline__ int kth_dest(const SmemGame* G, int s, int k, const uint64_t* pi, uint32_t rule_flags)
+{
+    const uint32_t d = G->desc[s];
+    if ((d & kDescStep) == kDescStep) {
+        const int b = nth_set_bit(d & 0xFu, k);   // 0 south, 1 west, 2 east, 3 north
+        return s + (b == 0 ? -10 : b == 1 ? -1 : b == 2 ? 1 : 10);
+    }
+    if (d != kDescFiltered) {
+        const int ns = d & 15, nw = (d >> 4) & 15, ne = (d >> 8) & 15;
+        if (k < ns) return s - 10 * (ns - k);
+        k -= ns;
+        if (k < nw) return s - nw + k;
+        k -= nw;
+        if (k < ne) return s + 1 + k;
+        return s + 10 * (k - ne + 1);
+    }
+    const int P = G->c.ply & 1;
+    const Set128 own = ld128(G->bocc[P]), enm = ld128(G->bocc[1 - P]);
+    const int ts_pid = G->c.ts_pid[P];
+    const bool ts_here = (rule_flags & kTwoSquare) && ts_pid != kNone && G->c.ts_len[P] == 4 &&
+                         (G->c.flags[ts_pid] & 1) && G->c.sq[ts_pid] == s;
+    const Set128 ds = filter_dests(G, P, s, ts_here, G->gen_chase != 0, make_ctx(G), pi,
+                                   scout_set(s, scout_runs(G, s, Set128{own.lo | enm.lo, own.hi | enm.hi}, enm)));
+    const int nlo = __popcll(ds.lo);
+    return k < nlo ? nth_set_bit64(ds.lo, k) : 64 + nth_set_bit64(ds.hi, k - nlo);
+}
+
+// Is action a among the legal moves the last generation recorded?
+__device__ __forceinline__ bool move_recorded(const SmemGame* G, int a, const uint64_t* pi, uint32_t rule_flags)
+{
+    if (a < 0 || a >= 10000) return false;
+    const int s = a / 100, to = a - 100 * s;
+    const int n = G->sq_cnt[s];
+    for (int k = 0; k < n; ++k)
+        if (kth_dest(G, s, k, pi, rule_flags) == to) return true;
+    return false;
+}
+
+// Clears a 1,264-byte mask row (the mask of a player without moves).
+template <int L>
+__device__ __forceinline__ void zero_row(uint32_t* mdst, const Team<L>& T)
+{
+    if (mdst) {
+        uint4* m4 = reinterpret_cast<uint4*>(mdst);
+        for (int i = T.tl; i < kMaskBytes / 16; i += L) m4[i] = make_uint4(0, 0, 0, 0);
+    }
+}
+
 // The four mask words holding from-square s's row (actions 100s .. 100s+99),
 // bits of the neighbouring rows cleared; returns the row's first word index.
-__device__ __forceinline__ int row_words(const SmemGame* G, int s, uint32_t r[4])
+__device__ __forceinline__ int row_words(const uint32_t* mask, int s, uint32_t r[4])
 {
     const int b = 100 * s, w = b >> 5, off = b & 31;   // off = 4s mod 32: 0 .. 28
     const int hb = off + 4;                             // row bits in the fourth word
-    r[0] = G->mask[w] & (~0u << off);
-    r[1] = G->mask[w + 1];
-    r[2] = G->mask[w + 2];
-    r[3] = G->mask[w + 3] & (hb >= 32 ? ~0u : ((1u << hb) - 1u));
+    r[0] = mask[w] & (~0u << off);
+    r[1] = mask[w + 1];
+    r[2] = mask[w + 2];
+    r[3] = mask[w + 3] & (hb >= 32 ? ~0u : ((1u << hb) - 1u));
     return w;
 }
 
-// The idx-th set bit (ascending) of G->mask; team-uniform result.  Lane t
-// owns squares [Q*t, Q*t + Q) (Q = 128 / L) and sums their move counts from
-// G->sq_cnt; a scan over the team finds the lane holding move idx, that
-// lane finds the square (per-byte prefix sums of its count words) and then
-// the bit within the square's mask row.
-template <int L>
-__device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
+// The idx-th legal action (ascending action order) of the player to move;
+// team-uniform result.  Lane t owns squares [Q*t, Q*t + Q) (Q = 128 / L) and
+// sums their move counts from G->sq_cnt; a scan over the team finds the lane
+// holding move idx, that lane finds the square (per-byte prefix sums of its
+// count words) and then the move among the square's own: from the square's
+// mask row (row mode, rows_of) or from its descriptor (kth_dest).
+template <int L, bool kRows>
+__device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx, const uint64_t* pi, uint32_t rule_flags)
 {
     const Team<L> T;
     constexpr int NW = kCntBytes / L / 4;   // count words per lane: 8, 4, 2, 1
@@ -771,37 +940,40 @@ __device__ __forceinline__ int select_impl(const SmemGame* G, uint32_t idx)
         const int b = (__ffs(__vcmpgtu4(pre, 0x01010101u * (uint32_t)k)) - 1) >> 3;
         if (b > 0) k -= (int)((pre >> (8 * (b - 1))) & 0xFFu);
         const int s = 4 * (NW * t + j) + b;
-        uint32_t r[4];
-        const int w0 = row_words(G, s, r);
-        int i = 0;
-        while (i < 3 && k >= __popc(r[i])) { k -= __popc(r[i]); ++i; }
-        a = 32 * (w0 + i) + nth_set_bit(r[i], k);
+        if constexpr (kRows) {
+            uint32_t r[4];
+            const int w0 = row_words(rows_of(G), s, r);
+            int i = 0;
+            while (i < 3 && k >= __popc(r[i])) { k -= __popc(r[i]); ++i; }
+            a = 32 * (w0 + i) + nth_set_bit(r[i], k);
+        } else {
+            a = 100 * s + kth_dest(G, s, k, pi, rule_flags);
+        }
     }
     return T.shfl(a, own ? __ffs(own) - 1 : 0);
 }
 
-
-// The magnet policy's move (Tab. notation rho) from the mask of the player
-// to move: piece number uniform_below(w0, pieces with a legal move) in
-// ascending square order, then move number uniform_below(w1, its moves) in
-// ascending action order.  Lane j looks at the own movable pieces of its
-// segment of squares only.  Team-uniform result.
+// The magnet policy's move (Tab. notation rho) for the player to move:
+// piece number uniform_below(w0, pieces with a legal move) in ascending
+// square order, then move number uniform_below(w1, its moves) in ascending
+// action order.  Lane t looks at the squares [Q*t, Q*t + Q) of G->sq_cnt
+// (Q = 128 / L).  Team-uniform result.
 template <int L>
-__device__ __forceinline__ int magnet_impl(const SmemGame* G, uint32_t w0, uint32_t w1)
+__device__ __forceinline__ int magnet_impl(const SmemGame* G, uint32_t w0, uint32_t w1, const uint64_t* pi,
+                                           uint32_t rule_flags)
 {
     const Team<L> T;
-    constexpr int SW = Seg<L>::W;
-    const int t = T.tl, P = G->c.ply & 1;
-    const int lo = SW * t;
-    const Set128 own = or128(ld128(G->bmov[P]), ld128(G->bsco[P]));
-    uint32_t cand = lo < kSquares ? bits_at(own, lo, min(SW, kSquares - lo)) : 0u;
-    uint32_t live = 0;   // bit i: square lo + i has a legal move
-    while (cand) {
-        const int i = __ffs(cand) - 1;
-        cand &= cand - 1;
-        uint32_t r[4];
-        row_words(G, lo + i, r);
-        if (r[0] | r[1] | r[2] | r[3]) live |= 1u << i;
+    constexpr int NW = kCntBytes / L / 4;
+    const int t = T.tl;
+    // bit i: square 4*NW*t + i has a legal move
+    uint32_t live = 0;
+    const uint32_t* cw = reinterpret_cast<const uint32_t*>(G->sq_cnt) + NW * t;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint32_t v = cw[j];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if ((v >> (8 * b)) & 0xFFu) live |= 1u << (4 * j + b);
     }
     const int np = __popc(live);
     int incl = np;
@@ -815,27 +987,18 @@ __device__ __forceinline__ int magnet_impl(const SmemGame* G, uint32_t w0, uint3
     const uint32_t own_lane = T.ballot(want >= incl - np && want < incl);
     int a = -1;
     if (own_lane & (1u << t)) {
-        const int s = lo + nth_set_bit(live, want - (incl - np));
-        uint32_t r[4];
-        const int w = row_words(G, s, r);
-        const int m = __popc(r[0]) + __popc(r[1]) + __popc(r[2]) + __popc(r[3]);
-        int k = (int)uniform_below(w1, (uint32_t)m);
-        int i = 0;
-        while (i < 3 && k >= __popc(r[i])) { k -= __popc(r[i]); ++i; }
-        a = 32 * (w + i) + nth_set_bit(r[i], k);
+        const int s = 4 * NW * t + nth_set_bit(live, want - (incl - np));
+        const int k = (int)uniform_below(w1, (uint32_t)G->sq_cnt[s]);
+        a = 100 * s + kth_dest(G, s, k, pi, rule_flags);
     }
     return T.shfl(a, own_lane ? __ffs(own_lane) - 1 : 0);
 }
 
-template <int L>
-__device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx)
+template <int L, bool kRows = false>
+__device__ __noinline__ int select_action(const SmemGame* G, Team<L>, uint32_t idx, const uint64_t* pi,
+                                          uint32_t rule_flags)
 {
-    return select_impl<L>(G, idx);
-}
-
-__device__ __forceinline__ bool mask_has(const SmemGame* G, int a)
-{
-    return a >= 0 && a < 10000 && ((G->mask[a >> 5] >> (a & 31)) & 1u);
+    return select_impl<L, kRows>(G, idx, pi, rule_flags);
 }
 
 // Is the flag of `side` captured?
@@ -985,18 +1148,20 @@ __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* r
 // The idx-th legal action (a < 0) or action a, then played: selection and
 // the move in one call (the rollouts' ply).  Returns the action.
 template <int L>
-__device__ __noinline__ int select_apply(SmemGame* G, Team<L>, int a, uint32_t idx, uint16_t* ring, uint64_t* pi)
+__device__ __noinline__ int select_apply(SmemGame* G, Team<L>, int a, uint32_t idx, uint16_t* ring, uint64_t* pi,
+                                         uint32_t rule_flags)
 {
-    if (a < 0) a = select_impl<L>(G, idx);
+    if (a < 0) a = select_impl<L, false>(G, idx, pi, rule_flags);
     apply_impl<L>(G, a, ring, pi);
     return a;
 }
 
 // The magnet policy's move for Philox words (w0, w1), then played.
 template <int L>
-__device__ __noinline__ int magnet_apply(SmemGame* G, Team<L>, uint32_t w0, uint32_t w1, uint16_t* ring, uint64_t* pi)
+__device__ __noinline__ int magnet_apply(SmemGame* G, Team<L>, uint32_t w0, uint32_t w1, uint16_t* ring, uint64_t* pi,
+                                         uint32_t rule_flags)
 {
-    const int a = magnet_impl<L>(G, w0, w1);
+    const int a = magnet_impl<L>(G, w0, w1, pi, rule_flags);
     apply_impl<L>(G, a, ring, pi);
     return a;
 }
@@ -1054,25 +1219,38 @@ struct PlyResult {
 };
 
 // Ending after the ply just played (App. A "Game Summary", App. D.1); also
-// leaves the mask of the player to move in G->mask and its count in n.
-template <int L>
+// records the moves of the player to move (G->sq_cnt, G->desc; their mask in
+// mdst when given) and their count in n.  A captured flag ends the game
+// before any move is recorded.
+template <int L, bool kRows = false>
 __device__ __forceinline__ void check_end(SmemGame* G, const Team<L>& T, const Rules& R, const uint64_t* pi,
-                                          int& code, int& winner, int& n)
+                                          int& code, int& winner, int& n, uint32_t* mdst)
 {
     const int Q = G->c.ply & 1, P = 1 - Q;
     code = 0;
     winner = -1;
     n = 0;
-    if (flag_dead(G, Q)) { code = 1; winner = P; return; }
-    n = gen_moves(G, T, Q, R.flags, false, true, pi);
-    if (n == 0) {
-        const int phys = gen_moves(G, T, P, R.flags, true, false, pi);
-        code = phys == 0 ? 3 : 2;
-        winner = phys == 0 ? -1 : P;
-        return;
+    if (flag_dead(G, Q)) {
+        code = 1;
+        winner = P;
+    } else {
+        n = gen_moves<L, kRows>(G, T, Q, R.flags, false, true, pi, mdst);
+        if (n == 0) {
+            const int phys = gen_moves<L, false>(G, T, P, R.flags, true, false, pi, (uint32_t*)nullptr);
+            code = phys == 0 ? 3 : 2;
+            winner = phys == 0 ? -1 : P;
+        } else if (G->c.battleless >= R.k) {
+            code = 4;
+        } else if (G->c.ply >= R.cap) {
+            code = 5;
+        }
     }
-    if (G->c.battleless >= R.k) { code = 4; return; }
-    if (G->c.ply >= R.cap) { code = 5; return; }
+    // Every lane has read the state the ending depends on before any lane
+    // goes on to change it (a restart or the next rollout rewrites the game
+    // record): without this barrier a lane that lags could read the new game
+    // and take a different ending than its team, and the team's lanes would
+    // then meet at different collectives.
+    T.sync();
 }
 
 // The acting player of a fresh position has no legal move (n == 0).
@@ -1081,17 +1259,9 @@ __device__ __forceinline__ void start_end(SmemGame* G, const Team<L>& T, const R
                                           int& winner)
 {
     const int P = G->c.ply & 1;
-    const int phys = gen_moves(G, T, 1 - P, R.flags, true, false, pi);
+    const int phys = gen_moves<L, false>(G, T, 1 - P, R.flags, true, false, pi, (uint32_t*)nullptr);
     code = phys == 0 ? 3 : 2;
     winner = phys == 0 ? -1 : 1 - P;
-}
-
-template <int L>
-__device__ __forceinline__ void zero_mask(SmemGame* G, const Team<L>& T)
-{
-    uint4* m4 = reinterpret_cast<uint4*>(G->mask);
-    for (int i = T.tl; i < kMaskWordsAlloc / 4; i += L) m4[i] = make_uint4(0, 0, 0, 0);
-    T.sync();
 }
 
 }  // namespace stg

@@ -103,37 +103,30 @@ __device__ __forceinline__ void latch(int32_t* status, int code, int slot)
     atomicMin(&status[1], slot);
 }
 
+// The persistent step renders each ply's mask into a per-team staging
+// buffer in shared memory and writes it to its ring row with one bulk
+// asynchronous copy (TMA) issued by the team's first lane; the copy runs
+// while the team selects and plays the next move (selection reads the move
+// records, not the mask), and the buffer is not written again before
+// mask_free.  Both addresses and the size are multiples of 16 bytes (the
+// buffers sit at 16-byte offsets of the dynamic shared memory; ring rows are
+// 1,264 bytes apart from a 256-byte-aligned base).
 template <int L>
-__device__ __forceinline__ void write_mask(const SmemGame* G, const Team<L>& T, uint8_t* dst)
-{
-    const uint4* src = reinterpret_cast<const uint4*>(G->mask);
-    uint4* d = reinterpret_cast<uint4*>(dst);
-    for (int i = T.tl; i < kMaskBytes / 16; i += L) d[i] = src[i];
-}
-
-// The persistent step writes each 1,264-byte mask with one bulk asynchronous
-// copy (TMA) from shared memory, issued by the team's first lane, instead of
-// the team's 16-byte stores; the copy runs while the team selects and plays
-// the next move, and the mask is not touched again before mask_free.
-// Both addresses and the size are multiples of 16 bytes (the mask sits at a
-// 16-byte offset of the 16-byte-aligned game record; ring rows are 1,264
-// bytes apart from a 256-byte-aligned base).
-template <int L>
-__device__ __forceinline__ void write_mask_async(const SmemGame* G, const Team<L>& T, uint8_t* dst)
+__device__ __forceinline__ void write_mask_async(const uint32_t* staged, const Team<L>& T, uint8_t* dst)
 {
     // the lanes' mask writes (generic proxy) become visible to the copy engine
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     T.sync();
     if (T.leader()) {
-        const uint32_t src = static_cast<uint32_t>(__cvta_generic_to_shared(G->mask));
+        const uint32_t src = static_cast<uint32_t>(__cvta_generic_to_shared(staged));
         asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                      :: "l"(dst), "r"(src), "r"((uint32_t)kMaskBytes) : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
 }
 
-// Before the mask is written again: the leader waits until its copies have
-// read the mask out of shared memory.
+// Before the staging buffer is written again: the leader waits until its
+// copies have read it.
 template <int L>
 __device__ __forceinline__ void mask_free(const Team<L>& T)
 {
@@ -222,57 +215,77 @@ __device__ __forceinline__ void new_game(SmemGame* G, const Team<L>& T, const Re
     T.sync();
 }
 
-// Auto-reset inside a launch: the new game, then the mask of its player to
-// move (its move count returned).  One out-of-line call on the rare path.
-template <int L>
+// Auto-reset inside a launch: the new game, then the moves of its player to
+// move (recorded, their mask in mdst when given; their count returned).  One
+// out-of-line call on the rare path.
+template <int L, bool kRows>
 __device__ __noinline__ int restart_slot(SmemGame* G, Team<L>, ResetSrc src, uint32_t k0, uint32_t k1,
                                          uint32_t rule_flags, uint32_t slot, uint32_t episode, uint16_t* ring,
-                                         uint64_t* pi)
+                                         uint64_t* pi, uint32_t* mdst)
 {
     const Team<L> T;
     new_game(G, T, src, k0, k1, slot, episode, ring, pi);
-    return gen_moves(G, T, G->c.ply & 1, rule_flags, false, true, pi);
+    return gen_moves<L, kRows>(G, T, G->c.ply & 1, rule_flags, false, true, pi, mdst);
 }
 
-// One ply of slot `slot` (App. B.1): the mask of the player to move is in
-// G->mask with count n.  given: the supplied action or -1 for the random
-// policy.
-template <int L>
+// One ply of slot `slot` (App. B.1): the moves of the player to move are
+// recorded in G (sq_cnt, and desc or, with kRows, the mask rows in mdst), n
+// of them.  given: the supplied action or -1 for the random policy.  mdst:
+// the row that receives the mask of the player to move after the ply (of the
+// new game after an auto-reset; all zero for a finished game), or null
+// (required with kRows).  staged: a bulk copy may still be reading mdst (the
+// team's staging buffer), so it is waited for before mdst is written.  An
+// illegal supplied action changes nothing and leaves mdst untouched.
+template <int L, bool kRows = false>
 __device__ __forceinline__ PlyResult env_ply(SmemGame* G, const Team<L>& T, int& n, const EnvArgs& A, uint32_t slot,
-                                             int given, uint16_t* ring, uint64_t* pi, bool& illegal,
-                                             bool async_mask = false)
+                                             int given, uint16_t* ring, uint64_t* pi, bool& illegal, uint32_t* mdst,
+                                             bool staged = false)
 {
     PlyResult res;
     // the ply index is read by the leader alone, which is the lane that
     // writes it and the only one whose result is used
     res.action = -1; res.code = 0; res.winner = -1; res.ply_idx = T.leader() ? G->c.ply : 0;
     illegal = false;
-    if (G->c.terminated) return res;
+    if (G->c.terminated) {
+        if (staged) mask_free(T);
+        zero_row(mdst, T);
+        T.sync();
+        return res;
+    }
     if (n == 0) {
+        if (staged) mask_free(T);
         start_end(G, T, A.R, pi, res.code, res.winner);
     } else {
         int a = given;
         if (a >= 0) {
-            if (!mask_has(G, a)) { illegal = true; return res; }
+            const bool ok = kRows ? (a < 10000 && ((rows_of(G)[a >> 5] >> (a & 31)) & 1u))
+                                  : move_recorded(G, a, pi, A.R.flags);
+            if (!ok) {
+                illegal = true;
+                T.sync();   // every lane has read the records before the caller rewrites them
+                return res;
+            }
         } else {
             const uint4 w = philox(make_uint4(slot, G->c.episode, (uint32_t)G->c.ply, 2u << 24), A.k0, A.k1);
-            a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
+            a = select_action<L, kRows>(G, T, uniform_below(w.x, (uint32_t)n), pi, A.R.flags);
         }
         apply_move(G, T, a, ring, pi);
         res.action = a;
-        if (async_mask) mask_free(T);
-        check_end(G, T, A.R, pi, res.code, res.winner, n);
+        if (staged) mask_free(T);
+        check_end<L, kRows>(G, T, A.R, pi, res.code, res.winner, n, mdst);
     }
     if (res.code) {
-        if (async_mask) mask_free(T);
         if (A.R.flags & kAutoreset) {
-            n = restart_slot(G, T, A.reset, A.k0, A.k1, A.R.flags, slot, G->c.episode + 1, ring, pi);
+            n = restart_slot<L, kRows>(G, T, A.reset, A.k0, A.k1, A.R.flags, slot, G->c.episode + 1, ring, pi, mdst);
         } else {
             if (T.leader()) G->c.terminated = (uint8_t)res.code;
-            zero_mask(G, T);
+            zero_row(mdst, T);
             n = 0;
+            T.sync();   // every lane sees the game as finished before the next ply reads the record
         }
     }
+    // (apply_move, gen_moves and a restart end with a team barrier: the
+    // record the next ply reads is the same for every lane)
     return res;
 }
 
@@ -324,7 +337,7 @@ __global__ void k_env_reset(EnvArgs A, const uint8_t* setups, const uint8_t* whi
     } else {
         new_game(G, T, A.reset, A.k0, A.k1, (uint32_t)g, episode, ring, pi);
     }
-    const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
+    const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi, (uint32_t*)nullptr);
     if (T.leader()) G->c.n_legal = (uint16_t)n;
     store_core(G, A.core + g, T);
 }
@@ -369,15 +382,17 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     derive_state(G, ring, pi, T);
     const int P = G->c.ply & 1;
     int n = 0;
-    if (G->c.terminated) zero_mask(G, T);
-    else n = gen_moves(G, T, P, A.R.flags, false, true, pi);
+    if (!G->c.terminated) n = gen_moves(G, T, P, A.R.flags, false, true, pi, (uint32_t*)nullptr);
     bool illegal = false;
     const int given = actions ? (int)actions[g] : -1;
     if (A.hist) {
         if (T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
         hist_before(G, T);
     }
-    const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, given, ring, pi, illegal);
+    uint32_t* mdst = mask_out ? reinterpret_cast<uint32_t*>(mask_out + (size_t)g * kMaskBytes) : nullptr;
+    const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, given, ring, pi, illegal, mdst);
+    // an illegal action changed nothing: the mask is the one of the player still to move
+    if (illegal && mdst) gen_moves(G, T, P, A.R.flags, false, true, pi, mdst);
     if (T.leader()) {
         if (A.hist) hist_after(G, A, g, r);
         if (illegal) latch(A.status, ST_ERR_ILLEGAL_ACTION, g);
@@ -396,7 +411,6 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
         }
         G->c.n_legal = (uint16_t)n;
     }
-    if (mask_out) write_mask(G, T, mask_out + (size_t)g * kMaskBytes);
     store_core(G, A.core + g, T);   // an illegal action changed nothing but the history marks
 }
 
@@ -413,7 +427,10 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<L> T;
-    SmemGame* G = team_game<L>(smem);
+    // the team's game record in row mode: no descriptors, the mask of the
+    // player to move right after it (rows_of), which is also the buffer the
+    // bulk copies send to the ring
+    SmemGame* G = reinterpret_cast<SmemGame*>(smem + (size_t)(threadIdx.x / L) * kRowsRecordBytes);
     for (;;) {
         // each team claims its own slots: no collective spans more than one team
         int first = 0;
@@ -428,9 +445,9 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             load_core(G, A.core + g, T);
             build_board(G, T);
             derive_state(G, ring, pi, T);
+            if (mask_ring) mask_free(T);   // the previous slot's last copy has read the staging buffer
             int n = 0;
-            if (G->c.terminated) zero_mask(G, T);
-            else n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
+            if (!G->c.terminated) n = gen_moves<L, true>(G, T, G->c.ply & 1, A.R.flags, false, true, pi, rows_of(G));
             // the launch's counters live in shared memory, not in registers
             // that every engine call would have to save
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
@@ -439,9 +456,13 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             for (int j = 0; j < n_steps; ++j) {
                 bool illegal;
                 if (kHist) hist_before(G, T);
-                const PlyResult r = env_ply(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal, mask_ring != nullptr);
                 const size_t o = (size_t)row * (size_t)A.N + (size_t)g;
                 if (++row == ring_steps) row = 0;
+                // the mask of the player to move after the ply is rendered into
+                // the staging buffer, which the next ply's selection reads, and
+                // leaves it by a bulk copy
+                const PlyResult r = env_ply<L, true>(G, T, n, A, (uint32_t)g, -1, ring, pi, illegal, rows_of(G),
+                                                     mask_ring != nullptr);
                 if (T.leader()) {
                     if (kHist) hist_after(G, A, g, r);
                     count_result(G->stat, r);
@@ -450,9 +471,8 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
                     if (done_ring) done_ring[o] = (uint8_t)r.code;
                     if (ply_ring) ply_ring[o] = (int16_t)r.ply_idx;
                 }
-                if (mask_ring) write_mask_async(G, T, mask_ring + o * kMaskBytes);
+                if (mask_ring) write_mask_async(rows_of(G), T, mask_ring + o * kMaskBytes);
             }
-            if (mask_ring) mask_free(T);   // the next slot's first mask overwrites this one
             if (T.leader()) {
                 uint32_t* gs = A.stats + 8 * (size_t)g;
 #pragma unroll
@@ -483,10 +503,10 @@ __global__ void k_env_sample(EnvArgs A, int16_t* out)
     derive_state(G, ring, pi, T);
     int a = -1;
     if (!G->c.terminated) {
-        const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi);
+        const int n = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, true, pi, (uint32_t*)nullptr);
         if (n > 0) {
             const uint4 w = philox(make_uint4((uint32_t)g, G->c.episode, (uint32_t)G->c.ply, 2u << 24), A.k0, A.k1);
-            a = select_action(G, T, uniform_below(w.x, (uint32_t)n));
+            a = select_action(G, T, uniform_below(w.x, (uint32_t)n), pi, A.R.flags);
         }
     }
     if (T.leader()) out[g] = (int16_t)a;
@@ -555,7 +575,7 @@ __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_posi
         if (T.leader()) latch(A.status, ST_ERR_BAD_POSITION, g);
         return;
     }
-    const int nl = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi);
+    const int nl = gen_moves(G, T, G->c.ply & 1, A.R.flags, false, false, pi, (uint32_t*)nullptr);
     if (T.leader()) {
         G->c.episode = episode;
         G->c.n_legal = (uint16_t)nl;
@@ -818,7 +838,7 @@ struct DeviceGuard {
 };
 
 // Dynamic shared memory of one block of the persistent launch.
-size_t run_smem(int wpb, int gpw) { return (size_t)wpb * gpw * sizeof(SmemGame); }
+size_t run_smem(int wpb, int gpw) { return (size_t)wpb * gpw * kRowsRecordBytes; }
 
 template <int L>
 cudaError_t run_occupancy_t(int wpb, int* occ)

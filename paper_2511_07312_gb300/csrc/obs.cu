@@ -159,12 +159,9 @@ __global__ void k_replay(ReplayArgs A)
             o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
             for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
         }
-        if (A.mask_out) {
-            gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi);
-            const uint4* src = reinterpret_cast<const uint4*>(G->mask);
-            uint4* d = reinterpret_cast<uint4*>(A.mask_out + (size_t)i * kMaskBytes);
-            for (int k = lane; k < kMaskBytes / 16; k += 32) d[k] = src[k];
-        }
+        if (A.mask_out)
+            gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi,
+                      reinterpret_cast<uint32_t*>(A.mask_out + (size_t)i * kMaskBytes));
         __syncwarp();
     }
 }

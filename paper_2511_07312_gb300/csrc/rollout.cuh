@@ -115,6 +115,7 @@ struct __align__(16) RolloutSmem {
     uint64_t pi[kPiWords];
     uint16_t ring[kRing];
     uint8_t types[48];
+    uint32_t mask[kMaskWordsAlloc];   // a legal mask when a kernel needs one in shared memory
 };
 
 // A rollout team's shared-memory record when no history ring is kept; its
@@ -204,14 +205,14 @@ __device__ __forceinline__ int rollout_one(SmemGame* G, uint8_t* types_s, uint64
 {
     begin_rollout(G, types_s, pi, ring, T, R, plan, types, k0, k1, stream, k);
     const int searcher = G->c.ply & 1;
-    int n = gen_moves(G, T, searcher, Rl.flags, false, true, pi);
+    int n = gen_moves(G, T, searcher, Rl.flags, false, true, pi, (uint32_t*)nullptr);
     int code = 0, winner = -1;
     if (n == 0) start_end(G, T, Rl, pi, code, winner);
     for (int d = 0; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, k, (uint32_t)d, 4u << 24), k0, k1);
-        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, ring, pi);
-        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi);
-        check_end(G, T, Rl, pi, code, winner, n);
+        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, ring, pi, Rl.flags);
+        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), ring, pi, Rl.flags);
+        check_end(G, T, Rl, pi, code, winner, n, (uint32_t*)nullptr);
     }
     return tally_slot(code, winner, searcher);
 }
@@ -234,13 +235,13 @@ __device__ __forceinline__ int search_rollout(SmemGame* G, uint8_t* types_s, uin
     // changes when the forced first move is played)
     const int searcher = R->c.ply & 1;
     int code = 0, winner = -1, n = 0;
-    select_apply(G, T, first, 0u, (uint16_t*)nullptr, pi);
-    check_end(G, T, Rl, pi, code, winner, n);
+    select_apply(G, T, first, 0u, (uint16_t*)nullptr, pi, Rl.flags);
+    check_end(G, T, Rl, pi, code, winner, n, (uint32_t*)nullptr);
     for (int d = 1; !code && d < depth; ++d) {
         const uint4 w = philox(make_uint4(stream, c1, (uint32_t)d, 5u << 24), k0, k1);
-        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, (uint16_t*)nullptr, pi);
-        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), (uint16_t*)nullptr, pi);
-        check_end(G, T, Rl, pi, code, winner, n);
+        if (Rl.flags & kMagnet) magnet_apply(G, T, w.x, w.y, (uint16_t*)nullptr, pi, Rl.flags);
+        else select_apply(G, T, -1, uniform_below(w.x, (uint32_t)n), (uint16_t*)nullptr, pi, Rl.flags);
+        check_end(G, T, Rl, pi, code, winner, n, (uint32_t*)nullptr);
     }
     return tally_slot(code, winner, searcher);
 }

@@ -196,11 +196,11 @@ __global__ void k_search_prep(const st_position* pos, int P, Rules Rl, RootState
     uint32_t words[kCompactWords];
     int mine = 0;
     if (!bad_w) {
-        n = gen_moves(&S->g, T, S->g.c.ply & 1, Rl.flags, false, true, S->pi);
+        n = gen_moves(&S->g, T, S->g.c.ply & 1, Rl.flags, false, true, S->pi, S->mask);
         if (n > kSearchMoves) { bad_w = 14; n = 0; }   // more moves than a position can have
         for (int i = 0; i < kCompactWords; ++i) {
             const int w = lane * kCompactWords + i;
-            words[i] = w < kMaskWordsUsed ? S->g.mask[w] : 0u;
+            words[i] = w < kMaskWordsUsed ? S->mask[w] : 0u;
             mine += __popc(words[i]);
         }
     }
@@ -382,17 +382,16 @@ __global__ void k_positions_mask(const st_position* pos, int P, Rules Rl, uint8_
     int n = 0, ts = 0;
     if (!bad) {
         const int Pl = S->g.c.ply & 1;
-        n = gen_moves(&S->g, T, Pl, Rl.flags, false, true, S->pi);
+        n = gen_moves(&S->g, T, Pl, Rl.flags, false, true, S->pi,
+                      mask ? reinterpret_cast<uint32_t*>(mask + (size_t)p * kMaskBytes) : nullptr);
         if (Rl.flags & kTwoSquare) {
-            const int n_ts = gen_moves(&S->g, T, Pl, kTwoSquare, false, false, S->pi);
-            const int n_ph = gen_moves(&S->g, T, Pl, 0u, true, false, S->pi);
+            const int n_ts = gen_moves(&S->g, T, Pl, kTwoSquare, false, false, S->pi, (uint32_t*)nullptr);
+            const int n_ph = gen_moves(&S->g, T, Pl, 0u, true, false, S->pi, (uint32_t*)nullptr);
             ts = n_ts < n_ph;
         }
-    }
-    if (mask) {
+    } else if (mask) {
         uint4* d = reinterpret_cast<uint4*>(mask + (size_t)p * kMaskBytes);
-        const uint4* m = reinterpret_cast<const uint4*>(S->g.mask);
-        for (int i = lane; i < kMaskBytes / 16; i += 32) d[i] = bad ? make_uint4(0, 0, 0, 0) : m[i];
+        for (int i = lane; i < kMaskBytes / 16; i += 32) d[i] = make_uint4(0, 0, 0, 0);
     }
     if (lane == 0) {
         if (n_legal) n_legal[p] = n;

@@ -15,7 +15,7 @@ template <int L>
 static void run(EnvArgs a, int32_t* queue, int S, int gpf, int wpb, int blocks, int16_t* act, int8_t* rew, uint8_t* done,
                 int16_t* ply, uint8_t* mask)
 {
-    const size_t sm = (size_t)wpb * (32 / L) * sizeof(SmemGame);
+    const size_t sm = (size_t)wpb * (32 / L) * kRowsRecordBytes;   // row-mode records, each followed by its mask
     launch(blocks, 32 * wpb, sm, [=] { k_env_run<L, false>(a, queue, S, S, gpf, act, rew, done, ply, mask); });
 }
 

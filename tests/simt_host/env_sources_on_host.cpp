@@ -71,7 +71,7 @@ int main(int argc, char** argv)
         int16_t* ap = act.data(); int8_t* rp = rew.data(); uint8_t* dp = done.data(); int16_t* pp = ply.data();
         uint8_t* mp = mask.data();
         int32_t* qp = &queue;
-        const size_t sm = (size_t)wpb * 4 * sizeof(SmemGame);
+        const size_t sm = (size_t)wpb * 4 * kRowsRecordBytes;   // row-mode records, each followed by its mask
         launch(nblocks, 32 * wpb, sm, [=] { k_env_run<8, true>(a, qp, S, S, gpf, ap, rp, dp, pp, mp); });
     }
     d_now += S;

@@ -32,7 +32,7 @@ HARNESS = os.path.join(ROOT, "tests", "simt_host")
 
 
 def _host_source(text):
-    """The CUDA source with its shared-memory declaration and its bulk-copy
+    """The CUDA source with its shared-memory declarations and its bulk-copy
     inline assembly replaced by the harness's host equivalents."""
     text = text.replace("extern __shared__ __align__(16) unsigned char smem[];",
                         "unsigned char* const smem = emu::block_smem();")
@@ -40,12 +40,13 @@ def _host_source(text):
     text = re.sub(r"(?<!extern )__shared__\s+([A-Za-z_][\w ]*?)\s+([A-Za-z_]\w*)((?:\[[^\]]+\])*)\s*;",
                   lambda m: "auto& %s = *emu::block_static<%s%s>(__LINE__);" % (m.group(2), m.group(1), m.group(3)),
                   text)
+    # the persistent step's bulk copy of a mask staging buffer and its waits
     text = text.replace('asm volatile("fence.proxy.async.shared::cta;" ::: "memory");', ";")
-    text = re.sub(r'const uint32_t src = static_cast<uint32_t>\(__cvta_generic_to_shared\(G->mask\)\);\s*'
+    text = re.sub(r'const uint32_t src = static_cast<uint32_t>\(__cvta_generic_to_shared\(staged\)\);\s*'
                   r'asm volatile\("cp\.async\.bulk\.global\.shared::cta\.bulk_group \[%0\], \[%1\], %2;"\s*'
                   r'::\s*"l"\(dst\), "r"\(src\), "r"\(\(uint32_t\)kMaskBytes\) : "memory"\);\s*'
                   r'asm volatile\("cp\.async\.bulk\.commit_group;" ::: "memory"\);',
-                  "emu::bulk_copy(dst, G->mask, kMaskBytes);", text)
+                  "emu::bulk_copy(dst, staged, kMaskBytes);", text)
     text = text.replace('asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");', "emu::bulk_wait();")
     text = text.replace('asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");', "emu::bulk_wait();")
     assert "asm" not in re.sub(r"//.*", "", text), "inline assembly the harness does not know"
