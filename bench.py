@@ -348,7 +348,7 @@ def main():
         wpb, gpw, gpf, bps = args.wpb, args.gpw, args.gpf or 1, args.bps
     else:
         from paper_2511_07312_gb300 import autotune
-        tuned = autotune.tune(N, device=local)
+        tuned = autotune.tune(N, device=local, final_plies=S)
         wpb, gpw, gpf = tuned["warps_per_block"], tuned["games_per_warp"], tuned["games_per_fetch"]
         bps = tuned.get("blocks_per_sm", 0)
     env.set_launch(wpb, bps, gpf, games_per_warp=gpw)

@@ -30,48 +30,65 @@ def _cache_path():
     return os.path.join(base, "launch_shapes.json")
 
 
-def _key(num_games, device):
-    return "%s|%d|%s" % (torch.cuda.get_device_name(device), num_games, version())
+def _key(num_games, device, plies):
+    return "%s|%d|%d|%s" % (torch.cuda.get_device_name(device), num_games, plies, version())
 
 
-def load(num_games, device=0):
+def load(num_games, device=0, plies=400):
+    """The cached shape for this device, size and launch length (plies per slot), if any."""
     try:
-        return json.load(open(_cache_path())).get(_key(num_games, device))
+        return json.load(open(_cache_path())).get(_key(num_games, device, plies))
     except (OSError, ValueError):
         return None
 
 
-def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False):
+def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False, final_plies=None, finalists=4):
     """Return {"warps_per_block", "games_per_warp", "games_per_fetch",
     "blocks_per_sm", "env_steps_per_s"} of the fastest shape, timed with
-    CUDA events."""
+    CUDA events: every shape on runs of `plies` plies, then (final_plies)
+    the `finalists` fastest again on runs of final_plies plies, the length
+    the caller will launch (how full the last wave of slots is depends on
+    it)."""
+    key_plies = final_plies or plies
     if not force:
-        hit = load(num_games, device)
+        hit = load(num_games, device, key_plies)
         if hit:
             return hit
     env = Env(num_games, seed=12345, device=device)
     ring = env.run(1, 4)
     results = []
+    def timed(wpb, gpw, gpf, bps, n_plies, n_reps):
+        env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
+        env.run(n_plies, 4, out=ring)        # warm-up, captures the graph
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(env.stream)
+        for _ in range(n_reps):
+            env.run(n_plies, 4, out=ring)
+        end.record(env.stream)
+        end.synchronize()
+        return num_games * n_plies * n_reps / (start.elapsed_time(end) / 1000.0)
+
     for wpb in WARPS_PER_BLOCK:
         for gpw in GAMES_PER_WARP:
             for gpf in GAMES_PER_FETCH:
                 for bps in (BLOCKS_PER_SM if gpw >= 4 else (0,)):
                     try:
-                        env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
+                        rate = timed(wpb, gpw, gpf, bps, plies, reps)
                     except RuntimeError:
                         continue
-                    env.run(plies, 4, out=ring)        # warm-up, captures the graph
-                    start = torch.cuda.Event(enable_timing=True)
-                    end = torch.cuda.Event(enable_timing=True)
-                    start.record(env.stream)
-                    for _ in range(reps):
-                        env.run(plies, 4, out=ring)
-                    end.record(env.stream)
-                    end.synchronize()
-                    rate = num_games * plies * reps / (start.elapsed_time(end) / 1000.0)
                     results.append((rate, wpb, gpw, gpf, bps))
                     if verbose:
                         print("wpb %2d gpw %d gpf %d bps %d: %.3e env-steps/s" % (wpb, gpw, gpf, bps, rate), flush=True)
+    if final_plies and final_plies != plies:
+        final = []
+        for _, wpb, gpw, gpf, bps in sorted(results, reverse=True)[:finalists]:
+            rate = timed(wpb, gpw, gpf, bps, final_plies, 2)
+            final.append((rate, wpb, gpw, gpf, bps))
+            if verbose:
+                print("final wpb %2d gpw %d gpf %d bps %d: %.3e env-steps/s" % (wpb, gpw, gpf, bps, rate), flush=True)
+        results = final
+        plies = final_plies
     env.close()
     rate, wpb, gpw, gpf, bps = max(results)
     best = {"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf, "blocks_per_sm": bps,
@@ -81,7 +98,7 @@ def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False):
         data = json.load(open(path))
     except (OSError, ValueError):
         data = {}
-    data[_key(num_games, device)] = best
+    data[_key(num_games, device, key_plies)] = best
     tmp = path + ".tmp.%d" % os.getpid()
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1)

@@ -112,9 +112,10 @@ def test_full_size_65536_games_2000_plies_sampled_slots():
     # checked against the oracle (counters, final snapshot, last 16 plies)
     from paper_2511_07312_gb300 import autotune
     N, S, R = 65536, 2000, 16
-    best = autotune.tune(N)
+    best = autotune.tune(N, final_plies=S)
     env = st.Env(N, seed=1)
-    env.set_launch(best["warps_per_block"], 0, best["games_per_fetch"], games_per_warp=best["games_per_warp"])
+    env.set_launch(best["warps_per_block"], best["blocks_per_sm"], best["games_per_fetch"],
+                   games_per_warp=best["games_per_warp"])
     out = env.run(S, R)
     env.sync()
     stats = _np(env.stats())
@@ -143,9 +144,10 @@ def test_full_size_all_65536_slots_counters_and_final_positions():
     import threading
     from paper_2511_07312_gb300 import autotune
     N, S = 65536, 2000
-    best = autotune.tune(N)
+    best = autotune.tune(N, final_plies=S)
     env = st.Env(N, seed=1)
-    env.set_launch(best["warps_per_block"], 0, best["games_per_fetch"], games_per_warp=best["games_per_warp"])
+    env.set_launch(best["warps_per_block"], best["blocks_per_sm"], best["games_per_fetch"],
+                   games_per_warp=best["games_per_warp"])
     env.run(S, 16)
     env.sync()
     stats = _np(env.stats())
