@@ -195,6 +195,11 @@ st_status st_env_sample_actions(st_env* env, int16_t* actions);
  * the outputs of st_env_step into ring row j % ring_steps of each output
  * ([ring_steps][N] and [ring_steps][N][1264]); any output may be NULL.
  * Results are identical to n_steps calls of st_env_step with actions NULL.
+ * When the slots outnumber the games resident on the GPU and n_steps >= 512,
+ * each slot's plies may run as 2 to 4 parts of >= 256 plies, claimed as
+ * separate work units so that the launch's last wave is nearly full (a part
+ * waits, with a bound of a few seconds, for the slot's previous part to be
+ * stored; running out latches ST_ERR_TIMEOUT for the slot).
  */
 st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
                      int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring);

@@ -5,6 +5,7 @@
 // persistent launch runs 1, 2, 4 or 8 games per warp (teams of 32, 16, 8 or
 // 4 lanes), the shape chosen by st_env_set_launch.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 #include "rollout.cuh"
@@ -24,6 +25,7 @@ struct st_env {
     uint32_t* stats = nullptr;
     int32_t* status = nullptr;      // [0] latched st_status, [1] first slot (min)
     int32_t* queue = nullptr;       // work counter of the persistent launch
+    int32_t* part_done = nullptr;   // [N] parts of each slot played in the current persistent launch
     int wpb = 4, bps = 0, gpf = 1;  // launch shape of st_env_run
     int gpw = 1;                    // games per warp (1, 2, 4 or 8)
     int sms = 0;
@@ -414,16 +416,26 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
     store_core(G, A.core + g, T);   // an illegal action changed nothing but the history marks
 }
 
-// Persistent form: each team claims gpf slots at a time from a global
-// counter and plays n_steps plies in each of them, keeping the game in
-// shared memory.
+// Persistent form: each team claims gpf work units at a time from a global
+// counter, a unit being one part of a slot's n_steps plies (nsplit parts,
+// all first parts before any second part, and so on), and plays it keeping
+// the game in shared memory.  Splitting the plies fills the last wave of
+// units when the slots are a little more than a whole number of resident
+// games (65,536 slots over 14,592 games: 4.49 waves of whole slots, 8.98
+// of halves).  A part waits for its slot's previous part, which was claimed
+// a wave or more earlier and has normally finished; the wait is bounded
+// and latches ST_ERR_TIMEOUT for the slot if it ever ran out.
+constexpr int kMinPartPlies = 256;      // no part shorter than this many plies
+constexpr int kMaxParts = 4;
+constexpr long long kPartSpinLimit = 1ll << 22;   // polls of ~0.3-1 us: a few seconds
 // At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
 // thread; shared memory, not registers, bounds the resident teams.
 constexpr int kRunMaxWarps = 8;
 template <int L, bool kHist>
 __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
                                                  int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
-                                                 int16_t* ply_ring, uint8_t* mask_ring)
+                                                 int16_t* ply_ring, uint8_t* mask_ring, int nsplit,
+                                                 int32_t* part_done)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<L> T;
@@ -431,15 +443,37 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
     // player to move right after it (rows_of), which is also the buffer the
     // bulk copies send to the ring
     SmemGame* G = reinterpret_cast<SmemGame*>(smem + (size_t)(threadIdx.x / L) * kRowsRecordBytes);
+    const int units = A.N * nsplit;
+    const int part = (n_steps + nsplit - 1) / nsplit;
     for (;;) {
-        // each team claims its own slots: no collective spans more than one team
+        // each team claims its own units: no collective spans more than one team
         int first = 0;
         if (T.leader()) first = atomicAdd(queue, gpf);
         first = T.shfl(first, 0);
-        if (first >= A.N) break;
+        if (first >= units) break;
         for (int gi = 0; gi < gpf; ++gi) {
-            const int g = first + gi;
-            if (g >= A.N) break;
+            const int u = first + gi;
+            if (u >= units) break;
+            const int h = u / A.N, g = u - h * A.N;          // part h of slot g
+            const int j0 = h * part, j1 = min(n_steps, j0 + part);
+            if (h > 0) {
+                // the slot's previous part has been stored (release below)
+                int ok = 1;
+                if (T.leader()) {
+                    long long spins = 0;
+                    while (atomicAdd(&part_done[g], 0) < h && spins < kPartSpinLimit) {
+                        __nanosleep(256);
+                        ++spins;
+                    }
+                    ok = spins < kPartSpinLimit;
+                    __threadfence();
+                }
+                ok = T.shfl(ok, 0);
+                if (!ok) {
+                    if (T.leader()) latch(A.status, ST_ERR_TIMEOUT, g);
+                    continue;
+                }
+            }
             uint16_t* ring = A.ring + (size_t)g * kRing;
             uint64_t* pi = A.pi + (size_t)g * kPiWords;
             load_core(G, A.core + g, T);
@@ -451,9 +485,9 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             // the launch's counters live in shared memory, not in registers
             // that every engine call would have to save
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
-            if (kHist && T.leader()) G->c.hrow = (uint16_t)(*A.now % A.H);
-            int row = 0;   // output ring row of ply j: j mod ring_steps
-            for (int j = 0; j < n_steps; ++j) {
+            if (kHist && T.leader()) G->c.hrow = (uint16_t)((*A.now + j0) % A.H);
+            int row = j0 % ring_steps;   // output ring row of ply j: j mod ring_steps
+            for (int j = j0; j < j1; ++j) {
                 bool illegal;
                 if (kHist) hist_before(G, T);
                 const size_t o = (size_t)row * (size_t)A.N + (size_t)g;
@@ -480,6 +514,13 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
                 G->c.n_legal = (uint16_t)n;
             }
             store_core(G, A.core + g, T);
+            if (nsplit > 1) {
+                // release: the slot's record, counters, history ring and chase
+                // store are in global memory before the next part may start
+                __threadfence();
+                T.sync();
+                if (T.leader()) atomicExch(&part_done[g], h + 1);
+            }
         }
     }
     // the team's last mask copies have landed before it leaves
@@ -864,26 +905,46 @@ cudaError_t run_occupancy(int wpb, int gpw, int* occ)
     }
 }
 
+// Parts per slot of a persistent launch over N slots by R resident games:
+// only when the slots outnumber the resident games (more than one wave, so
+// each part is claimed a wave after the slot's previous part), parts of at
+// least kMinPartPlies plies, and the count whose last wave is fullest: the
+// launch lasts about ceil(n N / R) / n whole-slot waves, the fewest parts
+// within 2% of the best.
+int parts_per_slot(int N, int R, int n_steps)
+{
+    if (R <= 0 || N <= R) return 1;
+    const double w = (double)N / (double)R;
+    double best = 1e30;
+    for (int n = 1; n <= kMaxParts && n_steps >= n * kMinPartPlies; ++n)
+        best = std::min(best, std::ceil(n * w) / n);
+    for (int n = 1; n <= kMaxParts && n_steps >= n * kMinPartPlies; ++n)
+        if (std::ceil(n * w) / n <= 1.02 * best) return n;
+    return 1;
+}
+
 template <int L>
 void launch_run_t(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
-                  int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+                  int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring, int nsplit)
 {
     if (a.hist)
         k_env_run<L, true><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
-            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit,
+            e->part_done);
     else
         k_env_run<L, false><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
-            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+            a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit,
+            e->part_done);
 }
 
 void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,
-                int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
+                int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring, int nsplit)
 {
     switch (e->gpw) {
-    case 8: launch_run_t<4>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
-    case 4: launch_run_t<8>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
-    case 2: launch_run_t<16>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring); break;
-    default: launch_run_t<32>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    case 8: launch_run_t<4>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit); break;
+    case 4: launch_run_t<8>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit); break;
+    case 2: launch_run_t<16>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit); break;
+    default: launch_run_t<32>(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit);
     }
 }
 
@@ -918,6 +979,7 @@ extern "C" st_status st_env_create(const st_env_config* cfg, st_env** out)
     if (err == cudaSuccess) err = cudaMalloc(&e->stats, N * 8 * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->status, 2 * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->queue, sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->part_done, N * sizeof(int32_t));
     if (err != cudaSuccess) {
         stg::set_error("st_env_create: device allocation failed: %s", cudaGetErrorString(err));
         cudaGetLastError();
@@ -955,7 +1017,7 @@ extern "C" st_status st_env_destroy(st_env* e)
     cudaStreamSynchronize(e->stream);
     if (e->graph) cudaGraphExecDestroy(e->graph);
     cudaFree(e->core); cudaFree(e->ring); cudaFree(e->pi); cudaFree(e->stats);
-    cudaFree(e->status); cudaFree(e->queue);
+    cudaFree(e->status); cudaFree(e->queue); cudaFree(e->part_done);
     cudaFree(e->pool); cudaFree(e->pin_of); cudaFree(e->pins);
     cudaFree(e->hist); cudaFree(e->d_now);
     delete e;
@@ -1038,6 +1100,7 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
                              (int64_t)ply_ring, (int64_t)mask_ring, e->wpb, bps, e->gpf, e->gpw};
     const int per_block = e->wpb * e->gpw;
     const int blocks = std::max(1, std::min(e->sms * bps, (e->N + per_block - 1) / per_block));
+    const int nsplit = parts_per_slot(e->N, blocks * per_block, n_steps);
     EnvArgs a = env_args(e);
     // A non-default stream gets the launch pair (queue reset + persistent
     // kernel) captured once into a CUDA graph and replayed afterwards.
@@ -1051,7 +1114,8 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         cudaGraph_t graph = nullptr;
         ST_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream);
-        launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+        if (nsplit > 1) cudaMemsetAsync(e->part_done, 0, (size_t)e->N * sizeof(int32_t), e->stream);
+        launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit);
         if (e->hist) k_env_advance<<<1, 1, 0, e->stream>>>(e->d_now, n_steps);
         const cudaError_t launch_err = cudaGetLastError();
         const cudaError_t cap_err = cudaStreamEndCapture(e->stream, &graph);
@@ -1074,7 +1138,8 @@ extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, 
         return ST_OK;
     }
     ST_CUDA(cudaMemsetAsync(e->queue, 0, sizeof(int32_t), e->stream));
-    launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring);
+    if (nsplit > 1) ST_CUDA(cudaMemsetAsync(e->part_done, 0, (size_t)e->N * sizeof(int32_t), e->stream));
+    launch_run(e, a, blocks, n_steps, ring_steps, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit);
     ST_CUDA(cudaGetLastError());
     if (e->hist) {
         k_env_advance<<<1, 1, 0, e->stream>>>(e->d_now, n_steps);

@@ -5,6 +5,8 @@
 // written to <out>.{action,reward,done,ply,mask,stats} for comparison with
 // the oracle.
 //   env_on_host N S L wpb gpf blocks seed out [actions]
+// NSPLIT in the environment (default 1) sets the persistent launch's parts
+// per slot.
 // With an actions file ([S][N] int16, -1 = the random policy) the plain
 // path runs instead: one k_env_step launch per ply (teams of 32 lanes, 4
 // warps per block) with those actions supplied.
@@ -13,10 +15,11 @@
 
 template <int L>
 static void run(EnvArgs a, int32_t* queue, int S, int gpf, int wpb, int blocks, int16_t* act, int8_t* rew, uint8_t* done,
-                int16_t* ply, uint8_t* mask)
+                int16_t* ply, uint8_t* mask, int nsplit, int32_t* part_done)
 {
     const size_t sm = (size_t)wpb * (32 / L) * kRowsRecordBytes;   // row-mode records, each followed by its mask
-    launch(blocks, 32 * wpb, sm, [=] { k_env_run<L, false>(a, queue, S, S, gpf, act, rew, done, ply, mask); });
+    launch(blocks, 32 * wpb, sm,
+           [=] { k_env_run<L, false>(a, queue, S, S, gpf, act, rew, done, ply, mask, nsplit, part_done); });
 }
 
 int main(int argc, char** argv)
@@ -31,6 +34,8 @@ int main(int argc, char** argv)
     std::vector<uint32_t> stats((size_t)N * 8);
     int32_t status[2] = {0, 0x7FFFFFFF};
     int32_t queue = 0;
+    const int nsplit = std::getenv("NSPLIT") ? std::atoi(std::getenv("NSPLIT")) : 1;
+    std::vector<int32_t> part_done((size_t)N, 0);
     EnvArgs a{};
     a.core = core.data(); a.ring = ring.data(); a.pi = pi.data(); a.stats = stats.data(); a.status = status;
     a.N = N; a.k0 = (uint32_t)seed; a.k1 = (uint32_t)(seed >> 32);
@@ -55,10 +60,14 @@ int main(int argc, char** argv)
             uint8_t* mo = mask.data() + o * kMaskBytes;
             launch((N + 3) / 4, 128, 4 * sizeof(SmemGame), [=] { k_env_step<32>(a, gv, ao, ro, dn, po, mo); });
         }
-    } else if (L == 8) run<8>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
-    else if (L == 4) run<4>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
-    else if (L == 16) run<16>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
-    else run<32>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data());
+    } else if (L == 8) run<8>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data(), nsplit,
+                       part_done.data());
+    else if (L == 4) run<4>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data(), nsplit,
+                       part_done.data());
+    else if (L == 16) run<16>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data(), nsplit,
+                       part_done.data());
+    else run<32>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data(), nsplit,
+                 part_done.data());
     dump(out + ".action", act.data(), act.size());
     dump(out + ".reward", rew.data(), rew.size());
     dump(out + ".done", done.data(), done.size());

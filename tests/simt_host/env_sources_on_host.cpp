@@ -71,8 +71,11 @@ int main(int argc, char** argv)
         int16_t* ap = act.data(); int8_t* rp = rew.data(); uint8_t* dp = done.data(); int16_t* pp = ply.data();
         uint8_t* mp = mask.data();
         int32_t* qp = &queue;
+        // two parts per slot, the second starting mid-way through the history ring
+        std::vector<int32_t> part_done((size_t)N, 0);
+        int32_t* dn = part_done.data();
         const size_t sm = (size_t)wpb * 4 * kRowsRecordBytes;   // row-mode records, each followed by its mask
-        launch(nblocks, 32 * wpb, sm, [=] { k_env_run<8, true>(a, qp, S, S, gpf, ap, rp, dp, pp, mp); });
+        launch(nblocks, 32 * wpb, sm, [=] { k_env_run<8, true>(a, qp, S, S, gpf, ap, rp, dp, pp, mp, 2, dn); });
     }
     d_now += S;
     dump(out + ".action", act.data(), act.size());

@@ -26,6 +26,7 @@
 #include <mutex>
 #include <atomic>
 #include <condition_variable>
+#include <thread>
 #include <vector>
 #define __device__
 #define __global__
@@ -289,5 +290,5 @@ inline cudaError_t cudaGetLastError() { return 0; }
 template <class K> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, K, int, size_t) { *n = 1; return 0; }
 inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void __threadfence_system() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
-inline void __nanosleep(unsigned) {}
+inline void __nanosleep(unsigned) { std::this_thread::yield(); }
 inline unsigned long long __cvta_generic_to_shared(const void* p) { return (unsigned long long)(uintptr_t)p; }

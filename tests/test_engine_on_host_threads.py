@@ -166,17 +166,21 @@ def tsan_exe(built):
     return exe, os.path.dirname(src)
 
 
-@pytest.mark.parametrize("L,wpb,gpf,blocks", [(8, 1, 1, 1), (4, 1, 2, 1), (16, 2, 1, 2), (32, 2, 1, 1)])
-def test_step_kernel_under_threadsanitizer(tsan_exe, L, wpb, gpf, blocks):
+@pytest.mark.parametrize("L,wpb,gpf,blocks,nsplit", [(8, 1, 1, 1, 1), (4, 1, 2, 1, 2), (16, 2, 1, 2, 1),
+                                                      (32, 2, 1, 1, 3), (8, 1, 2, 1, 2)])
+def test_step_kernel_under_threadsanitizer(tsan_exe, L, wpb, gpf, blocks, nsplit):
+    # nsplit > 1: each slot's plies in parts claimed as separate work units,
+    # a later part waiting for the earlier one's release
     exe, tmp = tsan_exe
-    _run_and_compare(exe, tmp, 8, 120, L, wpb, gpf, blocks, 7, env={"TSAN_OPTIONS": "halt_on_error=0"})
+    _run_and_compare(exe, tmp, 8, 120, L, wpb, gpf, blocks, 7,
+                     env={"TSAN_OPTIONS": "halt_on_error=0", "NSPLIT": str(nsplit)})
 
 
 def test_step_kernel_under_address_and_ub_sanitizers(tmp_path, built):
     exe, _ = built("env_on_host.cpp", SANITIZERS[1][0])
-    for L, wpb, gpf, blocks in ((8, 2, 1, 2), (4, 1, 1, 1)):
+    for L, wpb, gpf, blocks, nsplit in ((8, 2, 1, 2, 1), (4, 1, 1, 1, 2)):
         _run_and_compare(exe, str(tmp_path), 8, 150, L, wpb, gpf, blocks, 11,
-                         env={"ASAN_OPTIONS": "detect_leaks=0"})
+                         env={"ASAN_OPTIONS": "detect_leaks=0", "NSPLIT": str(nsplit)})
 
 
 def test_harness_reports_a_planted_missing_sync(tmp_path):

@@ -95,6 +95,38 @@ def test_persistent_launch_shapes_ragged(wpb, gpf, gpw):
         np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
 
 
+@pytest.mark.parametrize("wpb,gpf,gpw", [(1, 1, 1), (4, 3, 2), (2, 2, 4)])
+def test_persistent_launch_in_parts_per_slot(wpb, gpf, gpw):
+    # one block per SM and 1.25 waves of slots (R resident games, N = R +
+    # R/4 + 3): with 800 plies each slot's plies run as three work units of
+    # 267, 267 and 266 plies, later parts claimed after every earlier one;
+    # ring of 7 rows, then a second launch continuing the same slots
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    R = sms * wpb * gpw
+    N, S, K = R + R // 4 + 3, 800, 7
+    env = st.Env(N, seed=9)
+    env.set_launch(wpb, 1, gpf, games_per_warp=gpw)
+    out = env.run(S, K)
+    env.stream.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in out.items()}
+    stats = _np(env.stats())
+    slots = np.array([0, 1, R - 1, R, N - 2, N - 1] + list(range(61, N, max(1, N // 9))))
+    pos = _np(env.export(torch.from_numpy(slots).to(torch.int32)))
+    for j, s in enumerate(slots):
+        r = oracle.env_run(9, 1, S, slot0=int(s), want_final=True)
+        for row in range(S - K, S):
+            for k in ("action", "reward", "done", "ply"):
+                assert gpu[k][row % K, s] == r[k][row, 0], (k, s, row)
+            assert np.array_equal(gpu["mask"][row % K, s], r["mask"][row, 0]), ("mask", s, row)
+        np.testing.assert_array_equal(stats[s], r["stats"][0].astype(np.int32))
+        np.testing.assert_array_equal(pos[j], r["final"][0])
+    env.run(S, K)
+    st2 = _np(env.stats())
+    for s in slots[:4]:
+        r = oracle.env_run(9, 1, 2 * S, slot0=int(s), want_mask=False)
+        np.testing.assert_array_equal(st2[s], r["stats"][0].astype(np.int32))
+
+
 def test_oversized_launch_shape_is_rejected_and_leaves_no_error_behind():
     env = st.Env(64, seed=1)
     with pytest.raises(st.StrategoError):
