@@ -195,7 +195,7 @@ st_status st_env_sample_actions(st_env* env, int16_t* actions);
  * the outputs of st_env_step into ring row j % ring_steps of each output
  * ([ring_steps][N] and [ring_steps][N][1264]); any output may be NULL.
  * Results are identical to n_steps calls of st_env_step with actions NULL.
- * When the slots outnumber the games resident on the GPU and n_steps >= 512,
+ * When the slots outnumber the games resident on the GPU and 512 <= n_steps <= 32768,
  * each slot's plies may run as 2 to 4 parts of >= 256 plies, claimed as
  * separate work units so that the launch's last wave is nearly full (a part
  * waits, with a bound of a few seconds, for the slot's previous part to be

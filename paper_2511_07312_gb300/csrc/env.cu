@@ -427,7 +427,11 @@ __global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_ou
 // and latches ST_ERR_TIMEOUT for the slot if it ever ran out.
 constexpr int kMinPartPlies = 256;      // no part shorter than this many plies
 constexpr int kMaxParts = 4;
-constexpr long long kPartSpinLimit = 1ll << 22;   // polls of ~0.3-1 us: a few seconds
+constexpr int kMaxSplitPlies = 32768;   // launches longer than this are not split (a part's wait stays short)
+#ifndef ST_PART_SPIN_LIMIT
+#define ST_PART_SPIN_LIMIT (1ll << 22)   // polls of ~0.3-1 us: a few seconds
+#endif
+constexpr long long kPartSpinLimit = ST_PART_SPIN_LIMIT;
 // At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
 // thread; shared memory, not registers, bounds the resident teams.
 constexpr int kRunMaxWarps = 8;
@@ -907,13 +911,14 @@ cudaError_t run_occupancy(int wpb, int gpw, int* occ)
 
 // Parts per slot of a persistent launch over N slots by R resident games:
 // only when the slots outnumber the resident games (more than one wave, so
-// each part is claimed a wave after the slot's previous part), parts of at
-// least kMinPartPlies plies, and the count whose last wave is fullest: the
-// launch lasts about ceil(n N / R) / n whole-slot waves, the fewest parts
-// within 2% of the best.
+// each part is claimed a wave after the slot's previous part), for launches
+// of at most kMaxSplitPlies plies (a part waits at most about one part's
+// time) and parts of at least kMinPartPlies plies; the count whose last
+// wave is fullest (the launch lasts about ceil(n N / R) / n whole-slot
+// waves), the fewest parts within 2% of the best.
 int parts_per_slot(int N, int R, int n_steps)
 {
-    if (R <= 0 || N <= R) return 1;
+    if (R <= 0 || N <= R || n_steps > kMaxSplitPlies) return 1;
     const double w = (double)N / (double)R;
     double best = 1e30;
     for (int n = 1; n <= kMaxParts && n_steps >= n * kMinPartPlies; ++n)

@@ -33,7 +33,9 @@ int main(int argc, char** argv)
     std::vector<uint64_t> pi((size_t)N * kPiWords);
     std::vector<uint32_t> stats((size_t)N * 8);
     int32_t status[2] = {0, 0x7FFFFFFF};
-    int32_t queue = 0;
+    // QUEUE0: the persistent launch's first work unit (N with NSPLIT 2 runs
+    // only second parts, whose first parts never finish: every wait runs out)
+    int32_t queue = std::getenv("QUEUE0") ? std::atoi(std::getenv("QUEUE0")) : 0;
     const int nsplit = std::getenv("NSPLIT") ? std::atoi(std::getenv("NSPLIT")) : 1;
     std::vector<int32_t> part_done((size_t)N, 0);
     EnvArgs a{};

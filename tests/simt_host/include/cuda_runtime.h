@@ -27,6 +27,7 @@
 #include <atomic>
 #include <condition_variable>
 #include <thread>
+#include <chrono>
 #include <vector>
 #define __device__
 #define __global__
@@ -290,5 +291,7 @@ inline cudaError_t cudaGetLastError() { return 0; }
 template <class K> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, K, int, size_t) { *n = 1; return 0; }
 inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void __threadfence_system() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
-inline void __nanosleep(unsigned) { std::this_thread::yield(); }
+// a real sleep: a bounded wait keeps its bound in time however slowly the
+// host threads run (at least the timer's granularity per call)
+inline void __nanosleep(unsigned ns) { std::this_thread::sleep_for(std::chrono::nanoseconds(ns)); }
 inline unsigned long long __cvta_generic_to_shared(const void* p) { return (unsigned long long)(uintptr_t)p; }

@@ -183,6 +183,22 @@ def test_step_kernel_under_address_and_ub_sanitizers(tmp_path, built):
                          env={"ASAN_OPTIONS": "detect_leaks=0", "NSPLIT": str(nsplit)})
 
 
+def test_part_wait_runs_out_and_latches_a_timeout(tmp_path, built):
+    # two parts per slot, the queue starting at the second parts: no first
+    # part ever runs, so every wait (bounded at 200 polls here) runs out,
+    # latches ST_ERR_TIMEOUT (5) for the lowest slot and skips the unit; the
+    # launch returns
+    exe, _ = built("env_on_host.cpp", SANITIZERS[1][0] + ["-DST_PART_SPIN_LIMIT=200"])
+    N, S = 8, 120
+    out = str(tmp_path / "o")
+    r = subprocess.run([exe, str(N), str(S), "8", "1", "1", "1", "3", out], capture_output=True, text=True,
+                       timeout=600, env=dict(os.environ, ASAN_OPTIONS="detect_leaks=0", NSPLIT="2", QUEUE0=str(N)))
+    _check_report(r)
+    assert "status 5 0" in r.stdout, r.stdout[-2000:]
+    # nothing was played: the counters stay zero
+    assert not np.fromfile(out + ".stats", dtype=np.uint32).any()
+
+
 def test_harness_reports_a_planted_missing_sync(tmp_path):
     # the check itself: without the team barrier between clearing the board
     # and placing the pieces, ThreadSanitizer must report a race
@@ -233,6 +249,7 @@ def _run_driver(exe, args, env, known=()):
                        env=dict(os.environ, **env))
     report = _check_report(r, known)
     assert "done" in r.stdout, report[-6000:]
+    return r.stdout
 
 
 SANITIZERS = [
@@ -392,8 +409,8 @@ def test_reset_sources_and_history_under_sanitizers(tmp_path, built, san):
     np.stack([pins[i] for i in sorted(pins)]).tofile(inp + ".pins")
     np.array(sorted(pins), np.int32).tofile(inp + ".idx")
     steps = [200, 150, 60, 0]
-    _run_driver(exe, [inp, out, N, S, 8, 2, 1, 2, seed, H, M, 1, len(pins)] + steps, env,
-                ())
+    stdout = _run_driver(exe, [inp, out, N, S, 8, 2, 1, 2, seed, H, M, 1, len(pins)] + steps, env, ())
+    assert "status 0 " in stdout, stdout[-2000:]
     ref = oracle.env_run(seed, N, S, pool=pool, mirror=True, episode0=1, pins=pins)
     for k, dt in (("action", np.int16), ("reward", np.int8), ("done", np.uint8), ("ply", np.int16)):
         np.testing.assert_array_equal(np.fromfile(out + "." + k, dt).reshape(S, N), ref[k], err_msg=k)
