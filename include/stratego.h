@@ -330,8 +330,9 @@ st_status st_replay_positions(const uint8_t* setups, const int16_t* actions, int
                               const int32_t* game, const int16_t* ply, int32_t B, const st_rules* rules,
                               st_position* out, uint8_t* item_status, void* stream);
 
-/* Items a replay warp takes (default 8); a process-wide tuning knob. */
-st_status st_replay_set_chunk(int32_t items_per_warp);
+/* Consecutive items a replay block takes (default 32); a process-wide
+ * tuning knob. */
+st_status st_replay_set_chunk(int32_t items_per_block);
 
 /*
  * st_obs_encode: observation planes of App. C for B replayed items, for the

@@ -158,8 +158,8 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def set_replay_chunk(items_per_warp):
-    _check(lib().st_replay_set_chunk(int(items_per_warp)))
+def set_replay_chunk(items_per_block):
+    _check(lib().st_replay_set_chunk(int(items_per_block)))
 
 
 def make_rules(k=100, cap=1000, flags=RULES_ALL):

@@ -1139,6 +1139,183 @@ __device__ __forceinline__ void apply_impl(SmemGame* G, int a, uint16_t* ring, u
     T.sync();
 }
 
+// The same move in two halves, for kernels whose other warps read the
+// position while the move is worked out (the replay): plan_apply reads
+// every input and computes the new state in registers without writing;
+// commit_apply writes it.  Together they make exactly the changes of
+// apply_impl.
+struct ApplyPlan {
+    int a, from, to, X, D, to_after, cls, ply, battleless, h0;
+    int cf, ct;
+    uint32_t vf, vt;              // new column occupancy of the from- and to-columns
+    bool battle, x_alive, d_died, scout;
+    uint8_t fx, fd;
+    uint64_t h, hq;
+    Set128 occP, kindP, occQ, movQ, scoQ;
+    int ts_mode, ts_len, s1, s2, s3;   // 0 reset, 1 shift in `to`, 2 append `to`, 3 new piece
+    bool ts_reset_q;
+    int chaser, n_pi, chase_plies;
+};
+
+__device__ __forceinline__ ApplyPlan plan_apply(const SmemGame* G, int a)
+{
+    ApplyPlan q;
+    const GameCore& c = G->c;
+    q.a = a;
+    const int from = a / 100, to = a - 100 * (a / 100);
+    q.from = from; q.to = to;
+    const int rf = from / 10, cf = from - 10 * rf, rt = to / 10, ct = to - 10 * rt;
+    q.cf = cf; q.ct = ct;
+    const int ply = c.ply;
+    q.ply = ply;
+    const int P = ply & 1, Q = 1 - P;
+    const int X = G->board[from];
+    const int D = G->board[to];
+    const int h0 = G->h0;
+    q.h0 = h0;
+    const int prev_to = h0 == 0xFFFF ? -1 : h0 % 100;
+    const uint8_t on_prev = prev_to >= 0 ? G->board[prev_to] : kEmpty;
+    const uint8_t nS = rt > 0 ? G->board[to - 10] : kEmpty;
+    const uint8_t nN = rt < 9 ? G->board[to + 10] : kEmpty;
+    const uint8_t nW = ct > 0 ? G->board[to - 1] : kEmpty;
+    const uint8_t nE = ct < 9 ? G->board[to + 1] : kEmpty;
+    const bool prev_nb = !c.last_battle;
+    q.battleless = c.battleless;
+    const uint64_t hsP = c.hash_side[P], hsQ = c.hash_side[Q];
+    const Set128 occP = ld128(G->bocc[P]), occQ = ld128(G->bocc[Q]);
+    const Set128 movP = ld128(G->bmov[P]), scoP = ld128(G->bsco[P]);
+    const Set128 movQ = ld128(G->bmov[Q]), scoQ = ld128(G->bsco[Q]);
+    const uint32_t col_f = G->colocc[cf], col_t = G->colocc[ct];
+    const int ts_pidP = c.ts_pid[P], ts_lenP = c.ts_len[P], ts_pidQ = c.ts_pid[Q];
+    q.s1 = c.ts_sq[P][1]; q.s2 = c.ts_sq[P][2]; q.s3 = c.ts_sq[P][3];
+    q.chaser = c.chaser; q.n_pi = c.n_pi; q.chase_plies = c.chase_plies;
+    const bool battle = D != kEmpty;
+    const int Dp = battle ? D : X;   // the defender, or any valid piece
+    const uint8_t fX0 = c.flags[X], fD0 = c.flags[Dp];
+    const int tX = c.type[X], tD = c.type[Dp];
+    q.X = X; q.D = D; q.battle = battle;
+    if (battle) q.cls = kClBattle;
+    else if (prev_to >= 0 && prev_nb && enemy_of(on_prev, P) && adjacent(from, prev_to) && !adjacent(to, prev_to))
+        q.cls = kClEvade;
+    else
+        q.cls = (enemy_of(nS, P) || enemy_of(nN, P) || enemy_of(nW, P) || enemy_of(nE, P)) ? kClThreat : kClQuiet;
+    const uint64_t zXf = zkey(X, from), zXt = zkey(X, to), zDt = zkey(Dp, to);
+    const int dist = rf == rt ? abs(cf - ct) : abs(rf - rt);
+    uint8_t fx = (uint8_t)(fX0 | 4 | (dist > 1 ? 8 : 0));
+    uint8_t fd = fD0;
+    bool d_died = false, x_alive = true;
+    int to_after = X;
+    if (battle) {
+        const bool d_rev = fD0 & 2;
+        int out;
+        if (tD == kFlag) out = 1;
+        else if (tD == kBomb) out = tX == kMiner ? 1 : 2;
+        else if (tX == kSpy && tD == kMarshal) out = 1;
+        else out = tX > tD ? 1 : (tX < tD ? 2 : 3);
+        fx |= 2;
+        fd |= 2;
+        if (out == 1) {
+            fd = (uint8_t)((fd & 0x0E) | ((d_rev ? 4 : 6) << 4));
+            d_died = true;
+        } else if (out == 2) {
+            fx = (uint8_t)((fx & 0x0E) | ((d_rev ? 1 : 3) << 4));
+            x_alive = false;
+            to_after = D;
+        } else {
+            fx = (uint8_t)((fx & 0x0E) | ((d_rev ? 2 : 3) << 4));
+            fd = (uint8_t)((fd & 0x0E) | ((d_rev ? 5 : 6) << 4));
+            d_died = true;
+            x_alive = false;
+            to_after = kEmpty;
+        }
+    }
+    q.fx = fx; q.fd = fd; q.x_alive = x_alive; q.d_died = d_died; q.to_after = to_after;
+    q.h = hsP ^ zXf ^ (x_alive ? zXt : 0ull);
+    q.hq = hsQ ^ (d_died ? zDt : 0ull);
+    const Set128 bf = bit128(from), bt = bit128(to);
+    const Set128 add = x_alive ? bt : Set128{0ull, 0ull};
+    q.scout = tX == kScout;
+    const Set128 kind0 = q.scout ? scoP : movP;
+    q.occP = Set128{(occP.lo & ~bf.lo) | add.lo, (occP.hi & ~bf.hi) | add.hi};
+    q.kindP = Set128{(kind0.lo & ~bf.lo) | add.lo, (kind0.hi & ~bf.hi) | add.hi};
+    q.occQ = Set128{occQ.lo & ~bt.lo, occQ.hi & ~bt.hi};
+    q.movQ = Set128{movQ.lo & ~bt.lo, movQ.hi & ~bt.hi};
+    q.scoQ = Set128{scoQ.lo & ~bt.lo, scoQ.hi & ~bt.hi};
+    q.vf = col_f & ~(1u << rf);
+    const uint32_t vt0 = cf == ct ? q.vf : col_t;
+    q.vt = to_after != kEmpty ? (vt0 | (1u << rt)) : (vt0 & ~(1u << rt));
+    if (!x_alive) q.ts_mode = 0;
+    else if (ts_pidP == X && ts_lenP >= 2) q.ts_mode = ts_lenP == 4 ? 1 : 2;
+    else q.ts_mode = 3;
+    q.ts_len = ts_lenP;
+    q.ts_reset_q = d_died && ts_pidQ == D;
+    return q;
+}
+
+__device__ __forceinline__ void commit_apply(SmemGame* G, const ApplyPlan& q, uint16_t* ring, uint64_t* pi)
+{
+    GameCore& c = G->c;
+    const int P = q.ply & 1, Q = 1 - P;
+    G->board[q.from] = kEmpty;
+    G->board[q.to] = (uint8_t)q.to_after;
+    G->bocc[P][0] = q.occP.lo; G->bocc[P][1] = q.occP.hi;
+    uint64_t* kindX = q.scout ? G->bsco[P] : G->bmov[P];
+    kindX[0] = q.kindP.lo; kindX[1] = q.kindP.hi;
+    if (q.d_died) {
+        G->bocc[Q][0] = q.occQ.lo; G->bocc[Q][1] = q.occQ.hi;
+        G->bmov[Q][0] = q.movQ.lo; G->bmov[Q][1] = q.movQ.hi;
+        G->bsco[Q][0] = q.scoQ.lo; G->bsco[Q][1] = q.scoQ.hi;
+    }
+    if (q.cf != q.ct) G->colocc[q.cf] = (uint16_t)q.vf;
+    G->colocc[q.ct] = (uint16_t)q.vt;
+    c.sq[q.X] = (uint8_t)q.to;
+    c.flags[q.X] = q.fx;
+    if (q.battle) c.flags[q.D] = q.fd;
+    c.hash_side[P] = q.h;
+    c.hash_side[Q] = q.hq;
+    c.battleless = q.battle ? 0 : (int16_t)(q.battleless + 1);
+    c.last_battle = q.battle ? 1 : 0;
+    c.ply = (int16_t)(q.ply + 1);
+    if (q.ts_mode == 0) {
+        c.ts_pid[P] = kNone; c.ts_len[P] = 0;
+        c.ts_sq[P][0] = c.ts_sq[P][1] = c.ts_sq[P][2] = c.ts_sq[P][3] = kNone;
+    } else if (q.ts_mode == 1) {
+        c.ts_sq[P][0] = (uint8_t)q.s1; c.ts_sq[P][1] = (uint8_t)q.s2;
+        c.ts_sq[P][2] = (uint8_t)q.s3; c.ts_sq[P][3] = (uint8_t)q.to;
+    } else if (q.ts_mode == 2) {
+        c.ts_sq[P][q.ts_len] = (uint8_t)q.to;
+        c.ts_len[P] = (uint8_t)(q.ts_len + 1);
+    } else {
+        c.ts_pid[P] = (uint8_t)q.X; c.ts_len[P] = 2;
+        c.ts_sq[P][0] = (uint8_t)q.from; c.ts_sq[P][1] = (uint8_t)q.to;
+        c.ts_sq[P][2] = c.ts_sq[P][3] = kNone;
+    }
+    if (q.ts_reset_q) {
+        c.ts_pid[Q] = kNone; c.ts_len[Q] = 0;
+        c.ts_sq[Q][0] = c.ts_sq[Q][1] = c.ts_sq[Q][2] = c.ts_sq[Q][3] = kNone;
+    }
+    if (q.cls == kClThreat) {
+        int n = q.n_pi, plies = q.chase_plies;
+        if (q.chaser != P) { n = 0; plies = 0; }
+        if (n < kPiCap) {
+            pi[2 * n] = q.h; pi[2 * n + 1] = q.hq;
+            G->pi_theirs[n & 3] = q.hq;
+            G->pi_mine[n & 3] = q.h;
+            n += 1;
+        }
+        c.chaser = (uint8_t)P;
+        c.n_pi = (uint8_t)n;
+        c.chase_plies = (uint8_t)(plies + 1);
+    } else if (q.cls == kClEvade && q.chaser == Q) {
+        c.chase_plies = (uint8_t)(q.chase_plies + 1);
+    } else {
+        c.chaser = kNone; c.n_pi = 0; c.chase_plies = 0;
+    }
+    if (ring) ring[q.ply & (kRing - 1)] = (uint16_t)q.a;
+    G->h1 = (uint16_t)q.h0;
+    G->h0 = (uint16_t)q.a;
+}
+
 template <int L>
 __device__ __noinline__ void apply_move(SmemGame* G, Team<L>, int a, uint16_t* ring, uint64_t* pi)
 {

@@ -76,56 +76,67 @@ __device__ __forceinline__ bool move_legal(const SmemGame* G, int a, uint32_t ru
     return true;
 }
 
-// Features that depend on the position before action a (active adjacency,
-// evasion, protection).  Call before apply_move.
-__device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, int a, uint32_t rule_flags,
-                                                const uint16_t* ring)
+// Active adjacency before action a: every own movable piece next to an
+// enemy piece could have attacked it; those attacks other than the one
+// played (and other than moves the two-square rule forbids) set the
+// piece's bits 22-32.  Lane j handles from-squares 4j .. 4j+3 from the
+// square sets (south, north, west, east neighbour is an enemy).  The bits
+// are ORed in atomically: other warps may record features of the same ply.
+__device__ __forceinline__ void active_adjacency(const SmemGame* G, FeatSmem* F, int a, uint32_t rule_flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = G->c.ply & 1;
+    const bool ts_on = (rule_flags & kTwoSquare) && G->c.ts_pid[P] != kNone && G->c.ts_len[P] == 4;
+    const Set128 mv{G->bmov[P][0] | G->bsco[P][0], G->bmov[P][1] | G->bsco[P][1]};
+    const Set128 en = ld128(G->bocc[1 - P]);
+    const Set128 nS = and128(mv, up10(en)), nN = and128(mv, dn10(en));
+    const Set128 nW = and128(and128(mv, up1(en)), Set128{~kCol0Lo, ~kCol0Hi});
+    const Set128 nE = and128(and128(mv, dn1(en)), Set128{~kCol9Lo, ~kCol9Hi});
+    const int off = 4 * lane;
+    const uint32_t bs = bits_at(nS, off, 4), bn = bits_at(nN, off, 4);
+    const uint32_t bw = bits_at(nW, off, 4), be = bits_at(nE, off, 4);
+    uint32_t any = bs | bn | bw | be;
+    while (any) {
+        const int c = __ffs(any) - 1;
+        any &= any - 1;
+        const int sq = off + c;
+        const int pid = G->board[sq];
+        uint64_t bits = 0;
+#pragma unroll
+        for (int dir = 0; dir < 4; ++dir) {
+            const uint32_t m = dir == 0 ? bs : dir == 1 ? bn : dir == 2 ? bw : be;
+            if (!((m >> c) & 1u)) continue;
+            const int n = sq + (dir == 0 ? -10 : dir == 1 ? 10 : dir == 2 ? -1 : 1);
+            if (sq * 100 + n == a) continue;
+            if (ts_on && pid == G->c.ts_pid[P] && two_square_blocks(G, P, n)) continue;
+            bits |= fbit(feat_rank_or_hidden(G, G->board[n])) << 22;
+        }
+        if (bits) atomicOr(reinterpret_cast<unsigned long long*>(&F->a[pid]), (unsigned long long)bits);
+    }
+    __syncwarp(0xFFFFFFFFu);
+}
+
+// Evasion and protection by action a (a non-battle move), from the position
+// before it, on the calling warp's first lane: the mover evades the piece
+// the opponent's previous non-battle move brought next to it (bits 11-21),
+// or protects a piece that move threatens (B bits of the mover and the
+// protected piece).  Atomic ORs as in active_adjacency.
+__device__ __forceinline__ void evasion_protection(const SmemGame* G, FeatSmem* F, int a)
 {
     const int lane = threadIdx.x & 31;
     const int P = G->c.ply & 1;
     const int from = a / 100, to = a - 100 * (a / 100);
     const int X = G->board[from];
     const bool battle = G->board[to] != kEmpty;
-    const bool ts_on = (rule_flags & kTwoSquare) && G->c.ts_pid[P] != kNone && G->c.ts_len[P] == 4;
-    // active adjacency: own movable pieces next to enemy pieces, from the
-    // square sets (south, north, west, east neighbour is an enemy); lane j
-    // handles from-squares 4j .. 4j+3, each square's pairs in one pass
-    {
-        const Set128 mv{G->bmov[P][0] | G->bsco[P][0], G->bmov[P][1] | G->bsco[P][1]};
-        const Set128 en = ld128(G->bocc[1 - P]);
-        const Set128 nS = and128(mv, up10(en)), nN = and128(mv, dn10(en));
-        const Set128 nW = and128(and128(mv, up1(en)), Set128{~kCol0Lo, ~kCol0Hi});
-        const Set128 nE = and128(and128(mv, dn1(en)), Set128{~kCol9Lo, ~kCol9Hi});
-        const int off = 4 * lane;
-        const uint32_t bs = bits_at(nS, off, 4), bn = bits_at(nN, off, 4);
-        const uint32_t bw = bits_at(nW, off, 4), be = bits_at(nE, off, 4);
-        uint32_t any = bs | bn | bw | be;
-        while (any) {
-            const int c = __ffs(any) - 1;
-            any &= any - 1;
-            const int sq = off + c;
-            const int pid = G->board[sq];
-            uint64_t bits = 0;
-#pragma unroll
-            for (int dir = 0; dir < 4; ++dir) {
-                const uint32_t m = dir == 0 ? bs : dir == 1 ? bn : dir == 2 ? bw : be;
-                if (!((m >> c) & 1u)) continue;
-                const int n = sq + (dir == 0 ? -10 : dir == 1 ? 10 : dir == 2 ? -1 : 1);
-                if (sq * 100 + n == a) continue;
-                if (ts_on && pid == G->c.ts_pid[P] && two_square_blocks(G, P, n)) continue;
-                bits |= fbit(feat_rank_or_hidden(G, G->board[n])) << 22;
-            }
-            F->a[pid] |= bits;
-        }
-    }
-    __syncwarp(0xFFFFFFFFu);
     if (lane == 0 && !battle) {
+        unsigned long long* fa = reinterpret_cast<unsigned long long*>(F->a);
+        unsigned long long* fb = reinterpret_cast<unsigned long long*>(F->b);
         const PlyCtx x = make_ctx(G);
         const int ap = x.prev_to;
         if (ap >= 0 && x.prev_nb && enemy_of(G->board[ap], P)) {
             const int A = G->board[ap];
             if (adjacent(from, ap) && !adjacent(to, ap))
-                F->a[X] |= fbit(feat_rank_or_hidden(G, A)) << 11;
+                atomicOr(&fa[X], (unsigned long long)(fbit(feat_rank_or_hidden(G, A)) << 11));
             const int ar = ap / 10, ac = ap - 10 * ar;
             int nb[4], nn = 0;
             if (ar > 0 && !is_lake(ap - 10)) nb[nn++] = ap - 10;
@@ -146,13 +157,13 @@ __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, 
                     if (!(adjacent(to, s) && !adjacent(from, s))) continue;
                     uint64_t bx = B == kEmpty ? fbit(11) : fbit(feat_type11(G, B, 12));
                     if (a_idx >= 0) bx |= fbit(a_idx == 11 ? 25 : 13 + a_idx);
-                    F->b[X] |= bx;
+                    atomicOr(&fb[X], (unsigned long long)bx);
                     if (B < kPieces) {
                         const int c_idx = feat_type11(G, X, 11);
                         uint64_t bb = 0;
                         if (c_idx >= 0) bb |= fbit(c_idx == 11 ? 38 : 26 + c_idx);
                         if (a_idx >= 0) bb |= fbit(a_idx == 11 ? 51 : 39 + a_idx);
-                        F->b[B] |= bb;
+                        atomicOr(&fb[B], (unsigned long long)bb);
                     }
                 }
             }
@@ -161,12 +172,16 @@ __device__ __forceinline__ void features_before(const SmemGame* G, FeatSmem* F, 
     __syncwarp(0xFFFFFFFFu);
 }
 
-// Threats made by the move just applied (a = from*100+to); call after apply_move.
-__device__ __forceinline__ void features_after(const SmemGame* G, FeatSmem* F, int a, bool battle)
+// Threats made by action a (a non-battle move ending next to enemy pieces),
+// read from the position before the move: a non-battle move changes only
+// its two squares (`from` holds the mover's own piece before the move and
+// nothing after, neither an enemy of the mover) and no piece's flags, so a
+// warp can record them while another warp works out the move.
+__device__ __forceinline__ void threats_of_move(const SmemGame* G, FeatSmem* F, int a, bool battle)
 {
     if ((threadIdx.x & 31) == 0 && !battle) {
-        const int to = a - 100 * (a / 100);
-        const int X = G->board[to];
+        const int from = a / 100, to = a - 100 * (a / 100);
+        const int X = G->board[from];
         const int P = X / 40;
         const int r = to / 10, c = to - 10 * r;
         uint64_t bits = 0;
@@ -174,7 +189,7 @@ __device__ __forceinline__ void features_after(const SmemGame* G, FeatSmem* F, i
         if (r < 9 && enemy_of(G->board[to + 10], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to + 10]));
         if (c > 0 && enemy_of(G->board[to - 1], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to - 1]));
         if (c < 9 && enemy_of(G->board[to + 1], P)) bits |= fbit(feat_rank_or_hidden(G, G->board[to + 1]));
-        F->a[X] |= bits;
+        if (bits) atomicOr(reinterpret_cast<unsigned long long*>(&F->a[X]), (unsigned long long)bits);
     }
     __syncwarp(0xFFFFFFFFu);
 }

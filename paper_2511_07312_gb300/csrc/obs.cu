@@ -1,16 +1,19 @@
 // obs.cu -- replay of action logs into positions and the information-state
 // planes of App. C (st_replay_positions, st_obs_encode).
 //
-// Two kernels.  k_replay: one warp per chunk of consecutive items replays
-// each item's log in shared memory (with full legality checks and the
-// history features), continuing from the previous item of the chunk when it
-// is the same game at a later ply, so items sorted by (game, ply) walk each
-// log once per chunk (App. B.1: compact records, states reconstructed on
-// demand).  It writes the replayed state of every item to a scratch record
+// Two kernels.  k_replay: a block of four warps per run of consecutive
+// items replays each item's log in shared memory (with full legality checks
+// and the history features), continuing from the previous item of the run
+// when it is the same game at a later ply, so items sorted by (game, ply)
+// walk each log once per run (App. B.1: compact records, states
+// reconstructed on demand).  Within a ply the warps split the work on the
+// position before the move (the move worked out, its legality, two sets of
+// features), so the ply's serial path is the longest of them rather than
+// their sum.  It writes the replayed state of every item to a scratch record
 // (or an st_position), plus the legal mask.  k_obs_emit: one warp per item
 // turns the record into the 487 planes: lane l owns four squares, all lanes
-// walk the channels together, and each channel row is one coalesced 100-byte
-// uint8 store and one 200-byte bf16 store per warp.
+// walk the channels together, and each channel row is one coalesced
+// 100-byte uint8 store and one 200-byte bf16 store per warp.
 #include <mutex>
 #include <atomic>
 #include "engine.cuh"
@@ -21,7 +24,7 @@ using namespace stg;
 
 namespace {
 
-constexpr int kReplayWarps = 4;
+constexpr int kReplayWarps = 4;                    // a replay block: move, legality, two feature warps
 constexpr int kEmitWarps = 4;
 constexpr int kPlaneBytes = ST_NCHAN * 100;        // 48,700
 constexpr int kGroups = ST_NCHAN * 25;             // 4 squares per group
@@ -40,6 +43,7 @@ struct __align__(16) ReplaySmem {
     FeatSmem f;
     uint64_t pi[kPiWords];
     uint16_t ring[kRing];
+    int live, legal;   // the game goes on (warp 0), the action is legal (warp 1): written before the block's barrier
 };
 
 struct ReplayArgs {
@@ -51,7 +55,7 @@ struct ReplayArgs {
     const int16_t* ply;
     int B;
     Rules R;
-    int items_per_warp;
+    int items_per_block;
     ItemState* state_out;    // obs mode
     st_position* pos_out;    // position mode
     uint8_t* mask_out;
@@ -94,20 +98,31 @@ __device__ void write_position(const SmemGame* G, const uint16_t* ring, st_posit
     }
 }
 
-__device__ void zero_bytes(uint8_t* dst, int n)
+// Zeroes n bytes with every thread of the block.
+__device__ void zero_block(void* dst, int n)
 {
-    for (int i = lane_id(); i < n; i += 32) dst[i] = 0;
+    uint8_t* d = static_cast<uint8_t*>(dst);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = 0;
 }
 
-__global__ void k_replay(ReplayArgs A)
+// One block of four warps per run of items_per_block consecutive items
+// replays each item's log in shared memory, continuing from the previous
+// item of the run when it is the same game at a later ply.  Per ply the
+// warps read the position before the move side by side: warp 0 checks that
+// the game has not ended and works out the move without writing
+// (plan_apply), warp 1 checks the move's legality, warps 2 and 3 record the
+// history features it adds (active adjacency; evasion, protection and
+// threats); after a block barrier warp 0 writes the move (commit_apply).
+// At an item the block writes its status and, as asked, its snapshot or
+// replay record (warp 0) and its legal mask (warp 1).
+__global__ void __launch_bounds__(32 * kReplayWarps) k_replay(ReplayArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    ReplaySmem* S = reinterpret_cast<ReplaySmem*>(smem) + (threadIdx.x >> 5);
+    ReplaySmem* S = reinterpret_cast<ReplaySmem*>(smem);
     SmemGame* G = &S->g;
-    const int lane = lane_id();
-    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int i0 = warp * A.items_per_warp;
-    const int i1 = min(A.B, i0 + A.items_per_warp);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * A.items_per_block;
+    const int i1 = min(A.B, i0 + A.items_per_block);
     const bool track = A.state_out != nullptr;
     int cur_game = -1, cur_ply = 0;
     bool valid = false;
@@ -119,50 +134,70 @@ __global__ void k_replay(ReplayArgs A)
             const uint8_t* setup = A.setups + 80 * (size_t)gi;
             ok = setup_ok(setup);
             if (ok) {
-                reset_game(G, Team<32>(), 0, 0, 0, 0, setup);
-                for (int k = lane; k < kPieces; k += 32) { S->f.a[k] = 0; S->f.b[k] = 0; }
-                __syncwarp();
+                if (warp == 0) reset_game(G, Team<32>(), 0, 0, 0, 0, setup);
+                for (int k = threadIdx.x; k < kPieces; k += blockDim.x) { S->f.a[k] = 0; S->f.b[k] = 0; }
                 cur_game = gi;
                 cur_ply = 0;
                 valid = true;
             } else {
                 valid = false;
             }
+            __syncthreads();
         }
         if (ok) {
             const int16_t* log = A.actions + (size_t)A.log_len * (size_t)gi;
             while (cur_ply < p) {
-                // an intermediate position must not have ended the game
-                if (cur_ply > 0 && (flag_dead(G, G->c.ply & 1) || G->c.battleless >= A.R.k ||
-                                    G->c.ply >= A.R.cap)) { ok = false; break; }
                 const int a = log[cur_ply];
-                if (!move_legal(G, a, A.R.flags, S->ring, S->pi)) { ok = false; break; }
-                const bool battle = G->board[a - 100 * (a / 100)] != kEmpty;
-                if (track) features_before(G, &S->f, a, A.R.flags, S->ring);
-                apply_move(G, Team<32>(), a, S->ring, S->pi);
-                if (track) features_after(G, &S->f, a, battle);
+                const bool in_range = a >= 0 && a < 10000;
+                ApplyPlan plan;
+                if (warp == 0) {
+                    if (lane == 0) {
+                        // an intermediate position must not have ended the game
+                        S->live = !(cur_ply > 0 && (flag_dead(G, G->c.ply & 1) || G->c.battleless >= A.R.k ||
+                                                    G->c.ply >= A.R.cap));
+                        if (in_range) plan = plan_apply(G, a);
+                    }
+                } else if (warp == 1) {
+                    const bool legal = move_legal(G, a, A.R.flags, S->ring, S->pi);
+                    if (lane == 0) S->legal = legal;
+                } else if (track && in_range && G->board[a / 100] < kPieces) {
+                    // (an illegal action's features are discarded with the item)
+                    if (warp == 2) {
+                        active_adjacency(G, &S->f, a, A.R.flags);
+                    } else {
+                        evasion_protection(G, &S->f, a);
+                        threats_of_move(G, &S->f, a, G->board[a - 100 * (a / 100)] != kEmpty);
+                    }
+                }
+                __syncthreads();
+                const bool legal = S->live && S->legal;
+                if (warp == 0 && lane == 0 && legal) commit_apply(G, plan, S->ring, S->pi);
+                __syncthreads();
+                if (!legal) { ok = false; break; }
                 ++cur_ply;
             }
             if (!ok) valid = false;
         }
-        if (lane == 0 && A.status) A.status[i] = ok ? 0 : 1;
+        if (threadIdx.x == 0 && A.status) A.status[i] = ok ? 0 : 1;
         if (!ok) {
-            if (A.pos_out) zero_bytes(reinterpret_cast<uint8_t*>(A.pos_out + i), sizeof(st_position));
-            if (A.state_out) zero_bytes(reinterpret_cast<uint8_t*>(A.state_out + i), sizeof(ItemState));
-            if (A.mask_out) zero_bytes(A.mask_out + (size_t)i * kMaskBytes, kMaskBytes);
+            if (A.pos_out) zero_block(A.pos_out + i, sizeof(st_position));
+            if (A.state_out) zero_block(A.state_out + i, sizeof(ItemState));
+            if (A.mask_out) zero_block(A.mask_out + (size_t)i * kMaskBytes, kMaskBytes);
             continue;
         }
-        if (A.pos_out) write_position(G, S->ring, A.pos_out + i);
-        if (A.state_out) {
-            ItemState* o = A.state_out + i;
-            if (lane < 18) reinterpret_cast<uint4*>(&o->c)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
-            o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
-            for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
-        }
-        if (A.mask_out)
+        if (warp == 0) {
+            if (A.pos_out) write_position(G, S->ring, A.pos_out + i);
+            if (A.state_out) {
+                ItemState* o = A.state_out + i;
+                if (lane < 18) reinterpret_cast<uint4*>(&o->c)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
+                o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
+                for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
+            }
+        } else if (warp == 1 && A.mask_out) {
             gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi,
                       reinterpret_cast<uint32_t*>(A.mask_out + (size_t)i * kMaskBytes));
-        __syncwarp();
+        }
+        __syncthreads();   // outputs done before the next item's replay changes the game
     }
 }
 
@@ -434,19 +469,19 @@ ReplayArgs replay_args(const uint8_t* setups, const int16_t* actions, int32_t lo
     a.setups = setups; a.actions = actions; a.log_len = log_len; a.num_logs = num_logs;
     a.game = game; a.ply = ply; a.B = B;
     a.R.k = rules->battleless_limit; a.R.cap = rules->max_plies; a.R.flags = rules->flags;
-    a.items_per_warp = 4;
+    a.items_per_block = 32;
     return a;
 }
 
-std::atomic<int> g_items_per_warp{8};   // fastest measured on GB300 for 16,384 items of 64 logs
+std::atomic<int> g_items_per_block{32};   // fastest measured on GB300 for 16,384 items of 64 logs
 
 }  // namespace
 
-extern "C" st_status st_replay_set_chunk(int32_t items_per_warp)
+extern "C" st_status st_replay_set_chunk(int32_t items_per_block)
 {
     ST_NVTX("st_replay_set_chunk");
-    ST_CHECK_ARG(items_per_warp >= 1 && items_per_warp <= 65536, "st_replay_set_chunk: 1..65536");
-    g_items_per_warp.store(items_per_warp);
+    ST_CHECK_ARG(items_per_block >= 1 && items_per_block <= 65536, "st_replay_set_chunk: 1..65536");
+    g_items_per_block.store(items_per_block);
     return ST_OK;
 }
 
@@ -462,12 +497,11 @@ extern "C" st_status st_replay_positions(const uint8_t* setups, const int16_t* a
     ST_CHECK_ARG(setups && actions && game && ply && out, "st_replay_positions: null argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp.load();
+    a.items_per_block = g_items_per_block.load();
     a.pos_out = out;
     a.status = item_status;
-    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
-    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
-    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    const int blocks = (B + a.items_per_block - 1) / a.items_per_block;
+    k_replay<<<blocks, 32 * kReplayWarps, sizeof(ReplaySmem), s>>>(a);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
@@ -498,14 +532,13 @@ extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions
         }
     }
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp.load();
+    a.items_per_block = g_items_per_block.load();
     a.state_out = scratch;
     a.mask_out = mask;
     a.status = status;
     if (!need_planes && !mask && !status) return ST_OK;
-    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
-    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
-    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    const int blocks = (B + a.items_per_block - 1) / a.items_per_block;
+    k_replay<<<blocks, 32 * kReplayWarps, sizeof(ReplaySmem), s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess && need_planes) {
         EmitArgs e{};
@@ -605,13 +638,12 @@ extern "C" st_status st_obs_encode_static(const uint8_t* setups, const int16_t* 
     // k_obs_emit reads them, so nothing left by an earlier call is read and
     // nothing needs clearing first.
     ReplayArgs a = replay_args(setups, actions, log_len, num_logs, game, ply, B, rules);
-    a.items_per_warp = g_items_per_warp.load();
+    a.items_per_block = g_items_per_block.load();
     a.state_out = need_planes ? sc.items : nullptr;
     a.mask_out = mask;
     a.status = status;
-    const int warps = (B + a.items_per_warp - 1) / a.items_per_warp;
-    const int blocks = (warps + kReplayWarps - 1) / kReplayWarps;
-    k_replay<<<blocks, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem), s>>>(a);
+    const int blocks = (B + a.items_per_block - 1) / a.items_per_block;
+    k_replay<<<blocks, 32 * kReplayWarps, sizeof(ReplaySmem), s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess && need_planes) {
         EmitArgs e{};

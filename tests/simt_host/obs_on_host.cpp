@@ -2,7 +2,7 @@
 // k_obs_emit) on host threads through include/cuda_runtime.h of this
 // directory, on inputs read from <in>.{setups,actions,game,ply,player}
 // (player may be absent), and writes <out>.{planes,bf16,mask,status}.
-//   obs_on_host in num_logs log_len B items_per_warp out
+//   obs_on_host in num_logs log_len B items_per_block out
 #include <sys/stat.h>
 #include "host_launch.h"
 #include "obs_dev.cu"
@@ -30,13 +30,11 @@ int main(int argc, char** argv)
     std::vector<uint8_t> planes((size_t)B * kPlaneBytes, 0xAB);
     std::vector<uint16_t> bf((size_t)B * kPlaneBytes, 0xABAB);
     ReplayArgs a = replay_args(setups.data(), actions.data(), log_len, num_logs, game.data(), ply.data(), B, &rules);
-    a.items_per_warp = ipw;
+    a.items_per_block = ipw;
     a.state_out = items.data();
     a.mask_out = mask.data();
     a.status = status.data();
-    const int warps = (B + ipw - 1) / ipw;
-    launch((warps + kReplayWarps - 1) / kReplayWarps, 32 * kReplayWarps, kReplayWarps * sizeof(ReplaySmem),
-           [=] { k_replay(a); });
+    launch((B + ipw - 1) / ipw, 32 * kReplayWarps, sizeof(ReplaySmem), [=] { k_replay(a); });
     EmitArgs e{};
     e.items = items.data(); e.status = status.data(); e.player = player.empty() ? nullptr : player.data();
     e.B = B; e.R = a.R; e.planes = planes.data(); e.planes_bf16 = bf.data();

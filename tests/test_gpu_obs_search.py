@@ -43,7 +43,7 @@ def test_replay_positions_bit_exact(sort, chunk):
         pos, status = st.replay_positions(S, A, torch.from_numpy(games).cuda(), torch.from_numpy(plies).cuda())
         torch.cuda.synchronize()
     finally:
-        st.set_replay_chunk(8)
+        st.set_replay_chunk(32)
     assert (status.cpu().numpy() == 0).all()
     ref = oracle.replay_positions(g["setups"], g["actions"], games, plies)
     np.testing.assert_array_equal(pos.cpu().numpy(), ref)
