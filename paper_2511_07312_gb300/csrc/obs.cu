@@ -110,9 +110,10 @@ __device__ void zero_block(void* dst, int n)
 // item of the run when it is the same game at a later ply.  Per ply the
 // warps read the position before the move side by side: warp 0 checks that
 // the game has not ended and works out the move without writing
-// (plan_apply), warp 1 checks the move's legality, warps 2 and 3 record the
-// history features it adds (active adjacency; evasion, protection and
-// threats); after a block barrier warp 0 writes the move (commit_apply).
+// (plan_apply), warp 1 checks the move's legality and records its threats,
+// warps 2 and 3 record its other history features (active adjacency;
+// evasion and protection); after a block barrier warp 0 writes the move
+// (commit_apply).
 // At an item the block writes its status and, as asked, its snapshot or
 // replay record (warp 0) and its legal mask (warp 1).
 __global__ void __launch_bounds__(32 * kReplayWarps) k_replay(ReplayArgs A)
@@ -160,14 +161,12 @@ __global__ void __launch_bounds__(32 * kReplayWarps) k_replay(ReplayArgs A)
                 } else if (warp == 1) {
                     const bool legal = move_legal(G, a, A.R.flags, S->ring, S->pi);
                     if (lane == 0) S->legal = legal;
-                } else if (track && in_range && G->board[a / 100] < kPieces) {
                     // (an illegal action's features are discarded with the item)
-                    if (warp == 2) {
-                        active_adjacency(G, &S->f, a, A.R.flags);
-                    } else {
-                        evasion_protection(G, &S->f, a);
+                    if (track && in_range && G->board[a / 100] < kPieces)
                         threats_of_move(G, &S->f, a, G->board[a - 100 * (a / 100)] != kEmpty);
-                    }
+                } else if (track && in_range && G->board[a / 100] < kPieces) {
+                    if (warp == 2) active_adjacency(G, &S->f, a, A.R.flags);
+                    else evasion_protection(G, &S->f, a);
                 }
                 __syncthreads();
                 const bool legal = S->live && S->legal;
