@@ -259,17 +259,50 @@ struct RowOut {
     // cells of value 0 or 1 (u8 1, bf16 1.0)
     __device__ __forceinline__ void bits(int ch, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) const
     {
+        packed(ch, b0 | (b1 << 8) | (b2 << 16) | (b3 << 24));
+    }
+    // the same, the four cells given as the bytes of m (each 0 or 1)
+    __device__ __forceinline__ void packed(int ch, uint32_t m) const
+    {
         if (!on) return;
-        if (u8) *reinterpret_cast<uint32_t*>(u8 + 100 * ch + 4 * l) = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+        if (u8) *reinterpret_cast<uint32_t*>(u8 + 100 * ch + 4 * l) = m;
         if (bf)
             *reinterpret_cast<uint2*>(bf + 100 * ch + 4 * l) =
-                make_uint2((b0 | (b1 << 16)) * 0x3F80u, (b2 | (b3 << 16)) * 0x3F80u);
+                make_uint2(((m & 1u) | ((m << 8) & 0x10000u)) * 0x3F80u,
+                           (((m >> 16) & 1u) | ((m >> 8) & 0x10000u)) * 0x3F80u);
+    }
+    // channels ch0 .. ch0+N-1: bit k of the four squares' words w, eight
+    // channels from one gather of the words' k/8-th bytes (byte i of X is
+    // square i's)
+    template <int N>
+    __device__ __forceinline__ void bit_channels(int ch0, const uint64_t (&w)[4]) const
+    {
+#pragma unroll
+        for (int k0 = 0; k0 < N; k0 += 8) {
+            const uint32_t X = (uint32_t)((w[0] >> k0) & 0xFFu) | ((uint32_t)((w[1] >> k0) & 0xFFu) << 8) |
+                               ((uint32_t)((w[2] >> k0) & 0xFFu) << 16) | ((uint32_t)((w[3] >> k0) & 0xFFu) << 24);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k0 + k < N) packed(ch0 + k0 + k, (X >> k) & 0x01010101u);
+        }
+    }
+    // rows ch0 .. ch0+N-1 cleared over the lane's four squares
+    template <int N>
+    __device__ __forceinline__ void zero_rows(int ch0) const
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) packed(ch0 + k, 0u);
+    }
+    // cell (row ch, square 4l+i) set to 1; its row was cleared by this lane
+    // before (the same thread's later store to the same bytes wins)
+    __device__ __forceinline__ void one(int ch, int i) const
+    {
+        if (!on) return;
+        if (u8) u8[100 * ch + 4 * l + i] = 1;
+        if (bf) bf[100 * ch + 4 * l + i] = 0x3F80u;
     }
 };
 
-// bit k of four 64-bit words as 0/1
-#define ST_BITS4(w, k) (uint32_t)(((w)[0] >> (k)) & 1ull), (uint32_t)(((w)[1] >> (k)) & 1ull), \
-                       (uint32_t)(((w)[2] >> (k)) & 1ull), (uint32_t)(((w)[3] >> (k)) & 1ull)
 
 __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const RowOut& o)
 {
@@ -287,10 +320,11 @@ __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const Row
         fl[i] = pc[i] ? st.c.flags[occ[i]] : 0u;
         ty[i] = pc[i] ? st.c.type[occ[i]] : 0xFF;
     }
-    // 0-11: own pieces by type
-    for (int t = 0; t < 12; ++t)
-        o.bits(t, pc[0] && mn[0] && ty[0] == t, pc[1] && mn[1] && ty[1] == t, pc[2] && mn[2] && ty[2] == t,
-               pc[3] && mn[3] && ty[3] == t);
+    // 0-11: own pieces by type (one channel per square at most)
+    o.zero_rows<12>(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (pc[i] && mn[i] && ty[i] < 12) o.one(ty[i], i);
     // 12-23 (opponent's pieces), 24-35 (own pieces): probability of each type
     for (int g = 0; g < 2; ++g) {
         const int want = g == 0 ? 1 - me : me;
@@ -328,7 +362,7 @@ __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const Row
         uint64_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = (pc[i] && mn[i] == (g == 0)) ? st.fa[occ[i]] : 0ull;
-        for (int k = 0; k < 33; ++k) o.bits(43 + 33 * g + k, ST_BITS4(w, k));
+        o.bit_channels<33>(43 + 33 * g, w);
     }
     // 109-119 / 120-130: captured piece whose start square this is, by type
     for (int g = 0; g < 2; ++g) {
@@ -343,8 +377,10 @@ __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const Row
                 idx[i] = t <= kMarshal ? t : (t == kBomb ? 10 : -1);
             }
         }
-        for (int ti = 0; ti < 11; ++ti)
-            o.bits(109 + 11 * g + ti, idx[0] == ti, idx[1] == ti, idx[2] == ti, idx[3] == ti);
+        o.zero_rows<11>(109 + 11 * g);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (idx[i] >= 0) o.one(109 + 11 * g + idx[i], i);
     }
     // 131-190 / 191-250: deaths on the square by cause and rank (own / opponent)
     for (int g = 0; g < 2; ++g) {
@@ -352,21 +388,24 @@ __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const Row
         uint64_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = E->death[want_side][s0 + i];
-        for (int k = 0; k < 60; ++k) o.bits(131 + 60 * g + k, ST_BITS4(w, k));
+        o.bit_channels<60>(131 + 60 * g, w);
     }
     // 251-302 / 303-354: further history features (own / opponent)
     for (int g = 0; g < 2; ++g) {
         uint64_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = (pc[i] && mn[i] == (g == 0)) ? st.fb[occ[i]] : 0ull;
-        for (int k = 0; k < 52; ++k) o.bits(251 + 52 * g + k, ST_BITS4(w, k));
+        o.bit_channels<52>(251 + 52 * g, w);
     }
     // 355-454: the piece on the square started on square ch - 355
     {
         int ss[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) ss[i] = pc[i] ? start_square(occ[i]) : -1;
-        for (int q = 0; q < 100; ++q) o.bits(355 + q, ss[0] == q, ss[1] == q, ss[2] == q, ss[3] == q);
+        o.zero_rows<100>(355);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (ss[i] >= 0) o.one(355 + ss[i], i);
     }
     // 455-486: the last 32 moves, +1 on the to-square and -1 on the from-square
     for (int j = 0; j < 32; ++j) {
@@ -380,7 +419,6 @@ __device__ __forceinline__ void emit_planes(const EmitSmem* E, int me, const Row
         o.codes(455 + j, c[0], c[1], c[2], c[3]);
     }
 }
-#undef ST_BITS4
 
 __global__ void k_obs_emit(EmitArgs A)
 {
