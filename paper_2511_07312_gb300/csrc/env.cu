@@ -432,6 +432,27 @@ constexpr int kMaxSplitPlies = 32768;   // launches longer than this are not spl
 #define ST_PART_SPIN_LIMIT (1ll << 22)   // polls of ~0.3-1 us: a few seconds
 #endif
 constexpr long long kPartSpinLimit = ST_PART_SPIN_LIMIT;
+// Has the slot's part h-1 been stored (its count of finished parts, *done,
+// reached h; the release is in k_env_run)?  The team's first lane polls,
+// bounded, then fences; team-uniform result.  Out of line: the wait's
+// registers stay out of the step loop's allocation.
+template <int L>
+__device__ __noinline__ bool part_ready(int32_t* done, int h, Team<L>)
+{
+    const Team<L> T;
+    int ok = 1;
+    if (T.leader()) {
+        long long spins = 0;
+        while (atomicAdd(done, 0) < h && spins < kPartSpinLimit) {
+            __nanosleep(256);
+            ++spins;
+        }
+        ok = spins < kPartSpinLimit;
+        __threadfence();
+    }
+    return T.shfl(ok, 0) != 0;
+}
+
 // At most 256 threads per block and 3 blocks per SM: <= 85 (80) registers a
 // thread; shared memory, not registers, bounds the resident teams.
 constexpr int kRunMaxWarps = 8;
@@ -439,7 +460,7 @@ template <int L, bool kHist>
 __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int32_t* queue, int n_steps, int ring_steps, int gpf,
                                                  int16_t* action_ring, int8_t* reward_ring, uint8_t* done_ring,
                                                  int16_t* ply_ring, uint8_t* mask_ring, int nsplit,
-                                                 int32_t* part_done)
+                                                 int part, int32_t* part_done)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Team<L> T;
@@ -447,9 +468,11 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
     // player to move right after it (rows_of), which is also the buffer the
     // bulk copies send to the ring
     SmemGame* G = reinterpret_cast<SmemGame*>(smem + (size_t)(threadIdx.x / L) * kRowsRecordBytes);
-    const int units = A.N * nsplit;
-    const int part = (n_steps + nsplit - 1) / nsplit;
+    // (part = ceil(n_steps / nsplit) plies, a launch parameter: like every
+    // per-launch bound, it is read from the parameter bank rather than held
+    // in a register across the plies)
     for (;;) {
+        const int units = A.N * nsplit;
         // each team claims its own units: no collective spans more than one team
         int first = 0;
         if (T.leader()) first = atomicAdd(queue, gpf);
@@ -457,26 +480,12 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
         if (first >= units) break;
         for (int gi = 0; gi < gpf; ++gi) {
             const int u = first + gi;
-            if (u >= units) break;
+            if (u >= A.N * nsplit) break;
             const int h = u / A.N, g = u - h * A.N;          // part h of slot g
             const int j0 = h * part, j1 = min(n_steps, j0 + part);
-            if (h > 0) {
-                // the slot's previous part has been stored (release below)
-                int ok = 1;
-                if (T.leader()) {
-                    long long spins = 0;
-                    while (atomicAdd(&part_done[g], 0) < h && spins < kPartSpinLimit) {
-                        __nanosleep(256);
-                        ++spins;
-                    }
-                    ok = spins < kPartSpinLimit;
-                    __threadfence();
-                }
-                ok = T.shfl(ok, 0);
-                if (!ok) {
-                    if (T.leader()) latch(A.status, ST_ERR_TIMEOUT, g);
-                    continue;
-                }
+            if (h > 0 && !part_ready(part_done + g, h, T)) {
+                if (T.leader()) latch(A.status, ST_ERR_TIMEOUT, g);
+                continue;
             }
             uint16_t* ring = A.ring + (size_t)g * kRing;
             uint64_t* pi = A.pi + (size_t)g * kPiWords;
@@ -491,7 +500,9 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
             if (kHist && T.leader()) G->c.hrow = (uint16_t)((*A.now + j0) % A.H);
             int row = j0 % ring_steps;   // output ring row of ply j: j mod ring_steps
-            for (int j = j0; j < j1; ++j) {
+            // a countdown, so that neither the part's bounds nor its index
+            // stay live in registers across the plies
+            for (int left = j1 - j0; left > 0; --left) {
                 bool illegal;
                 if (kHist) hist_before(G, T);
                 const size_t o = (size_t)row * (size_t)A.N + (size_t)g;
@@ -523,7 +534,7 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
                 // store are in global memory before the next part may start
                 __threadfence();
                 T.sync();
-                if (T.leader()) atomicExch(&part_done[g], h + 1);
+                if (T.leader()) atomicAdd(&part_done[g], 1);   // parts end in order: the count of parts done
             }
         }
     }
@@ -935,11 +946,11 @@ void launch_run_t(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring
     if (a.hist)
         k_env_run<L, true><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
             a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit,
-            e->part_done);
+            (n_steps + nsplit - 1) / nsplit, e->part_done);
     else
         k_env_run<L, false><<<blocks, 32 * e->wpb, run_smem(e->wpb, 32 / L), e->stream>>>(
             a, e->queue, n_steps, ring_steps, e->gpf, action_ring, reward_ring, done_ring, ply_ring, mask_ring, nsplit,
-            e->part_done);
+            (n_steps + nsplit - 1) / nsplit, e->part_done);
 }
 
 void launch_run(st_env* e, const EnvArgs& a, int blocks, int n_steps, int ring_steps, int16_t* action_ring,

@@ -19,7 +19,7 @@ static void run(EnvArgs a, int32_t* queue, int S, int gpf, int wpb, int blocks, 
 {
     const size_t sm = (size_t)wpb * (32 / L) * kRowsRecordBytes;   // row-mode records, each followed by its mask
     launch(blocks, 32 * wpb, sm,
-           [=] { k_env_run<L, false>(a, queue, S, S, gpf, act, rew, done, ply, mask, nsplit, part_done); });
+           [=] { k_env_run<L, false>(a, queue, S, S, gpf, act, rew, done, ply, mask, nsplit, (S + nsplit - 1) / nsplit, part_done); });
 }
 
 int main(int argc, char** argv)

@@ -75,7 +75,7 @@ int main(int argc, char** argv)
         std::vector<int32_t> part_done((size_t)N, 0);
         int32_t* dn = part_done.data();
         const size_t sm = (size_t)wpb * 4 * kRowsRecordBytes;   // row-mode records, each followed by its mask
-        launch(nblocks, 32 * wpb, sm, [=] { k_env_run<8, true>(a, qp, S, S, gpf, ap, rp, dp, pp, mp, 2, dn); });
+        launch(nblocks, 32 * wpb, sm, [=] { k_env_run<8, true>(a, qp, S, S, gpf, ap, rp, dp, pp, mp, 2, (S + 1) / 2, dn); });
     }
     d_now += S;
     dump(out + ".action", act.data(), act.size());
