@@ -432,6 +432,49 @@ constexpr int kMaxSplitPlies = 32768;   // launches longer than this are not spl
 #define ST_PART_SPIN_LIMIT (1ll << 22)   // polls of ~0.3-1 us: a few seconds
 #endif
 constexpr long long kPartSpinLimit = ST_PART_SPIN_LIMIT;
+// A work unit's start: the slot's game into the team's record (core,
+// board, derived state), the staging buffer free of the previous unit's
+// last copy, the moves of the player to move recorded, the launch counters
+// cleared.  Returns the number of legal moves.  Out of line, like the other
+// per-unit steps, so that the step loop's registers are allocated alone.
+template <int L>
+__device__ __noinline__ int unit_start(SmemGame* G, const GameCore* core, uint16_t* ring, uint64_t* pi,
+                                       uint32_t rule_flags, bool staged, Team<L>)
+{
+    const Team<L> T;
+    load_core(G, core, T);
+    build_board(G, T);
+    derive_state(G, ring, pi, T);
+    if (staged) mask_free(T);   // the previous unit's last copy has read the staging buffer
+    int n = 0;
+    if (!G->c.terminated) n = gen_moves<L, true>(G, T, G->c.ply & 1, rule_flags, false, true, pi, rows_of(G));
+    // the launch's counters live in shared memory, not in registers that
+    // every engine call would have to save
+    for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
+    return n;
+}
+
+// A work unit's end: the launch counters added to the slot's, the record
+// back to the slot's core; with done (the slot's count of finished parts),
+// the release of the slot's next part: the record, counters, history ring
+// and chase store are in global memory first.
+template <int L>
+__device__ __noinline__ void unit_finish(SmemGame* G, GameCore* core, uint32_t* stats, int n, int32_t* done, Team<L>)
+{
+    const Team<L> T;
+    if (T.leader()) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) stats[k] += G->stat[k];
+        G->c.n_legal = (uint16_t)n;
+    }
+    store_core(G, core, T);
+    if (done) {
+        __threadfence();
+        T.sync();
+        if (T.leader()) atomicAdd(done, 1);   // parts end in order: the count of parts done
+    }
+}
+
 // Has the slot's part h-1 been stored (its count of finished parts, *done,
 // reached h; the release is in k_env_run)?  The team's first lane polls,
 // bounded, then fences; team-uniform result.  Out of line: the wait's
@@ -489,15 +532,7 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
             }
             uint16_t* ring = A.ring + (size_t)g * kRing;
             uint64_t* pi = A.pi + (size_t)g * kPiWords;
-            load_core(G, A.core + g, T);
-            build_board(G, T);
-            derive_state(G, ring, pi, T);
-            if (mask_ring) mask_free(T);   // the previous slot's last copy has read the staging buffer
-            int n = 0;
-            if (!G->c.terminated) n = gen_moves<L, true>(G, T, G->c.ply & 1, A.R.flags, false, true, pi, rows_of(G));
-            // the launch's counters live in shared memory, not in registers
-            // that every engine call would have to save
-            for (int k = T.tl; k < 8; k += L) G->stat[k] = 0;
+            int n = unit_start<L>(G, A.core + g, ring, pi, A.R.flags, mask_ring != nullptr, T);
             if (kHist && T.leader()) G->c.hrow = (uint16_t)((*A.now + j0) % A.H);
             int row = j0 % ring_steps;   // output ring row of ply j: j mod ring_steps
             // a countdown, so that neither the part's bounds nor its index
@@ -522,20 +557,7 @@ __global__ void __launch_bounds__(32 * kRunMaxWarps, 3) k_env_run(EnvArgs A, int
                 }
                 if (mask_ring) write_mask_async(rows_of(G), T, mask_ring + o * kMaskBytes);
             }
-            if (T.leader()) {
-                uint32_t* gs = A.stats + 8 * (size_t)g;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) gs[k] += G->stat[k];
-                G->c.n_legal = (uint16_t)n;
-            }
-            store_core(G, A.core + g, T);
-            if (nsplit > 1) {
-                // release: the slot's record, counters, history ring and chase
-                // store are in global memory before the next part may start
-                __threadfence();
-                T.sync();
-                if (T.leader()) atomicAdd(&part_done[g], 1);   // parts end in order: the count of parts done
-            }
+            unit_finish<L>(G, A.core + g, A.stats + 8 * (size_t)g, n, nsplit > 1 ? part_done + g : nullptr, T);
         }
     }
     // the team's last mask copies have landed before it leaves
