@@ -202,3 +202,35 @@ def test_masks_of_past_positions():
         assert m["n_legal"][g].item() == len(moves)
         assert m["two_square"][g].item() == oracle.two_square_applies(pos[g])
     env.close()
+
+
+def test_history_recorded_by_a_persistent_launch_in_two_parts():
+    # one block of one warp per SM and 1.25 waves of slots: a 700-ply launch
+    # runs each slot's plies as two parts of 350, the second part of a slot
+    # recording into the history ring where its first part stopped
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, S, H, seed = sms + sms // 4 + 3, 700, 500, 33
+    env = st.Env(N, seed=seed)
+    env.set_launch(1, 1, 1, games_per_warp=1)
+    env.enable_history(H)
+    env.run(S)
+    assert env.current_step() == S
+    ref = oracle.env_run(seed, N, S, want_mask=False)
+    lo = S - H
+    for t in (S, 600, 351, 349, lo + 1):
+        hp = env.history_positions(t)
+        torch.cuda.synchronize()
+        status = hp["status"].cpu().numpy()
+        start, _ = _games_at(ref["done"], t)
+        want = np.where(start < lo, 2, 0) if t < S else np.zeros(N)
+        np.testing.assert_array_equal(status, want)
+        ok = status == 0
+        np.testing.assert_array_equal(hp["pos"].cpu().numpy()[ok], _final(seed, N, t)[ok])
+    for t in (S - 1, 351, 350, 349, lo):
+        hs = env.history_steps(t)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hs["action"].cpu().numpy(), ref["action"][t])
+        np.testing.assert_array_equal(hs["done"].cpu().numpy(), ref["done"][t])
+        np.testing.assert_array_equal(hs["reward"].cpu().numpy(), ref["reward"][t])
+    np.testing.assert_array_equal(env.stats().cpu().numpy(), ref["stats"].astype(np.int32))
+    env.close()
