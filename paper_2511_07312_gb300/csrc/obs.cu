@@ -62,7 +62,7 @@ struct ReplayArgs {
     uint8_t* status;
 };
 
-__device__ bool setup_ok(const uint8_t* s)
+__device__ __noinline__ bool setup_ok(const uint8_t* s)
 {
     int cnt[24];
     for (int i = 0; i < 24; ++i) cnt[i] = 0;
@@ -103,6 +103,35 @@ __device__ void zero_block(void* dst, int n)
 {
     uint8_t* d = static_cast<uint8_t*>(dst);
     for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = 0;
+}
+
+// Item i's outputs, with every thread of the replay block: its status and,
+// as asked, its snapshot or replay record (warp 0) and its legal mask (warp
+// 1), or zeros for an invalid item.  Out of line, so that the ply loop's
+// registers are allocated alone.
+__device__ __noinline__ void item_outputs(const ReplayArgs& A, ReplaySmem* S, int i, bool ok)
+{
+    SmemGame* G = &S->g;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0 && A.status) A.status[i] = ok ? 0 : 1;
+    if (!ok) {
+        if (A.pos_out) zero_block(A.pos_out + i, sizeof(st_position));
+        if (A.state_out) zero_block(A.state_out + i, sizeof(ItemState));
+        if (A.mask_out) zero_block(A.mask_out + (size_t)i * kMaskBytes, kMaskBytes);
+        return;
+    }
+    if (warp == 0) {
+        if (A.pos_out) write_position(G, S->ring, A.pos_out + i);
+        if (A.state_out) {
+            ItemState* o = A.state_out + i;
+            if (lane < 18) reinterpret_cast<uint4*>(&o->c)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
+            o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
+            for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
+        }
+    } else if (warp == 1 && A.mask_out) {
+        gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi,
+                  reinterpret_cast<uint32_t*>(A.mask_out + (size_t)i * kMaskBytes));
+    }
 }
 
 // One block of four warps per run of items_per_block consecutive items
@@ -177,25 +206,7 @@ __global__ void __launch_bounds__(32 * kReplayWarps) k_replay(ReplayArgs A)
             }
             if (!ok) valid = false;
         }
-        if (threadIdx.x == 0 && A.status) A.status[i] = ok ? 0 : 1;
-        if (!ok) {
-            if (A.pos_out) zero_block(A.pos_out + i, sizeof(st_position));
-            if (A.state_out) zero_block(A.state_out + i, sizeof(ItemState));
-            if (A.mask_out) zero_block(A.mask_out + (size_t)i * kMaskBytes, kMaskBytes);
-            continue;
-        }
-        if (warp == 0) {
-            if (A.pos_out) write_position(G, S->ring, A.pos_out + i);
-            if (A.state_out) {
-                ItemState* o = A.state_out + i;
-                if (lane < 18) reinterpret_cast<uint4*>(&o->c)[lane] = reinterpret_cast<const uint4*>(&G->c)[lane];
-                o->hist[lane] = (uint16_t)hist_at(G, S->ring, lane);
-                for (int k = lane; k < kPieces; k += 32) { o->fa[k] = S->f.a[k]; o->fb[k] = S->f.b[k]; }
-            }
-        } else if (warp == 1 && A.mask_out) {
-            gen_moves(G, Team<32>(), G->c.ply & 1, A.R.flags, false, true, S->pi,
-                      reinterpret_cast<uint32_t*>(A.mask_out + (size_t)i * kMaskBytes));
-        }
+        item_outputs(A, S, i, ok);
         __syncthreads();   // outputs done before the next item's replay changes the game
     }
 }
