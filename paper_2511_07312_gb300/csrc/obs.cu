@@ -285,10 +285,12 @@ struct RowOut {
     // channels ch0 .. ch0+N-1: bit k of the four squares' words w, eight
     // channels from one gather of the words' k/8-th bytes (byte i of X is
     // square i's)
+    // (loops kept rolled: the emission's code would otherwise outgrow the
+    // instruction cache)
     template <int N>
     __device__ __forceinline__ void bit_channels(int ch0, const uint64_t (&w)[4]) const
     {
-#pragma unroll
+#pragma unroll 1
         for (int k0 = 0; k0 < N; k0 += 8) {
             const uint32_t X = (uint32_t)((w[0] >> k0) & 0xFFu) | ((uint32_t)((w[1] >> k0) & 0xFFu) << 8) |
                                ((uint32_t)((w[2] >> k0) & 0xFFu) << 16) | ((uint32_t)((w[3] >> k0) & 0xFFu) << 24);
@@ -301,7 +303,7 @@ struct RowOut {
     template <int N>
     __device__ __forceinline__ void zero_rows(int ch0) const
     {
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) packed(ch0 + k, 0u);
     }
     // cell (row ch, square 4l+i) set to 1; its row was cleared by this lane
