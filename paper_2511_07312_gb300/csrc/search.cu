@@ -131,10 +131,15 @@ __global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_rollout_fla
     const int team = threadIdx.x / kFlatLanes;
     FlatSmem* S = reinterpret_cast<FlatSmem*>(smem) + team;
     uint64_t* pi = pi_scratch + ((size_t)blockIdx.x * kFlatTeams + team) * kPiWords;
-    const long long units = (long long)P * K;
+    if (K <= 0) return;
+    // unit u = p*K + k, this team's units u0, u0 + stride, ...: (p, k) is
+    // stepped by the stride's quotient and remainder instead of dividing
+    // each unit (no 64-bit counter held across the rollout)
+    const long long u0 = (long long)blockIdx.x * kFlatTeams + team;
     const long long stride = (long long)gridDim.x * kFlatTeams;
-    for (long long u = (long long)blockIdx.x * kFlatTeams + team; u < units; u += stride) {
-        const int p = (int)(u / K), k = (int)(u - (long long)p * K);
+    int p = (int)(u0 / K), k = (int)(u0 - (long long)p * K);
+    const int dp = (int)(stride / K), dk = (int)(stride - (long long)dp * K);
+    for (; p < P; p += dp, k += dk, p += k >= K ? 1 : 0, k -= k >= K ? K : 0) {
         const RootState* R = roots + p;
         if (R->bad) continue;
         const uint32_t stream = stream_ids ? stream_ids[p] : (uint32_t)p;
