@@ -476,7 +476,7 @@ __device__ __noinline__ void unit_finish(SmemGame* G, GameCore* core, uint32_t* 
 }
 
 // Has the slot's part h-1 been stored (its count of finished parts, *done,
-// reached h; the release is in k_env_run)?  The team's first lane polls,
+// reached h; the release is unit_finish's)?  The team's first lane polls,
 // bounded, then fences; team-uniform result.  Out of line: the wait's
 // registers stay out of the step loop's allocation.
 template <int L>
