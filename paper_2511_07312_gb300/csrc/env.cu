@@ -592,13 +592,14 @@ __global__ void k_env_sample(EnvArgs A, int16_t* out)
 
 // ----------------------------------------------------------------- snapshots
 
-// Warp: the snapshot of game G (history ring `ring`) into o.
-__device__ void export_position(const SmemGame* G, const uint16_t* ring, st_position* o)
+// Team: the snapshot of game G (history ring `ring`) into o.
+template <int L>
+__device__ void export_position(const SmemGame* G, const uint16_t* ring, st_position* o, const Team<L>& T)
 {
     uint8_t* ob = reinterpret_cast<uint8_t*>(o);
-    const int lane = lane_id();
-    for (int b = lane; b < 240; b += 32) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
-    for (int h = lane; h < 256; h += 32) o->hist[h] = (uint16_t)hist_at(G, ring, h);
+    const int lane = T.tl;
+    for (int b = lane; b < 240; b += L) ob[b] = reinterpret_cast<const uint8_t*>(&G->c)[b];
+    for (int h = lane; h < 256; h += L) o->hist[h] = (uint16_t)hist_at(G, ring, h);
     if (lane == 0) {
         o->ply = G->c.ply;
         o->battleless = G->c.battleless;
@@ -613,7 +614,7 @@ __device__ void export_position(const SmemGame* G, const uint16_t* ring, st_posi
         }
         for (int k = 0; k < 12; ++k) o->reserved1[k] = 0;
     }
-    __syncwarp();
+    T.sync();
 }
 
 __global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* out)
@@ -629,7 +630,7 @@ __global__ void k_env_export(EnvArgs A, const int32_t* idx, int n, st_position* 
         return;
     }
     load_core(G, A.core + g, T);
-    export_position(G, A.ring + (size_t)g * kRing, out + i);
+    export_position(G, A.ring + (size_t)g * kRing, out + i, T);
 }
 
 __global__ void k_env_import(EnvArgs A, const int32_t* idx, int n, const st_position* in)
@@ -705,19 +706,19 @@ __device__ __forceinline__ uint32_t hist_row(const HistQuery& Q, int N, int g, l
 __device__ __forceinline__ uint32_t row_mark(uint32_t v) { return (v >> 14) & 3u; }
 __device__ __forceinline__ uint32_t row_done(uint32_t v) { return (v >> 16) & 7u; }
 
-// Warp: the latest step s in [lo, hi] whose row has a nonzero field
+// Team: the latest step s in [lo, hi] whose row has a nonzero field
 // (field(v) != 0), -1 if none; val: that field.
-template <typename F>
-__device__ long long latest_row(const HistQuery& Q, int N, int g, long long hi, F field, uint32_t& val)
+template <int L, typename F>
+__device__ long long latest_row(const HistQuery& Q, int N, int g, long long hi, F field, uint32_t& val,
+                                const Team<L>& T)
 {
-    const int lane = lane_id();
-    for (long long base = hi; base >= Q.lo; base -= 32) {
-        const long long s = base - lane;
+    for (long long base = hi; base >= Q.lo; base -= L) {
+        const long long s = base - T.tl;
         const uint32_t f = s >= Q.lo ? field(hist_row(Q, N, g, s)) : 0u;
-        const uint32_t m = __ballot_sync(~0u, f != 0);
+        const uint32_t m = T.ballot(f != 0);
         if (m) {
             const int l = __ffs(m) - 1;
-            val = __shfl_sync(~0u, f, l);
+            val = (uint32_t)T.shfl((int)f, l);
             return base - l;
         }
     }
@@ -725,9 +726,10 @@ __device__ long long latest_row(const HistQuery& Q, int N, int g, long long hi, 
     return -1;
 }
 
-// Warp: where the game holding slot g at step Q.t began (-1: before the
+// Team: where the game holding slot g at step Q.t began (-1: before the
 // window) and how (kFresh*).  At t = now a pending mark of the slot counts.
-__device__ long long game_start(const HistQuery& Q, const GameCore* cur, int N, int g, int& kind)
+template <int L>
+__device__ long long game_start(const HistQuery& Q, const GameCore* cur, int N, int g, int& kind, const Team<L>& T)
 {
     if (Q.t == Q.now && cur->fresh) {
         kind = cur->fresh;
@@ -735,42 +737,55 @@ __device__ long long game_start(const HistQuery& Q, const GameCore* cur, int N, 
     }
     uint32_t k = 0;
     const long long s0 = latest_row(Q, N, g, Q.t == Q.now ? Q.now - 1 : Q.t,
-                                    [](uint32_t v) { return row_mark(v); }, k);
+                                    [](uint32_t v) { return row_mark(v); }, k, T);
     kind = (int)k;
     return s0;
 }
 
-// Warp: the episode number of the game that began at step s0 (counted back
+// Team: the episode number of the game that began at step s0 (counted back
 // from the slot's current episode over the later new games and resets).
-__device__ uint32_t episode_at(const HistQuery& Q, const GameCore* cur, int N, int g, long long s0)
+template <int L>
+__device__ uint32_t episode_at(const HistQuery& Q, const GameCore* cur, int N, int g, long long s0, const Team<L>& T)
 {
     int cnt = 0;
-    for (long long s = s0 + 1 + lane_id(); s < Q.now; s += 32) {
+    for (long long s = s0 + 1 + T.tl; s < Q.now; s += L) {
         const uint32_t m = row_mark(hist_row(Q, N, g, s));
         cnt += (m == kFreshNew || m == kFreshSetup);
     }
-    cnt = (int)__reduce_add_sync(~0u, (unsigned)cnt);
+    cnt = T.sum(cnt);
     const int pending = (s0 < Q.now && (cur->fresh == kFreshNew || cur->fresh == kFreshSetup)) ? 1 : 0;
     return cur->episode - (uint32_t)cnt - (uint32_t)pending;
 }
 
-// Warp per slot: the position at step t, how the game stood (ended: its
-// ending code if it was over, since: steps since the step that ended it),
-// and a status (0 ok; 2 the game began before the window or before the last
-// change of reset sources; 3 it began from given setups or an import; the
-// current step always has its position).
+// A team's record for rebuilding a past position: the game and its history
+// ring; its chase store is the team's slot of a global scratch array.
+struct __align__(16) HistSmem {
+    SmemGame g;
+    uint16_t ring[kRing];
+};
+
+// Team of L lanes per slot: the position at step t, how the game stood
+// (ended: its ending code if it was over, since: steps since the step that
+// ended it), and a status (0 ok; 2 the game began before the window or
+// before the last change of reset sources; 3 it began from given setups or
+// an import; the current step always has its position).  The rebuild replays
+// the game's recorded moves from its start, the team's first lane playing
+// them; with several teams per warp, several slots replay side by side.
+// pi_scratch: kPiWords words per slot.
+template <int L>
 __global__ void k_env_hist_positions(EnvArgs A, HistQuery Q, st_position* out, uint8_t* status, uint8_t* ended,
-                                     int32_t* since)
+                                     int32_t* since, uint64_t* pi_scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    RolloutSmem* S = reinterpret_cast<RolloutSmem*>(smem) + (threadIdx.x >> 5);
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= A.N) return;
-    const Team<32> T;
-    const int lane = T.tl;
+    const Team<L> T;
+    const int team = threadIdx.x / L;
+    HistSmem* S = reinterpret_cast<HistSmem*>(smem) + team;
+    const int g = blockIdx.x * (blockDim.x / L) + team;
+    if (g >= A.N) return;   // a whole team leaves; collectives are per team
+    uint64_t* pi = pi_scratch + (size_t)g * kPiWords;
     const GameCore* cur = A.core + g;
     int kind = 0;
-    const long long s0 = game_start(Q, cur, A.N, g, kind);
+    const long long s0 = game_start(Q, cur, A.N, g, kind, T);
     // the step that ended the game, if it is over
     uint32_t code = 0;
     long long e = -1;
@@ -778,36 +793,36 @@ __global__ void k_env_hist_positions(EnvArgs A, HistQuery Q, st_position* out, u
         const long long from = s0 >= 0 ? s0 : Q.lo;
         HistQuery Qe = Q;
         Qe.lo = from;
-        if (Q.t - 1 >= from) e = latest_row(Qe, A.N, g, Q.t - 1, [](uint32_t v) { return row_done(v); }, code);
+        if (Q.t - 1 >= from) e = latest_row(Qe, A.N, g, Q.t - 1, [](uint32_t v) { return row_done(v); }, code, T);
     }
     if (Q.t == Q.now && cur->terminated && e < 0) code = cur->terminated;
-    if (lane == 0) {
+    if (T.leader()) {
         if (ended) ended[g] = (uint8_t)code;
         if (since) since[g] = e >= 0 ? (int32_t)(Q.t - e) : (code ? -1 : 0);
     }
     uint8_t st = 0;
     if (Q.t == Q.now) {
         load_core(&S->g, cur, T);
-        export_position(&S->g, A.ring + (size_t)g * kRing, out + g);
+        export_position(&S->g, A.ring + (size_t)g * kRing, out + g, T);
     } else if (s0 < 0 || s0 < Q.floor) {
         st = 2;
     } else if (kind != kFreshNew) {
         st = 3;
     } else {
-        const uint32_t ep = episode_at(Q, cur, A.N, g, s0);
-        new_game(&S->g, T, A.reset, A.k0, A.k1, (uint32_t)g, ep, S->ring, S->pi);
-        for (long long base = s0; base < Q.t; base += 32) {
-            const long long s = base + lane;
+        const uint32_t ep = episode_at(Q, cur, A.N, g, s0, T);
+        new_game(&S->g, T, A.reset, A.k0, A.k1, (uint32_t)g, ep, S->ring, pi);
+        for (long long base = s0; base < Q.t; base += L) {
+            const long long s = base + T.tl;
             const uint32_t v = s < Q.t ? hist_row(Q, A.N, g, s) : 0x3FFFu;
-            const int cnt = (int)min(32LL, Q.t - base);
+            const int cnt = (int)min((long long)L, Q.t - base);
             for (int j = 0; j < cnt; ++j) {
-                const int a = (int)(__shfl_sync(~0u, v, j) & 0x3FFFu);
-                if (a != 0x3FFF) apply_move(&S->g, T, a, S->ring, S->pi);
+                const int a = T.shfl((int)v, j) & 0x3FFF;
+                if (a != 0x3FFF) apply_move(&S->g, T, a, S->ring, pi);
             }
         }
-        export_position(&S->g, S->ring, out + g);
+        export_position(&S->g, S->ring, out + g, T);
     }
-    if (lane == 0 && status) status[g] = st;
+    if (T.leader() && status) status[g] = st;
 }
 
 // Thread per slot: the row of step t (t < now): action (-1 none), ending
@@ -838,7 +853,7 @@ __global__ void k_env_hist_logs(EnvArgs A, HistQuery Q, int L, uint8_t* setups, 
     const int lane = T.tl;
     const GameCore* cur = A.core + g;
     int kind = 0;
-    const long long s0 = game_start(Q, cur, A.N, g, kind);
+    const long long s0 = game_start(Q, cur, A.N, g, kind, T);
     int16_t* log = logs + (size_t)g * (size_t)L;
     uint8_t st = 0;
     if (s0 < 0 || s0 < Q.floor) st = 2;
@@ -846,7 +861,7 @@ __global__ void k_env_hist_logs(EnvArgs A, HistQuery Q, int L, uint8_t* setups, 
     else if (A.reset.pin_of && A.reset.pin_of[g] >= 0) st = 4;
     int n = 0;
     if (!st) {
-        const uint32_t ep = episode_at(Q, cur, A.N, g, s0);
+        const uint32_t ep = episode_at(Q, cur, A.N, g, s0, T);
         if (A.reset.pool) pool_types(G, T, A.reset.pool, A.reset.pool_m, A.reset.pool_flags, A.k0, A.k1, (uint32_t)g, ep);
         reset_game(G, T, A.k0, A.k1, (uint32_t)g, ep, A.reset.pool ? G->c.type : (const uint8_t*)nullptr);
         for (int i = lane; i < kPieces; i += 32) setups[(size_t)g * kPieces + i] = G->c.type[i];
@@ -1394,10 +1409,17 @@ extern "C" st_status st_env_history_positions(st_env* e, int64_t t, st_position*
     ST_CHECK_ARG(out, "st_env_history_positions: null out");
     DeviceGuard guard(e->device);
     EnvArgs a = env_args(e);
-    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
-    k_env_hist_positions<<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(RolloutSmem), e->stream>>>(
-        a, hist_query(e, t), out, status, ended, since);
-    ST_CUDA(cudaGetLastError());
+    // teams of kHistLanes lanes (32 / kHistLanes slots per warp), their chase
+    // stores in a stream-ordered scratch array
+    constexpr int kHistLanes = 8, kHistWarps = 4, kTeams = kHistWarps * 32 / kHistLanes;
+    uint64_t* pi = nullptr;
+    ST_CUDA(cudaMallocAsync(&pi, (size_t)e->N * kPiWords * sizeof(uint64_t), e->stream));
+    const int blocks = (e->N + kTeams - 1) / kTeams;
+    k_env_hist_positions<kHistLanes><<<blocks, 32 * kHistWarps, kTeams * sizeof(HistSmem), e->stream>>>(
+        a, hist_query(e, t), out, status, ended, since, pi);
+    const cudaError_t err = cudaGetLastError();
+    cudaFreeAsync(pi, e->stream);
+    ST_CUDA(err);
     return ST_OK;
 }
 

@@ -95,7 +95,10 @@ int main(int argc, char** argv)
         uint8_t* hsp = hs.data();
         uint8_t* ep = ended.data();
         int32_t* sp = since.data();
-        launch((N + 3) / 4, 128, 4 * sizeof(RolloutSmem), [=] { k_env_hist_positions(a, q, hpp, hsp, ep, sp); });
+        // teams of 8 lanes, 16 slots per block (the last block ragged when N % 16)
+        std::vector<uint64_t> hpi((size_t)N * kPiWords);
+        uint64_t* pp = hpi.data();
+        launch((N + 15) / 16, 128, 16 * sizeof(HistSmem), [=] { k_env_hist_positions<8>(a, q, hpp, hsp, ep, sp, pp); });
         dump(out + ".hist" + std::to_string(t) + ".pos", hp.data(), hp.size());
         dump(out + ".hist" + std::to_string(t) + ".status", hs.data(), hs.size());
         if (t < d_now) {   // the record of step t
