@@ -369,7 +369,7 @@ __device__ __forceinline__ void hist_after(SmemGame* G, const EnvArgs& A, int g,
 }
 
 template <int L>
-__global__ void k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
+__global__ void __launch_bounds__(128, 6) k_env_step(EnvArgs A, const int16_t* actions, int16_t* action_out, int8_t* reward_out,
                            uint8_t* done_out, int16_t* ply_out, uint8_t* mask_out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1097,8 +1097,12 @@ extern "C" st_status st_env_step(st_env* e, const int16_t* actions, int16_t* act
     ST_CHECK_ARG(!mask_out || aligned16(mask_out), "st_env_step: mask_out must be 16-byte aligned");
     DeviceGuard guard(e->device);
     EnvArgs a = env_args(e);
-    const int blocks = (e->N + kPlainWarps - 1) / kPlainWarps;
-    k_env_step<32><<<blocks, 32 * kPlainWarps, kPlainWarps * sizeof(SmemGame), e->stream>>>(
+    // teams of kStepLanes lanes: 32 / kStepLanes slots per warp (4 lanes: 8
+    // slots; a team size the tuned persistent step does not use, whose
+    // out-of-line engine calls it would otherwise share)
+    constexpr int kStepLanes = 4, kGames = kPlainWarps * 32 / kStepLanes;
+    const int blocks = (e->N + kGames - 1) / kGames;
+    k_env_step<kStepLanes><<<blocks, 32 * kPlainWarps, kGames * sizeof(SmemGame), e->stream>>>(
         a, actions, action_out, reward_out, done_out, ply_out, mask_out);
     ST_CUDA(cudaGetLastError());
     if (e->hist) {

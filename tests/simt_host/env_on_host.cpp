@@ -8,7 +8,7 @@
 // NSPLIT in the environment (default 1) sets the persistent launch's parts
 // per slot.
 // With an actions file ([S][N] int16, -1 = the random policy) the plain
-// path runs instead: one k_env_step launch per ply (teams of 32 lanes, 4
+// path runs instead: one k_env_step launch per ply (teams of 4 lanes, 4
 // warps per block) with those actions supplied.
 #include "host_launch.h"
 #include "env_dev.cu"
@@ -60,7 +60,7 @@ int main(int argc, char** argv)
             uint8_t* dn = done.data() + o;
             int16_t* po = ply.data() + o;
             uint8_t* mo = mask.data() + o * kMaskBytes;
-            launch((N + 3) / 4, 128, 4 * sizeof(SmemGame), [=] { k_env_step<32>(a, gv, ao, ro, dn, po, mo); });
+            launch((N + 31) / 32, 128, 32 * sizeof(SmemGame), [=] { k_env_step<4>(a, gv, ao, ro, dn, po, mo); });
         }
     } else if (L == 8) run<8>(a, &queue, S, gpf, wpb, blocks, act.data(), rew.data(), done.data(), ply.data(), mask.data(), nsplit,
                        part_done.data());
