@@ -57,6 +57,20 @@ def test_plain_step_64_games_1000_plies_bit_exact():
     np.testing.assert_array_equal(stats, ref["stats"].astype(np.int32))
 
 
+def test_plain_step_ragged_slots_sampled():
+    # 1,000 slots (the plain step runs 32 per block: a ragged last block),
+    # 300 one-launch plies; sampled slots against the oracle
+    N, S = 1000, 300
+    env = st.Env(N, seed=13)
+    gpu = _plain_steps(env, S)
+    slots = np.array([0, 1, 31, 32, 500, 991, 992, 998, 999] + list(range(45, N, 89)))
+    for s in slots:
+        r = oracle.env_run(13, 1, S, slot0=int(s))
+        for k in ("action", "reward", "done", "ply"):
+            np.testing.assert_array_equal(gpu[k][:, s], r[k][:, 0], err_msg="%s slot %d" % (k, s))
+        np.testing.assert_array_equal(gpu["mask"][:, s], r["mask"][:, 0], err_msg="mask slot %d" % s)
+
+
 @pytest.mark.parametrize("gpw", [1, 2, 4, 8])
 def test_persistent_run_matches_plain_and_oracle(gpw):
     env = st.Env(64, seed=1)
