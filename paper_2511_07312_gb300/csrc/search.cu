@@ -10,7 +10,7 @@
 // stream.
 // st_rollout: k_roots imports every position once (one warp each) into a
 // root record in HBM; k_draw_samples draws every belief sample ahead (a
-// thread per sample); k_rollout_flat runs one 8-lane team per (position,
+// thread per sample); k_rollout_flat runs one 4-lane team per (position,
 // sample) at a time on a resident grid, copying the root into shared memory,
 // so a single position's samples spread over the whole GPU.  A rollout keeps
 // no history ring (its last two moves start from the root's) and its chase
@@ -19,7 +19,7 @@
 // st_search (steps 1-4): k_search_prep imports every position, lists the
 // searcher's legal moves in ascending order and clears the outputs;
 // k_search_offsets turns the move counts into unit offsets; k_draw_samples
-// draws each configuration once; k_search_rollouts runs one 8-lane team per
+// draws each configuration once; k_search_rollouts runs one 4-lane team per
 // (position, move, sample) unit at a time on a resident grid; k_search_policy
 // forms the values, the magnet policy, the update and the sampled move, one
 // warp per position.
@@ -74,7 +74,7 @@ __global__ void k_belief(const st_position* pos, int P, int K, uint32_t k0, uint
 }
 
 constexpr int kRootWarps = 4;
-constexpr int kFlatLanes = 8;                              // one rollout per 8-lane team
+constexpr int kFlatLanes = 4;                              // one rollout per 4-lane team
 constexpr int kFlatWarps = 2;
 constexpr int kFlatTeams = 32 * kFlatWarps / kFlatLanes;   // rollouts per block
 constexpr int kFlatMinBlocks = 12;                          // resident blocks per SM the registers allow
@@ -117,7 +117,7 @@ __global__ void k_draw_samples(const RootState* roots, int P, int K, uint32_t k0
 constexpr long long kDrawAheadMinUnits = 16384;
 constexpr size_t kDrawAheadBytes = (size_t)1 << 30;
 
-// One (position, sample) unit per 8-lane team at a time, grid-stride over
+// One (position, sample) unit per 4-lane team at a time, grid-stride over
 // the units with a grid of resident blocks; consecutive teams of a block
 // share a position, so its root and plan come mostly from L1.  A rollout
 // keeps no history ring (its last two moves start from the root's); its
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kOffsetThreads) k_search_offsets(const int32_t
     if (threadIdx.x == kOffsetThreads - 1) offs[P] = part[threadIdx.x];
 }
 
-// One (position, move j, sample s) unit per 8-lane team, unit u of position
+// One (position, move j, sample s) unit per 4-lane team, unit u of position
 // p being offs[p] + j*S + s; consecutive teams share a position and mostly a
 // move.  Grid-stride over the units.
 __global__ void __launch_bounds__(32 * kFlatWarps, kFlatMinBlocks) k_search_rollouts(const RootState* roots, const long long* offs, int P, int S, int depth, uint32_t k0,
