@@ -1415,7 +1415,7 @@ extern "C" st_status st_env_history_positions(st_env* e, int64_t t, st_position*
     EnvArgs a = env_args(e);
     // teams of kHistLanes lanes (32 / kHistLanes slots per warp), their chase
     // stores in a stream-ordered scratch array
-    constexpr int kHistLanes = 8, kHistWarps = 4, kTeams = kHistWarps * 32 / kHistLanes;
+    constexpr int kHistLanes = 4, kHistWarps = 4, kTeams = kHistWarps * 32 / kHistLanes;
     uint64_t* pi = nullptr;
     ST_CUDA(cudaMallocAsync(&pi, (size_t)e->N * kPiWords * sizeof(uint64_t), e->stream));
     const int blocks = (e->N + kTeams - 1) / kTeams;

@@ -95,10 +95,10 @@ int main(int argc, char** argv)
         uint8_t* hsp = hs.data();
         uint8_t* ep = ended.data();
         int32_t* sp = since.data();
-        // teams of 8 lanes, 16 slots per block (the last block ragged when N % 16)
+        // teams of 4 lanes, 32 slots per block (the last block ragged when N % 32)
         std::vector<uint64_t> hpi((size_t)N * kPiWords);
         uint64_t* pp = hpi.data();
-        launch((N + 15) / 16, 128, 16 * sizeof(HistSmem), [=] { k_env_hist_positions<8>(a, q, hpp, hsp, ep, sp, pp); });
+        launch((N + 31) / 32, 128, 32 * sizeof(HistSmem), [=] { k_env_hist_positions<4>(a, q, hpp, hsp, ep, sp, pp); });
         dump(out + ".hist" + std::to_string(t) + ".pos", hp.data(), hp.size());
         dump(out + ".hist" + std::to_string(t) + ".status", hs.data(), hs.size());
         if (t < d_now) {   // the record of step t
