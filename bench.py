@@ -352,6 +352,7 @@ def main():
         wpb, gpw, gpf = tuned["warps_per_block"], tuned["games_per_warp"], tuned["games_per_fetch"]
         bps = tuned.get("blocks_per_sm", 0)
     env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
+    bps = env.launch_shape()["blocks_per_sm"]   # resident blocks per SM after the occupancy clamp
     ring = env.run(1, R)   # allocates the ring; later calls reuse it
     env.sync()
 
@@ -454,7 +455,7 @@ def main():
                 "data": "synthetic",
                 "config": dict(workload_config(N, S, R),
                                launch={"warps_per_block": wpb, "games_per_warp": gpw, "games_per_fetch": gpf,
-                                       "blocks_per_sm": bps or "max",
+                                       "blocks_per_sm": bps,
                                        "chosen_by": "autotuner" if tuned else "command line"}),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,

@@ -211,6 +211,12 @@ st_status st_env_run(st_env* env, int32_t n_steps, int32_t ring_steps, int16_t* 
 st_status st_env_set_launch(st_env* env, int32_t warps_per_block, int32_t blocks_per_sm, int32_t games_per_warp,
                             int32_t games_per_fetch);
 
+/* The launch shape st_env_run uses now, as four int32 values: warps per
+ * block, blocks per SM (the request of st_env_set_launch clamped to what
+ * fits on an SM, or that maximum for a request of 0), games per warp and
+ * slots per fetch.  out: host memory owned by the caller. */
+st_status st_env_get_launch(st_env* env, int32_t* out);
+
 /* Wait for the env's stream; return and clear a latched device error. */
 st_status st_env_sync(st_env* env);
 

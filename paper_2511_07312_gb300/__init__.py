@@ -94,6 +94,7 @@ def _declare(L):
         "st_env_step": [vp, vp, vp, vp, vp, vp, vp],
         "st_env_run": [vp, i32, i32, vp, vp, vp, vp, vp],
         "st_env_set_launch": [vp, i32, i32, i32, i32],
+        "st_env_get_launch": [vp, vp],
         "st_env_sync": [vp],
         "st_env_stats": [vp, vp],
         "st_env_export": [vp, vp, i32, vp],
@@ -247,6 +248,14 @@ class Env:
     def set_launch(self, warps_per_block, blocks_per_sm=0, games_per_fetch=1, games_per_warp=1):
         _check(lib().st_env_set_launch(self._h, int(warps_per_block), int(blocks_per_sm), int(games_per_warp),
                                        int(games_per_fetch)))
+
+    def launch_shape(self):
+        """The shape st_env_run uses now: {warps_per_block, blocks_per_sm
+        (resident, after clamping to the occupancy limit), games_per_warp,
+        games_per_fetch}."""
+        v = (ctypes.c_int32 * 4)()
+        _check(lib().st_env_get_launch(self._h, v))
+        return {"warps_per_block": v[0], "blocks_per_sm": v[1], "games_per_warp": v[2], "games_per_fetch": v[3]}
 
     def reset(self, setups=None, which=None):
         self._launch(lib().st_env_reset, self._h, _ptr(setups, torch.uint8, "setups", self.N * 80),

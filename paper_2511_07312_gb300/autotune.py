@@ -57,6 +57,7 @@ def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False, fin
     env = Env(num_games, seed=12345, device=device)
     ring = env.run(1, 4)
     results = []
+    seen = set()
     def timed(wpb, gpw, gpf, bps, n_plies, n_reps):
         env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
         env.run(n_plies, 4, out=ring)        # warm-up, captures the graph
@@ -73,6 +74,14 @@ def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False, fin
         for gpw in GAMES_PER_WARP:
             for gpf in GAMES_PER_FETCH:
                 for bps in (BLOCKS_PER_SM if gpw >= 4 else (0,)):
+                    try:
+                        env.set_launch(wpb, bps, gpf, games_per_warp=gpw)
+                    except RuntimeError:
+                        continue
+                    bps = env.launch_shape()["blocks_per_sm"]   # a request above the occupancy limit is clamped
+                    if (wpb, gpw, gpf, bps) in seen:
+                        continue
+                    seen.add((wpb, gpw, gpf, bps))
                     try:
                         rate = timed(wpb, gpw, gpf, bps, plies, reps)
                     except RuntimeError:

@@ -1142,6 +1142,16 @@ extern "C" st_status st_env_set_launch(st_env* e, int32_t warps_per_block, int32
     return ST_OK;
 }
 
+extern "C" st_status st_env_get_launch(st_env* e, int32_t* out)
+{
+    ST_CHECK_ARG(e && out, "st_env_get_launch: null argument");
+    out[0] = e->wpb;
+    out[1] = e->bps > 0 ? e->bps : std::max(1, e->max_bps);
+    out[2] = e->gpw;
+    out[3] = e->gpf;
+    return ST_OK;
+}
+
 extern "C" st_status st_env_run(st_env* e, int32_t n_steps, int32_t ring_steps, int16_t* action_ring,
                                 int8_t* reward_ring, uint8_t* done_ring, int16_t* ply_ring, uint8_t* mask_ring)
 {

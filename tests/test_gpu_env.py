@@ -152,6 +152,22 @@ def test_oversized_launch_shape_is_rejected_and_leaves_no_error_behind():
     st.Env(64, seed=2).close()
 
 
+def test_launch_shape_reports_the_clamped_blocks_per_sm():
+    env = st.Env(64, seed=1)
+    env.set_launch(8, 0, 1, games_per_warp=4)
+    full = env.launch_shape()
+    assert full["warps_per_block"] == 8 and full["games_per_warp"] == 4 and full["games_per_fetch"] == 1
+    assert full["blocks_per_sm"] >= 1
+    env.set_launch(8, 64, 3, games_per_warp=4)   # far above what fits: clamped to the occupancy limit
+    assert env.launch_shape() == dict(full, games_per_fetch=3)
+    env.set_launch(8, 1, 1, games_per_warp=4)
+    assert env.launch_shape()["blocks_per_sm"] == 1
+    out = env.run(50)
+    env.stream.synchronize()
+    _compare({k: v.cpu().numpy() for k, v in out.items()}, oracle.env_run(1, 64, 50))
+    env.close()
+
+
 def test_full_size_65536_games_2000_plies_sampled_slots():
     # the benchmark workload in the benchmark's launch shape: 65,536 slots,
     # 2,000 plies in one persistent launch, a 16-row ring; sampled slots are
