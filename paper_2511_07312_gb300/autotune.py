@@ -44,7 +44,9 @@ def load(num_games, device=0, plies=400):
 
 def tune(num_games, device=0, plies=400, reps=3, force=False, verbose=False, final_plies=None, finalists=4):
     """Return {"warps_per_block", "games_per_warp", "games_per_fetch",
-    "blocks_per_sm", "env_steps_per_s"} of the fastest shape, timed with
+    "blocks_per_sm" (resident: a request above what fits on an SM is
+    clamped, and shapes that clamp to one already timed are skipped),
+    "env_steps_per_s"} of the fastest shape, timed with
     CUDA events: every shape on runs of `plies` plies, then (final_plies)
     the `finalists` fastest again on runs of final_plies plies, the length
     the caller will launch (how full the last wave of slots is depends on
