@@ -804,6 +804,9 @@ __device__ __noinline__ int gen_moves(SmemGame* G, Team<L>, int P, uint32_t rule
                     const int clo = ctr - 10 * R.ns, chi = ctr + 10 * R.nn, rlo = ctr - R.nw, rhi = ctr + R.ne;
                     const int wlo = min(clo, rlo) >> 5, whi = max(chi, rhi) >> 5;
                     int m = (c + 640 - 2 * wlo) % 10;
+                    // kept rolled: the unrolled copies cost more in instruction
+                    // fetch than the loop's branches
+#pragma unroll 1
                     for (int wi = wlo; wi <= whi; ++wi) {
                         const int b0 = 32 * wi;
                         uint32_t v = ((0x40100401u << m) & range32(clo - b0, chi - b0)) | range32(rlo - b0, rhi - b0);
