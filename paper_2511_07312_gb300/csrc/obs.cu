@@ -577,7 +577,9 @@ extern "C" st_status st_obs_encode(const uint8_t* setups, const int16_t* actions
     if (need_planes) {
         ST_CUDA(cudaMallocAsync(&scratch, (size_t)B * sizeof(ItemState), s));
         if (!status) {
-            ST_CUDA(cudaMallocAsync(&own_status, (size_t)B, s));
+            const cudaError_t e2 = cudaMallocAsync(&own_status, (size_t)B, s);
+            if (e2 != cudaSuccess) cudaFreeAsync(scratch, s);   // the scratch is not left behind
+            ST_CUDA(e2);
             status = own_status;
         }
     }
