@@ -449,8 +449,15 @@ extern "C" st_status st_serve_create(const st_serve_config* cfg, st_server** out
         cudaStream_t str;
         cudaEvent_t ev;
         err = cudaStreamCreateWithFlags(&str, cudaStreamNonBlocking);
-        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (err == cudaSuccess) { s->streams.push_back(str); s->batch_done.push_back(ev); s->stream_busy.push_back(0); }
+        if (err != cudaSuccess) break;
+        err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            cudaStreamDestroy(str);   // not yet in the server's lists, which destroy frees
+            break;
+        }
+        s->streams.push_back(str);
+        s->batch_done.push_back(ev);
+        s->stream_busy.push_back(0);
     }
     if (err != cudaSuccess) {
         stg::set_error("st_serve_create: %s", cudaGetErrorString(err));
